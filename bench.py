@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark of the LEWalk hot path on GB300.
+
+One "step" = one pass of the whole hot path over one batch of samples of the
+workload graph: lap_sample (Wilson LE_v run + uniform-start and pi-start
+v-absorbed walks per sample, counts folded into uint64 totals) followed by
+the FP64 finalize (ECC for every node and Kemeny's constant).  The graph is
+resident in HBM; graph ingest and root choice run once before timing.
+
+Workload (default): Barabasi-Albert n = 10^6, m = 5, root = highest-degree
+node, 2^16 samples in total over 4 steps of 16384.
+
+Printed: one JSON line (rank 0) with throughput in walk steps/s (Wilson steps
+incl. loops + absorbed-walk steps), the sampler's HBM roofline, the CPU
+oracle baseline, an end-to-end figure through the C ABI with host buffers,
+clocks, and the time to reach relative error 1e-2 on the small Erdos-Renyi
+workload against its dense FP64 ground truth.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# Algorithmic bytes per unit (32-byte sectors of random access):
+#   Wilson step: row record, column entry, next node's state, state write,
+#                visited test -> 5 sectors; tree insertion (retrace): state
+#                read + write -> 2 sectors; absorbed-walk step: row record,
+#                column entry, count -> 3 sectors.
+SECTOR = 32
+BYTES_WILSON_STEP = 5 * SECTOR
+BYTES_TREE_INSERT = 2 * SECTOR
+BYTES_WALK_STEP = 3 * SECTOR
+
+BASELINE_METRIC = ("time to rel.err 1e-2 for all-node ECC+Kemeny; walk steps/s; CV vs plain, 1 GB300")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ba_1m", choices=["ba_1m", "er_1000", "rmat_22"])
+    ap.add_argument("--batch", type=int, default=16384, help="samples per step")
+    ap.add_argument("--seed", type=int, default=20231117)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
+    ap.add_argument("--no-tta", action="store_true", help="skip the time-to-accuracy run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--ws-frac", type=float, default=0.6, help="fraction of free HBM lent as Wilson state")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def load_graph(name):
+    from paper_2311_10290_gb300 import inputs
+    return {"ba_1m": inputs.ba_1m, "er_1000": inputs.er_1000, "rmat_22": inputs.rmat_22}[name]()
+
+
+# ------------------------------------------------------------ clocks
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def cpu_oracle_rate(g, v, seed, target_seconds, first_id=1 << 30):
+    """The oracle as it stands, on all host cores (disjoint sample-id ranges),
+    on a bounded number of samples of the same workload."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    c = oracle.sample(g.row_ptr, g.col, v, seed, first_id, 1, keep_per_sample=True)
+    t1 = time.perf_counter() - t0
+    per_sample = max(t1, 1e-4)
+    per_core = max(1, int(target_seconds / per_sample))
+    count = per_core * cores
+    t0 = time.perf_counter()
+    c = oracle.sample_threads(g.row_ptr, g.col, v, seed, first_id + 1, count, cores)
+    dt = time.perf_counter() - t0
+    steps = c.sum_y1 + int(c.cnt2.sum()) + c.sum_y2
+    return {"value": steps / dt, "unit": "walk steps/s", "cores": cores, "kind": "oracle",
+            "sample": "%d samples (ids %d..%d) of the same graph and root, %d threads, %.1f s" %
+                      (count, first_id + 1, first_id + count, cores, dt)}
+
+
+# ------------------------------------------------------------ accuracy
+
+def read_truth():
+    path = os.path.join(ROOT, "tests", "golden", "dense_truth_er1000.txt")
+    ecc, kc, meta = [], None, {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#"):
+                continue
+            k, val = line.split()
+            if k == "ecc":
+                ecc.append(float(val))
+            elif k == "kemeny":
+                kc = float(val)
+            else:
+                meta[k] = val
+    return np.array(ecc), kc, meta
+
+
+def time_to_accuracy(torch, LapGraph, seeds=10, target=1e-2):
+    """Smallest omega (doubling from 2^8) at which the mean over seeds of the
+    ECC max relative error and of the Kemeny relative error are both <= 1e-2,
+    on Erdos-Renyi G(1000, 0.01) against its dense FP64 truth; then the GPU
+    time of one fresh run to that omega."""
+    import hashlib
+    from paper_2311_10290_gb300 import inputs
+    g = inputs.er_1000()
+    ecc_t, kc_t, meta = read_truth()
+    h = hashlib.sha1()
+    h.update(g.row_ptr.astype("<i4").tobytes())
+    h.update(g.col.astype("<i4").tobytes())
+    if h.hexdigest() != meta.get("sha1"):
+        return {"error": "dense truth file does not match the generated graph"}
+    handles = [LapGraph(g.row_ptr, g.col, workspace_bytes=8 * g.n * 65536) for _ in range(seeds)]
+    for H in handles:
+        H.set_root()
+    omega, done, curve = 0, 0, []
+    found = None
+    for lg in range(8, 22):
+        target_omega = 1 << lg
+        e1, e2 = [], []
+        for s, H in enumerate(handles):
+            H.sample(target_omega - done, 1000 + s)
+        for H in handles:
+            ec = H.ecc()
+            e1.append(float(np.max(np.abs(ec - ecc_t) / ecc_t)))
+            e2.append(abs(H.kemeny() - kc_t) / kc_t)
+        done = target_omega
+        curve.append((target_omega, float(np.mean(e1)), float(np.mean(e2))))
+        if np.mean(e1) <= target and np.mean(e2) <= target:
+            found = target_omega
+            break
+    for H in handles:
+        H.close()
+    if found is None:
+        return {"workload": "er_1000", "reached": False, "curve": curve}
+    H = LapGraph(g.row_ptr, g.col, workspace_bytes=8 * g.n * 65536)
+    H.set_root()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    H.sample(found, 7)
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    H.ecc(out)
+    kc = H.kemeny()
+    b.record()
+    torch.cuda.synchronize()
+    H.close()
+    return {"workload": "er_1000 (Erdos-Renyi G(1000,0.01), dense FP64 truth)", "seeds": seeds,
+            "omega": found, "gpu_seconds": a.elapsed_time(b) / 1e3,
+            "ecc_max_rel_err_mean": curve[-1][1], "kc_rel_err_mean": curve[-1][2],
+            "curve": [{"omega": o, "ecc_max_rel": round(x, 5), "kc_rel": round(y, 6)} for o, x, y in curve]}
+
+
+# ------------------------------------------------------------ ours
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, LapGraph, lap_counts
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    g = load_graph(args.workload)
+    free, _ = torch.cuda.mem_get_info()
+    G = LapGraph(g.row_ptr, g.col, workspace_bytes=int(free * args.ws_frac))
+    v = G.set_root()
+    B = args.batch
+    total_steps = args.warmup + args.steps
+    G.set_option(LAP_OPT_CURSOR, rank * total_steps * B)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+
+    def step():
+        G.sample(B, args.seed)
+        G.ecc(out)                      # finalize on device (ECC for every node)
+        return G.kemeny()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    c1a, c2a, sa = lap_counts(G.h, g.n)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(dev) as clk:
+        for k in range(args.steps):
+            flush.zero_()                # L2 flush between timed steps (outside the events)
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            ev[k][0].record()
+            G.sample(B, args.seed)
+            ev[k][1].record()
+            G.ecc(out)
+            G.kemeny()
+            ev[k][2].record()
+            torch.cuda.synchronize()
+    c1b, c2b, sb = lap_counts(G.h, g.n)
+    step_ms = [a.elapsed_time(c) for a, _, c in ev]
+    kern_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    t_total = sum(step_ms) / 1e3
+    wilson = int(sb[1]) - int(sa[1])
+    uwalk = int(c2b.sum()) - int(c2a.sum())
+    piwalk = int(sb[2]) - int(sa[2])
+    samples = int(sb[0]) - int(sa[0])
+    walk_steps = wilson + uwalk + piwalk
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        w = torch.tensor([walk_steps], dtype=torch.int64, device="cuda")
+        dist.all_reduce(w)
+        t_total, walk_steps_all = float(t.item()), int(w.item())
+    else:
+        walk_steps_all = walk_steps
+    value = walk_steps_all / t_total
+    kernel_s = sum(kern_ms) / 1e3 / args.steps
+    alg_bytes = (BYTES_WILSON_STEP * wilson + BYTES_TREE_INSERT * (g.n - 1) * samples +
+                 BYTES_WALK_STEP * (uwalk + piwalk)) / args.steps
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / kernel_s / 1e9
+    traffic = os.environ.get("LAP_NCU_TRAFFIC_PER_LAUNCH")
+    res = {
+        "metric": BASELINE_METRIC, "value": value, "unit": "walk steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64 counts, f64 finalize", "data": "synthetic",
+        "config": {"workload": g.name + " (Barabasi-Albert n=1e6, m=5; root = max-degree node)"
+                   if args.workload == "ba_1m" else g.name,
+                   "n": g.n, "arcs": g.arcs, "root": v, "samples_per_step": B,
+                   "samples_timed": samples * world, "slots": G.slots,
+                   "wilson_state_gb": round(G.slots * 8 * g.n / 1e9, 1),
+                   "l2": "256 MB buffer written between timed steps (outside the events); "
+                         "Wilson state working set far above L2",
+                   "parallelism": "sample ids sharded over %d GPU(s)" % world},
+        "walk_steps": {"wilson": wilson, "uniform_walk": uwalk, "pi_walk": piwalk,
+                       "wilson_steps_per_node_per_sample": wilson / max(1, samples) / g.n},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": float(traffic) if traffic else None,
+                     "kernel": "lewalk_kernel", "kernel_ms": kernel_s * 1e3,
+                     "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind},
+        "gpu_launches": args.steps * 7,
+    }
+    res["clocks"] = clk.summary()
+    G.close()
+    del flush, out
+    torch.cuda.empty_cache()
+    # End to end through the C ABI with host buffers: each step copies the CSR
+    # from pinned host memory (graph create), samples, finalizes and reads the
+    # ECC vector and Kemeny's constant back to the host.
+    res["e2e"] = run_e2e(args, g, torch, LapGraph, rank, world)
+    if rank == 0 and not args.no_cpu and world == 1:
+        res["cpu_baseline"] = cpu_oracle_rate(g, v, args.seed, args.cpu_seconds)
+    if rank == 0 and not args.no_tta:
+        res["time_to_accuracy"] = time_to_accuracy(torch, LapGraph)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return res
+
+
+def run_e2e(args, g, torch, LapGraph, rank, world):
+    rp = torch.from_numpy(g.row_ptr).pin_memory()
+    cl = torch.from_numpy(g.col).pin_memory()
+    ecc_host = torch.empty(g.n, dtype=torch.float64).pin_memory()
+    B = args.batch
+    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, lap_counts
+    free, _ = torch.cuda.mem_get_info()
+    ws = int(free * args.ws_frac)
+    times, steps_total = [], 0
+    for k in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H = LapGraph(rp.numpy(), cl.numpy(), workspace_bytes=ws)
+        H.set_root()
+        H.set_option(LAP_OPT_CURSOR, (1 << 31) + (rank * args.e2e_steps + k) * B)
+        H.sample(B, args.seed)
+        H.ecc(ecc_host.numpy())
+        H.kemeny()
+        t1 = time.perf_counter()
+        _, c2, s = lap_counts(H.h, g.n)
+        H.close()
+        times.append(t1 - t0)
+        steps_total += int(s[1]) + int(c2.sum()) + int(s[2])
+    t = float(np.sum(times))
+    return {"value": steps_total * world / t, "unit": "walk steps/s",
+            "h2d_bytes_per_step": int(rp.numel() * 4 + cl.numel() * 4),
+            "d2h_bytes_per_step": int(g.n * 8 + 8),
+            "ms_per_step": 1e3 * t / len(times),
+            "note": "graph create (H2D of the CSR, GPU validation, BFS) + sample + finalize + D2H of ECC and Kemeny"}
+
+
+# ------------------------------------------------------------ reference (oracle)
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    g = load_graph(args.workload)
+    v = oracle.root_max_degree(g.row_ptr)
+    cores = os.cpu_count() or 1
+    # Size a step to a few seconds of host time.
+    t0 = time.perf_counter()
+    oracle.sample(g.row_ptr, g.col, v, args.seed, 0, 1)
+    per = max(time.perf_counter() - t0, 1e-4)
+    per_step = cores * max(1, min(64, int(4.0 / per)))
+    times, steps = [], 0
+    nxt = 1
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        c = oracle.sample_threads(g.row_ptr, g.col, v, args.seed, nxt, per_step, cores)
+        ld, ec, kc = oracle.finalize(g.row_ptr, v, per_step, c.cnt1, c.cnt2, c.sum_y1, c.sum_y2)
+        dt = time.perf_counter() - t0
+        nxt += per_step
+        if k >= args.warmup:
+            times.append(dt)
+            steps += c.sum_y1 + int(c.cnt2.sum()) + c.sum_y2
+    t = float(np.sum(times))
+    value = steps / t
+    return {"impl": "reference", "metric": BASELINE_METRIC, "value": value, "unit": "walk steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64 counts, f64 finalize", "data": "synthetic",
+            "config": {"workload": g.name, "n": g.n, "arcs": g.arcs, "root": v, "samples_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": "walk steps/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d samples per step on %d threads (bounded sample of the workload)" %
+                                       (per_step, cores)},
+            "e2e": {"value": value, "unit": "walk steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        res = run_ours(args, rank, world)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * lap.h - C ABI of the GB300 library for Monte Carlo estimation of Laplacian
+ * pseudo-inverse quantities by loop-erased-walk sampling (Liao et al.,
+ * "Scalable Algorithms for Laplacian Pseudo-inverse Computation",
+ * arXiv 2311.10290).
+ *
+ * Problem statement (Section 2): G = (V, E) unweighted, undirected and
+ * connected, n = |V|, m = |E|, L = D - A, P = D^{-1} A.  A landmark (root) v is
+ * fixed (Section 6, "Parameters": the highest-degree node by default).  For
+ * every sample id i the library runs, on the GPU,
+ *   - one Wilson LE_v run (Section 3.4; Alg. 2 and Alg. 4), counting every
+ *     pass of every node (visits) and the total number of walk steps Y1_i,
+ *   - one v-absorbed walk from a uniformly drawn start (Alg. 2), counting the
+ *     passes of every node,
+ *   - one v-absorbed walk from a start drawn from pi(u) = d_u / 2m (Alg. 4),
+ *     whose length is Y2_i,
+ * and maps the integer counts to (L^+)_uu, electrical closeness centrality
+ * c(u) = (n-1) / (n (L^+)_uu + Tr L^+) (Section 2) and Kemeny's constant
+ * kappa = E[Y1 - Y2] (Section 5, Alg. 4).
+ *
+ * Randomness is counter-based (Philox4x32-10, SC'11), keyed by the seed, the
+ * sample id, and (node, draw index) for Wilson draws or the step index for the
+ * absorbed walks.  Counts are therefore a pure function of (graph, root, seed,
+ * sample ids): they do not depend on launch shape, concurrency or how the
+ * sample ids are split across calls.
+ *
+ * Conventions shared by every function:
+ *   - Every function returns lap_status; nothing else crosses the ABI.
+ *   - Node ids are 0..n-1 in the caller's order.  CSR arrays are int32:
+ *     row_ptr[n+1], col_idx[2m]; every edge appears in both rows; rows sorted
+ *     strictly ascending (no duplicates); no self-loops; 2m < 2^31.
+ *   - A lap_graph handle owns the device memory it allocates; the caller owns
+ *     every buffer it passes in.  Handles are not thread-safe.
+ *   - Work is queued on the handle's stream (lap_set_stream; default: the
+ *     legacy default stream).  lap_sample is asynchronous; functions that
+ *     return results synchronise the stream first.
+ *   - After an error, lap_last_error(handle) gives a one-line explanation.
+ *     Device-side failures (step budget exceeded, CUDA errors) are sticky:
+ *     every later call on the handle returns the same status until
+ *     lap_set_root resets the handle.
+ */
+#ifndef LAP_H_
+#define LAP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lap_graph lap_graph;
+
+typedef enum {
+    LAP_OK = 0,
+    LAP_ERR_INVALID_ARG = 1,   /* a NULL pointer, n < 2, a bad option, a seed change, ... */
+    LAP_ERR_BAD_CSR = 2,       /* row_ptr not monotone, col out of range, unsorted or duplicate entries */
+    LAP_ERR_NOT_SYMMETRIC = 3, /* some arc (u,w) has no reverse arc (w,u) */
+    LAP_ERR_SELF_LOOP = 4,
+    LAP_ERR_DISCONNECTED = 5,  /* the root does not reach every node (Section 2 assumes G connected) */
+    LAP_ERR_TOO_LARGE = 6,     /* 2m >= 2^31, or more than 2^32 sample ids */
+    LAP_ERR_OOM = 7,           /* a device allocation failed or the workspace is too small */
+    LAP_ERR_NO_SAMPLES = 8,    /* results requested before any sample was drawn */
+    LAP_ERR_STEP_LIMIT = 9,    /* a sample exceeded the per-sample step budget */
+    LAP_ERR_CUDA = 10,         /* a CUDA runtime error; see lap_last_error */
+    LAP_ERR_NO_ROOT = 11       /* lap_set_root has not been called */
+} lap_status;
+
+/* Options for lap_set_option. */
+typedef enum {
+    LAP_OPT_STEP_LIMIT = 1,    /* per-sample budget on each of the three walks' steps; 0 = default
+                                  (2^20 + 1024 n); the value is clamped to [1, 2^62] */
+    LAP_OPT_SLOTS = 2,         /* samples kept in flight per launch; 0 = as many as the workspace holds */
+    LAP_OPT_BLOCK = 3,         /* threads per block of the sampler launch; 0 = automatic */
+    LAP_OPT_CURSOR = 4         /* first sample id of the next lap_sample (default 0); only before the
+                                  first sample after lap_set_root.  Lets several processes or GPUs
+                                  draw disjoint sample-id ranges whose counts add up exactly. */
+} lap_option;
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t lap_version(void);
+
+/*
+ * Ingest a CSR graph (row a1 of the hot path: the graph model of Section 2).
+ *   n              number of nodes, >= 2.
+ *   row_ptr        int32[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = 2m.
+ *   col_idx        int32[2m].
+ *   ptrs_on_device 0: both pointers are host memory; 1: both are device memory
+ *                  (e.g. torch CUDA tensors) on the current device.
+ *   out            receives the new handle; *out is NULL on failure.
+ * The arrays are copied; the caller keeps ownership of its buffers.  The CSR
+ * is validated on the GPU (monotone row_ptr, col range, strictly ascending
+ * rows, no self-loop, symmetry) and degrees and per-node row records are
+ * built.  Errors: LAP_ERR_INVALID_ARG, LAP_ERR_BAD_CSR, LAP_ERR_SELF_LOOP,
+ * LAP_ERR_NOT_SYMMETRIC, LAP_ERR_TOO_LARGE, LAP_ERR_OOM, LAP_ERR_CUDA.  On error
+ * nothing is allocated and the reason is available from lap_last_error(NULL).
+ */
+lap_status lap_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                            int ptrs_on_device, lap_graph **out);
+
+/* Frees all device memory the handle owns.  Accepts NULL. */
+lap_status lap_graph_destroy(lap_graph *g);
+
+/* Queue all later work of the handle on `cuda_stream` (a cudaStream_t, e.g.
+ * torch.cuda.current_stream().cuda_stream); NULL selects the legacy default
+ * stream. */
+lap_status lap_set_stream(lap_graph *g, void *cuda_stream);
+
+/* Set an option (see lap_option). */
+lap_status lap_set_option(lap_graph *g, int32_t option, int64_t value);
+
+/*
+ * Device workspace for the per-sample Wilson state (8 bytes per node per
+ * sample in flight).  lap_workspace_query returns the bytes needed to keep
+ * `slots` samples in flight.  lap_set_workspace lends the handle a caller-owned
+ * device buffer (at least 8*n bytes, 256-byte aligned), which must stay alive
+ * while the handle uses it; the handle zeroes it.  Without a workspace,
+ * lap_sample allocates one itself (up to 1/2 of the free device memory).
+ */
+lap_status lap_workspace_query(const lap_graph *g, uint64_t slots, uint64_t *bytes);
+lap_status lap_set_workspace(lap_graph *g, void *device_ptr, uint64_t bytes);
+
+/*
+ * Choose the landmark v (Section 3.1: L^+ does not depend on v, so an
+ * easy-to-hit node is picked; Section 6: the highest-degree node).
+ *   v >= 0  use node v;   v < 0  the highest-degree node, smallest id on ties.
+ * A breadth-first search from v on the GPU checks that v reaches all n nodes
+ * (LAP_ERR_DISCONNECTED otherwise) and records hop distances.  Resets all
+ * counts, the sample cursor and the seed, and clears a sticky error.
+ * root_out (may be NULL) receives the chosen v.
+ */
+lap_status lap_set_root(lap_graph *g, int32_t v, int32_t *root_out);
+
+/*
+ * Draw sample ids [cursor, cursor + n_samples) and add their counts (the
+ * cursor starts at 0, or at LAP_OPT_CURSOR)
+ * (Alg. 2 and Alg. 4; hot-path rows a2-a5).  Asynchronous.  The first call
+ * after lap_set_root fixes the seed; a later call with another seed returns
+ * LAP_ERR_INVALID_ARG.  Two calls of k/2 samples give exactly the counts of
+ * one call of k.  Errors: LAP_ERR_NO_ROOT, LAP_ERR_INVALID_ARG,
+ * LAP_ERR_TOO_LARGE (cursor would pass 2^32), LAP_ERR_OOM, LAP_ERR_CUDA; a step
+ * budget overrun is reported as LAP_ERR_STEP_LIMIT by the next synchronising
+ * call.
+ */
+lap_status lap_sample(lap_graph *g, uint64_t n_samples, uint64_t seed);
+
+/*
+ * lap_sample that also writes each sample's Y1 (Wilson steps, loops
+ * included) and Y2 (pi-start walk length) to device arrays y1_dev[n_samples],
+ * y2_dev[n_samples] (caller-owned device memory; entry q belongs to sample id
+ * cursor + q).  Both pointers must be set, or both NULL (then it is
+ * lap_sample).  Used for variance estimates and sampled parity checks.
+ */
+lap_status lap_sample_trace(lap_graph *g, uint64_t n_samples, uint64_t seed, uint64_t *y1_dev, uint64_t *y2_dev);
+
+/* Wait for queued work and report a device-side failure, if any. */
+lap_status lap_sync(lap_graph *g);
+
+/*
+ * Results (hot-path row a6, FP64).  With omega samples drawn:
+ *   y1(u) = cnt1[u]/(omega d_u) ~ (L_v^{-1})_uu,
+ *   y2(u) = cnt2[u]/(omega d_u) ~ (1/n) e_u^T L_v^{-1} 1,
+ *   (L^+)_uu = y1(u) - 2 y2(u) + (1/n) sum_w y2(w)   (u != v),
+ *   (L^+)_vv = (1/n) sum_w y2(w)                      (Section 3.1, element-wise Thm 1),
+ *   c(u) = (n-1) / (n (L^+)_uu + sum_w (L^+)_ww)      (Section 2),
+ *   kappa = (sum_i Y1_i - sum_i Y2_i) / omega         (Alg. 4).
+ * For very small omega the estimated denominator of c(u) can be <= 0; the
+ * raw IEEE result is returned.  `out` has n doubles (1 for lap_kemeny); it is
+ * host memory when out_on_device = 0, device memory otherwise.  These calls
+ * synchronise the handle's stream.  Errors: LAP_ERR_NO_ROOT,
+ * LAP_ERR_NO_SAMPLES, LAP_ERR_INVALID_ARG, sticky errors.
+ */
+lap_status lap_ecc(lap_graph *g, double *out, int out_on_device);
+lap_status lap_ldiag(lap_graph *g, double *out, int out_on_device);
+lap_status lap_kemeny(lap_graph *g, double *out1);
+
+/*
+ * Raw integer state (for parity checks and checkpointing):
+ *   cnt1[n]  visits per node summed over samples (0 at v),
+ *   cnt2[n]  passes of the uniform-start walks per node,
+ *   sums[4]  = { omega (samples drawn), sum Y1, sum Y2, seed }.
+ * Any pointer may be NULL.  Host memory when on_device = 0.  Synchronises.
+ */
+lap_status lap_counts(lap_graph *g, uint64_t *cnt1, uint64_t *cnt2, uint64_t *sums, int on_device);
+
+/* Hop distance from the root for every node (int32[n]; host when
+ * on_device = 0), as found by the connectivity check of lap_set_root. */
+lap_status lap_hops(lap_graph *g, int32_t *out, int on_device);
+
+/* Number of nodes, arcs (2m) and the current root (-1 when unset). */
+lap_status lap_graph_info(const lap_graph *g, int32_t *n, int64_t *arcs, int32_t *root);
+
+/* One-line description of the last error on this handle (or of the last
+ * failed lap_graph_create when g is NULL).  Never NULL. */
+const char *lap_last_error(const lap_graph *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAP_H_ */

@@ -1,0 +1,122 @@
+// FP64 finalize (hot-path row a6): integer counts -> (L^+)_uu, ECC, Kemeny.
+//
+//   y1(u) = cnt1[u] / (omega d_u)    estimates (L_v^{-1})_uu          (Alg. 2; LE-walk lemma)
+//   y2(u) = cnt2[u] / (omega d_u)    estimates (1/n) e_u^T L_v^{-1} 1 (Alg. 2; "sample the paths")
+//   (L^+)_uu = y1(u) - 2 y2(u) + (1/n) sum_w y2(w)   (u != v; element-wise Thm 1)
+//   (L^+)_vv = (1/n) sum_w y2(w)
+//   c(u) = (n-1) / (n (L^+)_uu + sum_w (L^+)_ww)     (Section 2, ECC)
+// with cnt1[u] = omega + (repeat visits of u) for u != v.
+//
+// Sums use a fixed two-level order (per-block tree, then one block over the
+// partials), so results are deterministic run to run.  All arithmetic uses
+// explicitly rounded operations (no FMA contraction).
+#include "lap_internal.h"
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kParts = 1024;   // number of partial sums (fixed)
+
+__device__ __forceinline__ double y_of(unsigned long long c, double wd) { return __ddiv_rn((double)c, wd); }
+
+__device__ double block_sum(double x)
+{
+    __shared__ double sh[kBlock];
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int w = kBlock / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] = __dadd_rn(sh[threadIdx.x], sh[threadIdx.x + w]);
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Partial p covers nodes [p*chunk, (p+1)*chunk).  which = 0: sum of y2;
+// which = 1: sum of ldiag.
+__global__ void partial_kernel(const int2 *__restrict__ rowinfo, int32_t n, double omega,
+                               const unsigned long long *__restrict__ cnt2, const double *__restrict__ ldiag,
+                               int which, int64_t chunk, double *part)
+{
+    const int64_t a = (int64_t)blockIdx.x * chunk;
+    const int64_t b = a + chunk < n ? a + chunk : n;
+    double acc = 0.0;
+    for (int64_t u = a + threadIdx.x; u < b; u += kBlock) {
+        double x;
+        if (which == 0) x = y_of(cnt2[u], __dmul_rn(omega, (double)rowinfo[u].y));
+        else x = ldiag[u];
+        acc = __dadd_rn(acc, x);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void total_kernel(const double *part, int parts, double *out)
+{
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < parts; k += kBlock) acc = __dadd_rn(acc, part[k]);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+__global__ void ldiag_kernel(const int2 *__restrict__ rowinfo, int32_t n, int32_t root, double omega,
+                             unsigned long long omega_u, const unsigned long long *__restrict__ rep1,
+                             const unsigned long long *__restrict__ cnt2, const double *s2, double *ldiag)
+{
+    const double lvv = __ddiv_rn(*s2, (double)n);
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        if (u == root) { ldiag[u] = lvv; continue; }
+        const double wd = __dmul_rn(omega, (double)rowinfo[u].y);
+        const double y1 = y_of(omega_u + rep1[u], wd);
+        const double y2 = y_of(cnt2[u], wd);
+        ldiag[u] = __dadd_rn(__dsub_rn(y1, __dmul_rn(2.0, y2)), lvv);
+    }
+}
+
+__global__ void ecc_kernel(int32_t n, const double *__restrict__ ldiag, const double *tr, double *ecc)
+{
+    const double t = *tr;
+    const double num = (double)(n - 1);
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        ecc[u] = __ddiv_rn(num, __dadd_rn(__dmul_rn((double)n, ldiag[u]), t));
+}
+
+__global__ void counts_kernel(int32_t n, int32_t root, unsigned long long omega,
+                              const unsigned long long *__restrict__ rep1, unsigned long long *cnt1)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        cnt1[u] = (u == root) ? 0ull : omega + rep1[u];
+}
+
+int grid_for(int64_t n)
+{
+    int64_t g = (n + kBlock - 1) / kBlock;
+    return (int)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
+}
+
+}  // namespace
+
+// red must hold kParts + 2 doubles: partials, then sum y2, then trace.
+cudaError_t lap_launch_finalize(const int2 *rowinfo, int32_t n, int32_t root, uint64_t omega,
+                                const unsigned long long *rep1, const unsigned long long *cnt2,
+                                double *ldiag, double *ecc, double *red, cudaStream_t st)
+{
+    const double w = (double)omega;
+    const int64_t chunk = ((int64_t)n + kParts - 1) / kParts;
+    double *part = red, *s2 = red + kParts, *tr = red + kParts + 1;
+    partial_kernel<<<kParts, kBlock, 0, st>>>(rowinfo, n, w, cnt2, nullptr, 0, chunk, part);
+    total_kernel<<<1, kBlock, 0, st>>>(part, kParts, s2);
+    ldiag_kernel<<<grid_for(n), kBlock, 0, st>>>(rowinfo, n, root, w, (unsigned long long)omega, rep1, cnt2, s2, ldiag);
+    partial_kernel<<<kParts, kBlock, 0, st>>>(rowinfo, n, w, nullptr, ldiag, 1, chunk, part);
+    total_kernel<<<1, kBlock, 0, st>>>(part, kParts, tr);
+    ecc_kernel<<<grid_for(n), kBlock, 0, st>>>(n, ldiag, tr, ecc);
+    return cudaGetLastError();
+}
+
+cudaError_t lap_launch_counts(int32_t n, int32_t root, uint64_t omega, const unsigned long long *rep1,
+                              unsigned long long *cnt1, cudaStream_t st)
+{
+    counts_kernel<<<grid_for(n), kBlock, 0, st>>>(n, root, (unsigned long long)omega, rep1, cnt1);
+    return cudaGetLastError();
+}

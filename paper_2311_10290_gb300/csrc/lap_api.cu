@@ -1,0 +1,463 @@
+// Host side of the C ABI declared in include/lap.h: argument checks, device
+// memory of a handle, stream handling, launch sizing and error reporting.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lap_internal.h"
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+lap_status fail(lap_graph *g, lap_status s, const std::string &msg)
+{
+    if (g) g->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+lap_status cuda_fail(lap_graph *g, cudaError_t e, const char *where)
+{
+    std::string m = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
+    if (g) g->sticky = LAP_ERR_CUDA;
+    return fail(g, LAP_ERR_CUDA, m);
+}
+
+#define LAP_CUDA(g, call)                                            \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((g), e_, #call);     \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count > 0 ? count : 1));
+}
+
+void free_all(lap_graph *g)
+{
+    cudaFree(g->d_row_ptr);
+    cudaFree(g->d_col);
+    cudaFree(g->d_rowinfo);
+    cudaFree(g->d_hops);
+    cudaFree(g->d_rep1);
+    cudaFree(g->d_cnt2);
+    cudaFree(g->d_acc);
+    cudaFree(g->d_ldiag);
+    cudaFree(g->d_ecc);
+    cudaFree(g->d_red);
+    cudaFree(g->d_slot_epoch);
+    if (g->ws_owned) cudaFree(g->ws);
+}
+
+lap_status check_sticky(lap_graph *g)
+{
+    if (!g) return fail(nullptr, LAP_ERR_INVALID_ARG, "NULL handle");
+    if (g->sticky != LAP_OK) return g->sticky;
+    return LAP_OK;
+}
+
+uint64_t default_step_limit(int32_t n) { return (1ull << 20) + 1024ull * (uint64_t)n; }
+
+// Reads the device status word and turns it into a sticky error.
+lap_status poll_status(lap_graph *g)
+{
+    LapDevAcc h;
+    LAP_CUDA(g, cudaMemcpyAsync(&h, g->d_acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    if (h.status & LAP_DEV_STEP_LIMIT) {
+        g->sticky = LAP_ERR_STEP_LIMIT;
+        return fail(g, LAP_ERR_STEP_LIMIT, "a sample exceeded the per-sample step budget (LAP_OPT_STEP_LIMIT)");
+    }
+    if (h.status & LAP_DEV_K_OVERFLOW) {
+        g->sticky = LAP_ERR_STEP_LIMIT;
+        return fail(g, LAP_ERR_STEP_LIMIT, "a node was visited more than 2^30 times in one sample");
+    }
+    return LAP_OK;
+}
+
+lap_status ensure_workspace(lap_graph *g)
+{
+    const uint64_t per_slot = 8ull * (uint64_t)g->n;
+    if (!g->ws) {
+        size_t free_b = 0, total_b = 0;
+        LAP_CUDA(g, cudaMemGetInfo(&free_b, &total_b));
+        uint64_t want = (uint64_t)free_b / 2;
+        uint64_t cap = per_slot * (uint64_t)g->num_sms * 2048ull;
+        if (want > cap) want = cap;
+        want = (want / per_slot) * per_slot;
+        if (want < per_slot) return fail(g, LAP_ERR_OOM, "not enough device memory for one Wilson state");
+        cudaError_t e = cudaMalloc(&g->ws, want);
+        if (e != cudaSuccess) { cudaGetLastError(); g->ws = nullptr; return fail(g, LAP_ERR_OOM, "workspace allocation failed"); }
+        g->ws_bytes = want;
+        g->ws_owned = true;
+        g->ws_zeroed = false;
+    }
+    const uint64_t slots = g->ws_bytes / per_slot;
+    if (slots > g->slot_epoch_cap) {
+        cudaFree(g->d_slot_epoch);
+        g->d_slot_epoch = nullptr;
+        g->slot_epoch_cap = 0;
+        if (dalloc(&g->d_slot_epoch, slots) != cudaSuccess) { cudaGetLastError(); return fail(g, LAP_ERR_OOM, "slot table allocation failed"); }
+        g->slot_epoch_cap = slots;
+        g->ws_zeroed = false;
+    }
+    if (!g->ws_zeroed) {
+        LAP_CUDA(g, cudaMemsetAsync(g->ws, 0, g->ws_bytes, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_slot_epoch, 0, sizeof(unsigned int) * g->slot_epoch_cap, g->stream));
+        g->ws_zeroed = true;
+    }
+    return LAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t lap_version(void) { return 10000; }
+
+const char *lap_last_error(const lap_graph *g) { return g ? g->err.c_str() : g_create_error.c_str(); }
+
+lap_status lap_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int ptrs_on_device,
+                            lap_graph **out)
+{
+    if (!out) return fail(nullptr, LAP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 2) return fail(nullptr, LAP_ERR_INVALID_ARG, "n must be at least 2");
+    if (!row_ptr || !col_idx) return fail(nullptr, LAP_ERR_INVALID_ARG, "row_ptr or col_idx is NULL");
+    if (ptrs_on_device != 0 && ptrs_on_device != 1) return fail(nullptr, LAP_ERR_INVALID_ARG, "ptrs_on_device must be 0 or 1");
+
+    int32_t first = 0, last = 0;
+    if (ptrs_on_device) {
+        cudaError_t e = cudaMemcpy(&first, row_ptr, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(&last, row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "reading row_ptr ends");
+    } else {
+        first = row_ptr[0];
+        last = row_ptr[n];
+    }
+    if (first != 0 || last < 0) return fail(nullptr, LAP_ERR_BAD_CSR, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
+    if (last == 0) return fail(nullptr, LAP_ERR_DISCONNECTED, "graph has no edges");
+
+    lap_graph *g = new (std::nothrow) lap_graph();
+    if (!g) return fail(nullptr, LAP_ERR_OOM, "host allocation failed");
+    g->n = n;
+    g->arcs = last;
+    cudaGetDevice(&g->device);
+    cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (g->num_sms <= 0) g->num_sms = 1;
+
+    const size_t nn = (size_t)n;
+    bool ok = dalloc(&g->d_row_ptr, nn + 1) == cudaSuccess && dalloc(&g->d_col, (size_t)last) == cudaSuccess &&
+              dalloc(&g->d_rowinfo, nn) == cudaSuccess && dalloc(&g->d_hops, nn) == cudaSuccess &&
+              dalloc(&g->d_rep1, nn) == cudaSuccess && dalloc(&g->d_cnt2, nn) == cudaSuccess &&
+              dalloc(&g->d_acc, 1) == cudaSuccess && dalloc(&g->d_ldiag, nn) == cudaSuccess &&
+              dalloc(&g->d_ecc, nn) == cudaSuccess && dalloc(&g->d_red, 1024 + 8) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_all(g);
+        delete g;
+        return fail(nullptr, LAP_ERR_OOM, "device allocation failed");
+    }
+    cudaMemcpyKind kind = ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(g->d_row_ptr, row_ptr, sizeof(int32_t) * (nn + 1), kind, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_col, col_idx, sizeof(int32_t) * (size_t)last, kind, g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_acc, 0, sizeof(LapDevAcc), g->stream);
+    if (e == cudaSuccess) e = lap_launch_validate(g->d_row_ptr, g->d_col, n, last, &g->d_acc->status, g->stream);
+    LapDevAcc h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, g->d_acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        lap_status s = cuda_fail(nullptr, e, "graph ingest");
+        free_all(g);
+        delete g;
+        return s;
+    }
+    lap_status bad = LAP_OK;
+    if (h.status & LAP_DEV_BAD_CSR) bad = fail(nullptr, LAP_ERR_BAD_CSR, "CSR malformed: row_ptr not monotone, column out of range, or a row not strictly ascending");
+    else if (h.status & LAP_DEV_SELF_LOOP) bad = fail(nullptr, LAP_ERR_SELF_LOOP, "graph has a self-loop");
+    else if (h.status & LAP_DEV_NOT_SYMMETRIC) bad = fail(nullptr, LAP_ERR_NOT_SYMMETRIC, "CSR is not symmetric (graph must be undirected)");
+    if (bad != LAP_OK) {
+        free_all(g);
+        delete g;
+        return bad;
+    }
+    e = lap_launch_rowinfo(g->d_row_ptr, n, g->d_rowinfo, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        lap_status s = cuda_fail(nullptr, e, "row records");
+        free_all(g);
+        delete g;
+        return s;
+    }
+    g->err = "no error";
+    *out = g;
+    return LAP_OK;
+}
+
+lap_status lap_graph_destroy(lap_graph *g)
+{
+    if (!g) return LAP_OK;
+    cudaStreamSynchronize(g->stream);
+    free_all(g);
+    delete g;
+    return LAP_OK;
+}
+
+lap_status lap_set_stream(lap_graph *g, void *cuda_stream)
+{
+    if (!g) return fail(nullptr, LAP_ERR_INVALID_ARG, "NULL handle");
+    g->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    return LAP_OK;
+}
+
+lap_status lap_set_option(lap_graph *g, int32_t option, int64_t value)
+{
+    if (!g) return fail(nullptr, LAP_ERR_INVALID_ARG, "NULL handle");
+    if (value < 0) return fail(g, LAP_ERR_INVALID_ARG, "option value must be >= 0");
+    switch (option) {
+    case LAP_OPT_STEP_LIMIT:
+        g->step_limit = value > (int64_t)(1ull << 62) ? (1ull << 62) : (uint64_t)value;
+        return LAP_OK;
+    case LAP_OPT_SLOTS:
+        g->slots_opt = (uint64_t)value;
+        return LAP_OK;
+    case LAP_OPT_CURSOR:
+        if (g->omega != 0) return fail(g, LAP_ERR_INVALID_ARG, "the cursor can only be set before the first sample after lap_set_root");
+        if ((uint64_t)value >= (1ull << 32)) return fail(g, LAP_ERR_TOO_LARGE, "sample ids are limited to 2^32");
+        g->cursor = (uint64_t)value;
+        return LAP_OK;
+    case LAP_OPT_BLOCK:
+        if (value != 0 && (value % 32 != 0 || value > 256)) return fail(g, LAP_ERR_INVALID_ARG, "block must be 0 or a multiple of 32 up to 256");
+        g->block_opt = (int)value;
+        return LAP_OK;
+    default:
+        return fail(g, LAP_ERR_INVALID_ARG, "unknown option");
+    }
+}
+
+lap_status lap_workspace_query(const lap_graph *g, uint64_t slots, uint64_t *bytes)
+{
+    if (!g || !bytes) return fail(nullptr, LAP_ERR_INVALID_ARG, "NULL argument");
+    *bytes = 8ull * (uint64_t)g->n * slots;
+    return LAP_OK;
+}
+
+lap_status lap_set_workspace(lap_graph *g, void *device_ptr, uint64_t bytes)
+{
+    if (!g) return fail(nullptr, LAP_ERR_INVALID_ARG, "NULL handle");
+    if (!device_ptr || bytes < 8ull * (uint64_t)g->n) return fail(g, LAP_ERR_INVALID_ARG, "workspace must hold at least 8*n bytes");
+    if (reinterpret_cast<uintptr_t>(device_ptr) % 256 != 0) return fail(g, LAP_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    cudaStreamSynchronize(g->stream);
+    if (g->ws_owned) cudaFree(g->ws);
+    g->ws = device_ptr;
+    g->ws_bytes = (bytes / (8ull * (uint64_t)g->n)) * 8ull * (uint64_t)g->n;
+    g->ws_owned = false;
+    g->ws_zeroed = false;
+    return LAP_OK;
+}
+
+lap_status lap_set_root(lap_graph *g, int32_t v, int32_t *root_out)
+{
+    if (!g) return fail(nullptr, LAP_ERR_INVALID_ARG, "NULL handle");
+    if (v >= g->n) return fail(g, LAP_ERR_INVALID_ARG, "root out of range");
+    g->sticky = LAP_OK;
+    g->root = -1;
+    if (v < 0) {
+        unsigned long long *best = reinterpret_cast<unsigned long long *>(g->d_red);
+        LAP_CUDA(g, cudaMemsetAsync(best, 0, sizeof(unsigned long long), g->stream));
+        LAP_CUDA(g, lap_launch_argmax_degree(g->d_rowinfo, g->n, best, g->stream));
+        unsigned long long h = 0;
+        LAP_CUDA(g, cudaMemcpyAsync(&h, best, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+        LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+        v = (int32_t)(0xFFFFFFFFu - (uint32_t)(h & 0xFFFFFFFFull));
+    }
+    // Breadth-first search from v: connectivity check and hop distances.
+    unsigned int *found = reinterpret_cast<unsigned int *>(g->d_red);
+    LAP_CUDA(g, lap_launch_bfs_init(g->d_hops, g->n, v, g->stream));
+    int64_t reached = 1;
+    for (int32_t level = 0;; ++level) {
+        LAP_CUDA(g, cudaMemsetAsync(found, 0, sizeof(unsigned int), g->stream));
+        LAP_CUDA(g, lap_launch_bfs_level(g->d_rowinfo, g->d_col, g->d_hops, g->n, level, found, g->stream));
+        unsigned int h = 0;
+        LAP_CUDA(g, cudaMemcpyAsync(&h, found, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+        LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+        if (h == 0) break;
+        reached += h;
+    }
+    if (reached != g->n) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "root %d reaches %lld of %d nodes: graph is not connected", v, (long long)reached, g->n);
+        return fail(g, LAP_ERR_DISCONNECTED, buf);
+    }
+    LAP_CUDA(g, cudaMemsetAsync(g->d_rep1, 0, sizeof(unsigned long long) * (size_t)g->n, g->stream));
+    LAP_CUDA(g, cudaMemsetAsync(g->d_cnt2, 0, sizeof(unsigned long long) * (size_t)g->n, g->stream));
+    LAP_CUDA(g, cudaMemsetAsync(g->d_acc, 0, sizeof(LapDevAcc), g->stream));
+    g->ws_zeroed = false;                 // a failed earlier run may have left partial state
+    g->root = v;
+    g->seed_set = false;
+    g->omega = 0;
+    g->cursor = 0;
+    g->results_valid = false;
+    g->err = "no error";
+    if (root_out) *root_out = v;
+    return LAP_OK;
+}
+
+lap_status lap_sample(lap_graph *g, uint64_t n_samples, uint64_t seed)
+{
+    return lap_sample_trace(g, n_samples, seed, nullptr, nullptr);
+}
+
+lap_status lap_sample_trace(lap_graph *g, uint64_t n_samples, uint64_t seed, uint64_t *y1_dev, uint64_t *y2_dev)
+{
+    if ((y1_dev == nullptr) != (y2_dev == nullptr)) return fail(g, LAP_ERR_INVALID_ARG, "y1_dev and y2_dev must both be set or both be NULL");
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (g->seed_set && seed != g->seed) return fail(g, LAP_ERR_INVALID_ARG, "seed differs from the seed in use since lap_set_root");
+    if (g->cursor + n_samples > (1ull << 32)) return fail(g, LAP_ERR_TOO_LARGE, "sample ids are limited to 2^32");
+    if (n_samples == 0) return LAP_OK;
+    if ((s = ensure_workspace(g)) != LAP_OK) return s;
+    g->seed = seed;
+    g->seed_set = true;
+
+    const uint64_t per_slot = 8ull * (uint64_t)g->n;
+    uint64_t slots = g->ws_bytes / per_slot;
+    if (g->slots_opt && g->slots_opt < slots) slots = g->slots_opt;
+    if (slots > n_samples) slots = n_samples;
+
+    LapSampleLaunch p;
+    p.g = LapDevGraph{g->d_rowinfo, g->d_col, g->n, g->arcs};
+    p.root = g->root;
+    p.seed = seed;
+    p.first = (uint32_t)g->cursor;
+    p.count = (uint32_t)n_samples;
+    p.slots = slots;
+    p.ws = g->ws;
+    p.slot_epoch = g->d_slot_epoch;
+    p.rep1 = g->d_rep1;
+    p.cnt2 = g->d_cnt2;
+    p.acc = g->d_acc;
+    p.step_limit = g->step_limit ? g->step_limit : default_step_limit(g->n);
+    p.block = g->block_opt;
+    p.y1_out = reinterpret_cast<unsigned long long *>(y1_dev);
+    p.y2_out = reinterpret_cast<unsigned long long *>(y2_dev);
+    LAP_CUDA(g, cudaMemsetAsync(&g->d_acc->claim, 0, sizeof(unsigned int), g->stream));
+    LAP_CUDA(g, lap_launch_sample(p, g->stream));
+    g->omega += n_samples;
+    g->cursor += n_samples;
+    g->results_valid = false;
+    return LAP_OK;
+}
+
+lap_status lap_sync(lap_graph *g)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    return poll_status(g);
+}
+
+static lap_status ensure_results(lap_graph *g)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (g->omega == 0) return fail(g, LAP_ERR_NO_SAMPLES, "no samples drawn");
+    if ((s = poll_status(g)) != LAP_OK) return s;
+    if (!g->results_valid) {
+        LAP_CUDA(g, lap_launch_finalize(g->d_rowinfo, g->n, g->root, g->omega, g->d_rep1, g->d_cnt2,
+                                        g->d_ldiag, g->d_ecc, g->d_red, g->stream));
+        g->results_valid = true;
+    }
+    return LAP_OK;
+}
+
+static lap_status copy_out(lap_graph *g, void *out, const void *src, size_t bytes, int on_device)
+{
+    if (!out) return fail(g, LAP_ERR_INVALID_ARG, "output pointer is NULL");
+    LAP_CUDA(g, cudaMemcpyAsync(out, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    return LAP_OK;
+}
+
+lap_status lap_ecc(lap_graph *g, double *out, int out_on_device)
+{
+    lap_status s = ensure_results(g);
+    if (s != LAP_OK) return s;
+    return copy_out(g, out, g->d_ecc, sizeof(double) * (size_t)g->n, out_on_device);
+}
+
+lap_status lap_ldiag(lap_graph *g, double *out, int out_on_device)
+{
+    lap_status s = ensure_results(g);
+    if (s != LAP_OK) return s;
+    return copy_out(g, out, g->d_ldiag, sizeof(double) * (size_t)g->n, out_on_device);
+}
+
+lap_status lap_kemeny(lap_graph *g, double *out1)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (!out1) return fail(g, LAP_ERR_INVALID_ARG, "output pointer is NULL");
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (g->omega == 0) return fail(g, LAP_ERR_NO_SAMPLES, "no samples drawn");
+    if ((s = poll_status(g)) != LAP_OK) return s;
+    LapDevAcc h;
+    LAP_CUDA(g, cudaMemcpyAsync(&h, g->d_acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    // Alg. 4: kappa = (sum Y1 - sum Y2) / omega.
+    *out1 = ((double)h.sum_y1 - (double)h.sum_y2) / (double)g->omega;
+    return LAP_OK;
+}
+
+lap_status lap_counts(lap_graph *g, uint64_t *cnt1, uint64_t *cnt2, uint64_t *sums, int on_device)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if ((s = poll_status(g)) != LAP_OK) return s;
+    const size_t bytes = sizeof(uint64_t) * (size_t)g->n;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (cnt1) {
+        // cnt1 = omega (the first visit of every non-root node) + repeats.
+        LAP_CUDA(g, lap_launch_counts(g->n, g->root, g->omega, g->d_rep1,
+                                      reinterpret_cast<unsigned long long *>(g->d_ldiag), g->stream));
+        LAP_CUDA(g, cudaMemcpyAsync(cnt1, g->d_ldiag, bytes, kind, g->stream));
+        g->results_valid = false;        // d_ldiag was used as scratch
+    }
+    if (cnt2) LAP_CUDA(g, cudaMemcpyAsync(cnt2, g->d_cnt2, bytes, kind, g->stream));
+    if (sums) {
+        LapDevAcc h;
+        LAP_CUDA(g, cudaMemcpyAsync(&h, g->d_acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+        LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+        uint64_t v4[4] = {g->omega, h.sum_y1, h.sum_y2, g->seed};
+        if (on_device) LAP_CUDA(g, cudaMemcpyAsync(sums, v4, sizeof(v4), cudaMemcpyHostToDevice, g->stream));
+        else memcpy(sums, v4, sizeof(v4));
+    }
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    return LAP_OK;
+}
+
+lap_status lap_hops(lap_graph *g, int32_t *out, int on_device)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    return copy_out(g, out, g->d_hops, sizeof(int32_t) * (size_t)g->n, on_device);
+}
+
+lap_status lap_graph_info(const lap_graph *g, int32_t *n, int64_t *arcs, int32_t *root)
+{
+    if (!g) return fail(nullptr, LAP_ERR_INVALID_ARG, "NULL handle");
+    if (n) *n = g->n;
+    if (arcs) *arcs = g->arcs;
+    if (root) *root = g->root;
+    return LAP_OK;
+}
+
+}  // extern "C"

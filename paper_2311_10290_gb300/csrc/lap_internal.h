@@ -1,0 +1,113 @@
+// Internal declarations of the GB300 library behind include/lap.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "lap.h"
+
+// Device-side view of a graph: per-node row records {offset, degree} (one
+// aligned 8-byte load per visit) and the column array.
+struct LapDevGraph {
+    const int2 *rowinfo;   // [n] {row_ptr[u], d_u}
+    const int32_t *col;    // [arcs]
+    int32_t n;
+    int64_t arcs;
+};
+
+// Status bits written by kernels into the handle's status word.
+enum : unsigned int {
+    LAP_DEV_BAD_CSR = 1u,
+    LAP_DEV_SELF_LOOP = 2u,
+    LAP_DEV_NOT_SYMMETRIC = 4u,
+    LAP_DEV_STEP_LIMIT = 8u,
+    LAP_DEV_K_OVERFLOW = 16u,
+};
+
+// Accumulators of a handle on the device (one cache line).
+struct LapDevAcc {
+    unsigned long long sum_y1;     // sum over samples of Y1 (Wilson steps incl. loops)
+    unsigned long long sum_y2;     // sum over samples of Y2 (pi-start walk length)
+    unsigned int status;           // LAP_DEV_* bits
+    unsigned int claim;            // next sample offset to claim inside a launch
+    unsigned long long pad[5];
+};
+
+struct lap_graph {
+    int device = 0;
+    int num_sms = 0;
+    int32_t n = 0;
+    int64_t arcs = 0;
+
+    int32_t *d_row_ptr = nullptr;
+    int32_t *d_col = nullptr;
+    int2 *d_rowinfo = nullptr;
+    int32_t *d_hops = nullptr;
+    unsigned long long *d_rep1 = nullptr;   // repeat visits per node (visits - 1, summed)
+    unsigned long long *d_cnt2 = nullptr;   // uniform-start walk passes per node
+    LapDevAcc *d_acc = nullptr;
+    double *d_ldiag = nullptr;
+    double *d_ecc = nullptr;
+    double *d_red = nullptr;                // reduction scratch
+    unsigned int *d_slot_epoch = nullptr;   // per-slot epoch parity of the Wilson state
+    uint64_t slot_epoch_cap = 0;
+
+    cudaStream_t stream = nullptr;
+    int32_t root = -1;
+    uint64_t seed = 0;
+    bool seed_set = false;
+    uint64_t omega = 0;                     // samples drawn since lap_set_root
+    uint64_t cursor = 0;                    // next sample id
+    bool results_valid = false;
+
+    void *ws = nullptr;                     // Wilson state workspace
+    uint64_t ws_bytes = 0;
+    bool ws_owned = false;
+    bool ws_zeroed = false;
+
+    uint64_t step_limit = 0;                // 0: default
+    uint64_t slots_opt = 0;
+    int block_opt = 0;
+
+    lap_status sticky = LAP_OK;
+    std::string err;
+};
+
+// ---------------------------------------------------------------- kernels
+// ingest.cu
+cudaError_t lap_launch_validate(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t arcs,
+                                unsigned int *status, cudaStream_t st);
+cudaError_t lap_launch_rowinfo(const int32_t *row_ptr, int32_t n, int2 *rowinfo, cudaStream_t st);
+cudaError_t lap_launch_argmax_degree(const int2 *rowinfo, int32_t n, unsigned long long *best, cudaStream_t st);
+cudaError_t lap_launch_bfs_init(int32_t *hops, int32_t n, int32_t root, cudaStream_t st);
+cudaError_t lap_launch_bfs_level(const int2 *rowinfo, const int32_t *col, int32_t *hops, int32_t n,
+                                 int32_t level, unsigned int *found, cudaStream_t st);
+
+// sampler.cu
+struct LapSampleLaunch {
+    LapDevGraph g;
+    int32_t root;
+    uint64_t seed;
+    uint32_t first;          // first sample id of this launch
+    uint32_t count;          // samples in this launch
+    uint64_t slots;          // lanes with their own Wilson state
+    void *ws;                // slots * n * 8 bytes
+    unsigned int *slot_epoch;
+    unsigned long long *rep1;
+    unsigned long long *cnt2;
+    LapDevAcc *acc;
+    uint64_t step_limit;
+    int block;
+    unsigned long long *y1_out;  // optional [count]: Y1 of sample first+q at q
+    unsigned long long *y2_out;  // optional [count]: Y2 of sample first+q at q
+};
+cudaError_t lap_launch_sample(const LapSampleLaunch &p, cudaStream_t st);
+
+// finalize.cu
+cudaError_t lap_launch_finalize(const int2 *rowinfo, int32_t n, int32_t root, uint64_t omega,
+                                const unsigned long long *rep1, const unsigned long long *cnt2,
+                                double *ldiag, double *ecc, double *red, cudaStream_t st);
+cudaError_t lap_launch_counts(int32_t n, int32_t root, uint64_t omega, const unsigned long long *rep1,
+                              unsigned long long *cnt1, cudaStream_t st);

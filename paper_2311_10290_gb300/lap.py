@@ -1,0 +1,280 @@
+"""Thin Python binding of the C ABI in include/lap.h (argument marshalling only).
+
+Every step of the sampling path runs in the CUDA library ``liblap.so``; this
+module only converts arguments, lends torch-allocated device memory (the
+Wilson-state workspace) and the current torch stream to the library, and
+turns status codes into exceptions.  Importing it fails loudly when the
+library has not been built: there is no CPU fallback.
+
+Functions keep the C names (``lap_graph_create``, ``lap_set_root``,
+``lap_sample``, ``lap_ecc``, ``lap_kemeny`` ...); :class:`LapGraph` bundles
+them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblap.so")
+
+STATUS = {
+    0: "LAP_OK", 1: "LAP_ERR_INVALID_ARG", 2: "LAP_ERR_BAD_CSR", 3: "LAP_ERR_NOT_SYMMETRIC",
+    4: "LAP_ERR_SELF_LOOP", 5: "LAP_ERR_DISCONNECTED", 6: "LAP_ERR_TOO_LARGE", 7: "LAP_ERR_OOM",
+    8: "LAP_ERR_NO_SAMPLES", 9: "LAP_ERR_STEP_LIMIT", 10: "LAP_ERR_CUDA", 11: "LAP_ERR_NO_ROOT",
+}
+LAP_OPT_STEP_LIMIT, LAP_OPT_SLOTS, LAP_OPT_BLOCK, LAP_OPT_CURSOR = 1, 2, 3, 4
+
+
+class LapError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+_lib = None
+
+
+def library():
+    """The loaded liblap.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("liblap.so is not built (run __graft_entry__.build() or "
+                          "python paper_2311_10290_gb300/build.py); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "lap_version": (i32, []),
+        "lap_graph_create": (i32, [i32, vp, vp, ctypes.c_int, ctypes.POINTER(vp)]),
+        "lap_graph_destroy": (i32, [vp]),
+        "lap_set_stream": (i32, [vp, vp]),
+        "lap_set_option": (i32, [vp, i32, i64]),
+        "lap_workspace_query": (i32, [vp, u64, ctypes.POINTER(u64)]),
+        "lap_set_workspace": (i32, [vp, vp, u64]),
+        "lap_set_root": (i32, [vp, i32, ctypes.POINTER(i32)]),
+        "lap_sample": (i32, [vp, u64, u64]),
+        "lap_sample_trace": (i32, [vp, u64, u64, vp, vp]),
+        "lap_sync": (i32, [vp]),
+        "lap_ecc": (i32, [vp, vp, ctypes.c_int]),
+        "lap_ldiag": (i32, [vp, vp, ctypes.c_int]),
+        "lap_kemeny": (i32, [vp, vp]),
+        "lap_counts": (i32, [vp, vp, vp, vp, ctypes.c_int]),
+        "lap_hops": (i32, [vp, vp, ctypes.c_int]),
+        "lap_graph_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]),
+        "lap_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = library().lap_last_error(handle)
+        raise LapError(status, msg.decode() if msg else "")
+
+
+def _host_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+# ------------------------------------------------------------ C-named calls
+
+def lap_version():
+    return library().lap_version()
+
+
+def lap_last_error(h=None):
+    m = library().lap_last_error(h)
+    return m.decode() if m else ""
+
+
+def lap_graph_create(n, row_ptr, col_idx):
+    """row_ptr/col_idx: int32 numpy arrays (host) or int32 CUDA torch tensors."""
+    if _is_torch(row_ptr):
+        assert row_ptr.is_cuda and col_idx.is_cuda and row_ptr.dtype == col_idx.dtype
+        ptrs = (ctypes.c_void_p(row_ptr.data_ptr()), ctypes.c_void_p(col_idx.data_ptr()), 1)
+    else:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        cl = np.ascontiguousarray(col_idx, dtype=np.int32)
+        ptrs = (_host_ptr(rp), _host_ptr(cl), 0)
+    h = ctypes.c_void_p()
+    _check(library().lap_graph_create(int(n), ptrs[0], ptrs[1], ptrs[2], ctypes.byref(h)))
+    return h
+
+
+def lap_graph_destroy(h):
+    _check(library().lap_graph_destroy(h))
+
+
+def lap_set_stream(h, stream_ptr):
+    _check(library().lap_set_stream(h, ctypes.c_void_p(stream_ptr)), h)
+
+
+def lap_set_option(h, option, value):
+    _check(library().lap_set_option(h, int(option), int(value)), h)
+
+
+def lap_workspace_query(h, slots):
+    b = ctypes.c_uint64()
+    _check(library().lap_workspace_query(h, int(slots), ctypes.byref(b)), h)
+    return b.value
+
+
+def lap_set_workspace(h, dev_ptr, nbytes):
+    _check(library().lap_set_workspace(h, ctypes.c_void_p(dev_ptr), int(nbytes)), h)
+
+
+def lap_set_root(h, v=-1):
+    r = ctypes.c_int32()
+    _check(library().lap_set_root(h, int(v), ctypes.byref(r)), h)
+    return r.value
+
+
+def lap_sample(h, n_samples, seed):
+    _check(library().lap_sample(h, int(n_samples), int(seed)), h)
+
+
+def lap_sample_trace(h, n_samples, seed, y1_dev, y2_dev):
+    """y1_dev, y2_dev: uint64 (int64) CUDA torch tensors of n_samples entries."""
+    _check(library().lap_sample_trace(h, int(n_samples), int(seed), ctypes.c_void_p(y1_dev.data_ptr()),
+                                      ctypes.c_void_p(y2_dev.data_ptr())), h)
+
+
+def lap_sync(h):
+    _check(library().lap_sync(h), h)
+
+
+def _out(h, fn, n, dtype, out):
+    if out is None:
+        out = np.empty(n, dtype=dtype)
+    if _is_torch(out):
+        _check(fn(h, ctypes.c_void_p(out.data_ptr()), 1), h)
+    else:
+        _check(fn(h, _host_ptr(out), 0), h)
+    return out
+
+
+def lap_ecc(h, n, out=None):
+    return _out(h, library().lap_ecc, n, np.float64, out)
+
+
+def lap_ldiag(h, n, out=None):
+    return _out(h, library().lap_ldiag, n, np.float64, out)
+
+
+def lap_hops(h, n, out=None):
+    return _out(h, library().lap_hops, n, np.int32, out)
+
+
+def lap_kemeny(h):
+    x = np.zeros(1, dtype=np.float64)
+    _check(library().lap_kemeny(h, _host_ptr(x)), h)
+    return float(x[0])
+
+
+def lap_counts(h, n, per_node=True):
+    """(cnt1, cnt2, sums) as host uint64 arrays; per_node=False reads only sums."""
+    c1 = np.zeros(n, dtype=np.uint64) if per_node else None
+    c2 = np.zeros(n, dtype=np.uint64) if per_node else None
+    s = np.zeros(4, dtype=np.uint64)
+    _check(library().lap_counts(h, None if c1 is None else _host_ptr(c1), None if c2 is None else _host_ptr(c2),
+                                _host_ptr(s), 0), h)
+    return c1, c2, s
+
+
+def lap_graph_info(h):
+    n, a, r = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+    _check(library().lap_graph_info(h, ctypes.byref(n), ctypes.byref(a), ctypes.byref(r)), h)
+    return n.value, a.value, r.value
+
+
+# ------------------------------------------------------------ convenience
+
+class LapGraph:
+    """A graph handle with a torch-allocated Wilson-state workspace.
+
+    row_ptr/col: numpy int32 (host, copied in) or CUDA int32 torch tensors.
+    workspace_bytes: bytes of device memory lent to the sampler (default: 60%
+    of the free device memory, capped at what 152 SMs x 2048 lanes can use).
+    """
+
+    def __init__(self, row_ptr, col, workspace_bytes=None, stream=None):
+        import torch
+        self.n = int(len(row_ptr) - 1)
+        self.h = lap_graph_create(self.n, row_ptr, col)
+        self._torch = torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        lap_set_stream(self.h, s.cuda_stream)
+        per_slot = 8 * self.n
+        if workspace_bytes is None:
+            free, _ = torch.cuda.mem_get_info()
+            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            workspace_bytes = min(int(free * 0.6), per_slot * sms * 2048)
+        workspace_bytes = max(per_slot, (int(workspace_bytes) // per_slot) * per_slot)
+        self.workspace = torch.empty(workspace_bytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        lap_set_workspace(self.h, aligned, workspace_bytes)
+        self.slots = workspace_bytes // per_slot
+        self.root = None
+
+    def close(self):
+        if self.h is not None:
+            lap_graph_destroy(self.h)
+            self.h = None
+            self.workspace = None
+            self._torch.cuda.empty_cache()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, option, value):
+        lap_set_option(self.h, option, value)
+
+    def set_root(self, v=-1):
+        self.root = lap_set_root(self.h, v)
+        return self.root
+
+    def sample(self, n_samples, seed):
+        lap_sample(self.h, n_samples, seed)
+
+    def sample_trace(self, n_samples, seed):
+        """Returns per-sample (Y1, Y2) as int64 CUDA tensors (asynchronous)."""
+        y1 = self._torch.zeros(n_samples, dtype=self._torch.int64, device="cuda")
+        y2 = self._torch.zeros(n_samples, dtype=self._torch.int64, device="cuda")
+        lap_sample_trace(self.h, n_samples, seed, y1, y2)
+        return y1, y2
+
+    def sync(self):
+        lap_sync(self.h)
+
+    def ecc(self, out=None):
+        return lap_ecc(self.h, self.n, out)
+
+    def ldiag(self, out=None):
+        return lap_ldiag(self.h, self.n, out)
+
+    def kemeny(self):
+        return lap_kemeny(self.h)
+
+    def counts(self, per_node=True):
+        return lap_counts(self.h, self.n, per_node)
+
+    def hops(self, out=None):
+        return lap_hops(self.h, self.n, out)

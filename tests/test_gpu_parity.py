@@ -1,0 +1,271 @@
+"""Parity of the CUDA path (called through the C ABI) with the CPU oracle.
+
+Integer outputs (per-node visit and pass counts, sum Y1, sum Y2, per-sample
+Y1/Y2) must be bit-exact; FP64 outputs ((L^+)_uu, ECC, Kemeny) must agree with
+the oracle's finalize of the same counts to 1e-12 relative: both sides do the
+same IEEE operations per node and differ only in the order of two n-term sums
+of positive numbers (a few ulp)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_10290_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from paper_2311_10290_gb300.lap import (LAP_OPT_BLOCK, LAP_OPT_SLOTS, LAP_OPT_STEP_LIMIT,  # noqa: E402
+                                        LapError, LapGraph)
+
+RTOL = 1e-12
+
+
+def gpu_run(g, seed, omega, root=-1, slots=None, block=None, splits=None, ws=None, device_inputs=False):
+    if device_inputs:
+        G = LapGraph(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda(), workspace_bytes=ws)
+    else:
+        G = LapGraph(g.row_ptr, g.col, workspace_bytes=ws)
+    try:
+        if slots:
+            G.set_option(LAP_OPT_SLOTS, slots)
+        if block:
+            G.set_option(LAP_OPT_BLOCK, block)
+        v = G.set_root(root)
+        for part in (splits or [omega]):
+            G.sample(part, seed)
+        c1, c2, s = G.counts()
+        return dict(v=v, cnt1=c1, cnt2=c2, sums=s, ld=G.ldiag(), ecc=G.ecc(), kc=G.kemeny())
+    finally:
+        G.close()
+
+
+def oracle_run(g, v, seed, omega, threads=1):
+    if threads > 1:
+        return oracle.sample_threads(g.row_ptr, g.col, v, seed, 0, omega, threads)
+    return oracle.sample(g.row_ptr, g.col, v, seed, 0, omega, keep_per_sample=False)
+
+
+def assert_parity(g, r, c, omega):
+    assert np.array_equal(r["cnt1"], c.cnt1), np.nonzero(r["cnt1"] != c.cnt1)[0][:10]
+    assert np.array_equal(r["cnt2"], c.cnt2), np.nonzero(r["cnt2"] != c.cnt2)[0][:10]
+    assert int(r["sums"][0]) == omega
+    assert int(r["sums"][1]) == c.sum_y1
+    assert int(r["sums"][2]) == c.sum_y2
+    ld, ec, kc = oracle.finalize(g.row_ptr, r["v"], omega, c.cnt1, c.cnt2, c.sum_y1, c.sum_y2)
+    np.testing.assert_allclose(r["ld"], ld, rtol=RTOL, atol=0)
+    np.testing.assert_allclose(r["ecc"], ec, rtol=RTOL, atol=0)
+    assert r["kc"] == pytest.approx(kc, rel=RTOL)
+
+
+CASES = [
+    ("k4e_v0", I.k4_minus_edge, 0, 5000),
+    ("k4e_auto", I.k4_minus_edge, -1, 777),
+    ("star50", lambda: I.star(50), -1, 3001),
+    ("path30_end", lambda: I.path(30), 0, 200),
+    ("cycle101", lambda: I.cycle(101), 50, 150),
+    ("er1000", I.er_1000, -1, 2000),
+    ("er300_sparse", lambda: I.er(300, 0.012, seed=4), -1, 999),
+    ("ba20000", lambda: I.ba(20000, 3, seed=2), -1, 300),
+    ("rmat12", lambda: I.rmat(12, 8, seed=3), -1, 257),
+    ("k2", lambda: I.complete(2), 0, 100),
+]
+
+
+@pytest.mark.parametrize("name,maker,root,omega", CASES, ids=[c[0] for c in CASES])
+def test_counts_and_estimates_match_oracle(name, maker, root, omega):
+    g = maker()
+    seed = 0x5EED0000 + len(name)
+    r = gpu_run(g, seed, omega, root=root)
+    v = r["v"] if root < 0 else root
+    if root < 0:
+        assert v == oracle.root_max_degree(g.row_ptr)
+    c = oracle_run(g, v, seed, omega, threads=4)
+    assert_parity(g, r, c, omega)
+
+
+def test_split_calls_equal_one_call():
+    g = I.er(500, 0.02, seed=9)
+    a = gpu_run(g, 11, 200)
+    b = gpu_run(g, 11, 200, splits=[37, 1, 100, 62])
+    for k in ("cnt1", "cnt2", "sums"):
+        assert np.array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("slots,block", [(1, 32), (7, 64), (64, 128), (1000, 256), (None, None)])
+def test_launch_shape_does_not_change_counts(slots, block):
+    g = I.ba(3000, 2, seed=5)
+    ref = gpu_run(g, 3, 500)
+    r = gpu_run(g, 3, 500, slots=slots, block=block)
+    for k in ("cnt1", "cnt2", "sums"):
+        assert np.array_equal(ref[k], r[k])
+
+
+def test_small_workspace_reuses_slots_across_launches():
+    """Two slots, many samples and several calls: the epoch bit must keep
+    every sample independent of the previous contents of its slot."""
+    g = I.er(400, 0.03, seed=1)
+    v = oracle.root_max_degree(g.row_ptr)
+    r = gpu_run(g, 8, 90, ws=2 * 8 * g.n, splits=[1, 2, 3, 40, 44])
+    c = oracle_run(g, v, 8, 90)
+    assert_parity(g, r, c, 90)
+
+
+def test_device_resident_csr():
+    g = I.rmat(10, 6, seed=8)
+    a = gpu_run(g, 21, 100)
+    b = gpu_run(g, 21, 100, device_inputs=True)
+    for k in ("cnt1", "cnt2", "sums"):
+        assert np.array_equal(a[k], b[k])
+
+
+def test_per_sample_trace_matches_oracle():
+    g = I.ba(5000, 4, seed=3)
+    G = LapGraph(g.row_ptr, g.col)
+    try:
+        v = G.set_root()
+        G.sample(17, 99)                      # ids 0..16
+        y1, y2 = G.sample_trace(40, 99)       # ids 17..56
+        torch.cuda.synchronize()
+        c = oracle.sample(g.row_ptr, g.col, v, 99, 17, 40)
+        assert np.array_equal(y1.cpu().numpy().astype(np.uint64), c.y1)
+        assert np.array_equal(y2.cpu().numpy().astype(np.uint64), c.y2)
+    finally:
+        G.close()
+
+
+def test_hops_are_bfs_distances():
+    g = I.er(600, 0.01, seed=2)
+    G = LapGraph(g.row_ptr, g.col)
+    try:
+        v = G.set_root()
+        h = G.hops()
+    finally:
+        G.close()
+    ref = np.full(g.n, -1)
+    ref[v] = 0
+    frontier = [v]
+    while frontier:
+        nxt = []
+        for u in frontier:
+            for w in g.col[g.row_ptr[u]:g.row_ptr[u + 1]]:
+                if ref[w] < 0:
+                    ref[w] = ref[u] + 1
+                    nxt.append(w)
+        frontier = nxt
+    assert np.array_equal(h, ref)
+
+
+# ------------------------------------------------------------- error paths
+
+def _expect(status, fn):
+    with pytest.raises(LapError) as e:
+        fn()
+    assert e.value.name == status, str(e.value)
+
+
+def test_rejects_bad_graphs():
+    two = I.from_edges(4, [(0, 1), (2, 3)])                   # two components
+    _expect("LAP_ERR_DISCONNECTED", lambda: LapGraph(two.row_ptr, two.col).set_root(0))
+    rp = np.array([0, 1, 1], dtype=np.int32)                  # arc 0->1 without 1->0
+    _expect("LAP_ERR_NOT_SYMMETRIC", lambda: LapGraph(rp, np.array([1], dtype=np.int32)))
+    rp = np.array([0, 2, 3], dtype=np.int32)                  # self-loop at 0
+    _expect("LAP_ERR_SELF_LOOP", lambda: LapGraph(rp, np.array([0, 1, 0], dtype=np.int32)))
+    k = I.complete(4)
+    col = k.col.copy()
+    col[[0, 1]] = col[[1, 0]]                                 # unsorted row 0
+    _expect("LAP_ERR_BAD_CSR", lambda: LapGraph(k.row_ptr, col))
+    col = k.col.copy()
+    col[0] = 7                                                # out of range
+    _expect("LAP_ERR_BAD_CSR", lambda: LapGraph(k.row_ptr, col))
+    _expect("LAP_ERR_INVALID_ARG", lambda: LapGraph(np.array([0, 0], dtype=np.int32), np.array([], dtype=np.int32)))
+
+
+def test_seed_change_and_no_samples_are_rejected():
+    g = I.cycle(10)
+    G = LapGraph(g.row_ptr, g.col)
+    try:
+        _expect("LAP_ERR_NO_ROOT", lambda: G.sample(1, 1))
+        G.set_root(0)
+        _expect("LAP_ERR_NO_SAMPLES", lambda: G.kemeny())
+        G.sample(3, 5)
+        _expect("LAP_ERR_INVALID_ARG", lambda: G.sample(3, 6))
+        G.sample(3, 5)
+        assert G.counts()[2][0] == 6
+    finally:
+        G.close()
+
+
+def test_step_budget_is_reported_and_cleared():
+    """A path rooted at an end needs about n^2 steps per sample; a budget of
+    100 steps must stop the kernel with LAP_ERR_STEP_LIMIT (no hang, no
+    fault), and lap_set_root must clear the error."""
+    g = I.path(400)
+    G = LapGraph(g.row_ptr, g.col, workspace_bytes=64 * 8 * g.n)
+    try:
+        G.set_option(LAP_OPT_STEP_LIMIT, 100)
+        G.set_root(0)
+        G.sample(20, 1)
+        _expect("LAP_ERR_STEP_LIMIT", lambda: G.sync())
+        _expect("LAP_ERR_STEP_LIMIT", lambda: G.kemeny())       # sticky
+        G.set_option(LAP_OPT_STEP_LIMIT, 0)
+        G.set_root(0)
+        G.sample(4, 1)
+        c1, _, s = G.counts()
+        c = oracle.sample(g.row_ptr, g.col, 0, 1, 0, 4)
+        assert np.array_equal(c1, c.cnt1) and int(s[1]) == c.sum_y1
+    finally:
+        G.close()
+
+
+# ------------------------------------------------------------- full size
+
+@pytest.fixture(scope="module")
+def ba_1m():
+    return I.ba_1m()
+
+
+def test_full_size_ba_counts_small_omega(ba_1m):
+    """The 10^6-node Barabasi-Albert workload graph: all counts bit-exact for 48 samples."""
+    g = ba_1m
+    r = gpu_run(g, 7, 48)
+    c = oracle_run(g, r["v"], 7, 48, threads=8)
+    assert_parity(g, r, c, 48)
+
+
+def test_full_size_ba_bench_launch_sampled(ba_1m):
+    """The benchmark's launch (default workspace, all slots busy, several
+    samples per slot): per-sample Y1/Y2 of sampled ids against the oracle one
+    by one, plus invariants that hold at any size (sum of visits = sum of Y1,
+    every non-root node visited at least once per sample)."""
+    g = ba_1m
+    G = LapGraph(g.row_ptr, g.col)
+    try:
+        v = G.set_root()
+        omega = int(min(2 * G.slots + 37, 40000))
+        y1, y2 = G.sample_trace(omega, 2024)
+        c1, c2, s = G.counts()
+        y1 = y1.cpu().numpy().astype(np.uint64)
+        y2 = y2.cpu().numpy().astype(np.uint64)
+    finally:
+        G.close()
+    assert int(s[0]) == omega and int(s[1]) == int(y1.sum()) and int(s[2]) == int(y2.sum())
+    assert int(c1.sum()) == int(s[1])
+    mask = np.ones(g.n, bool)
+    mask[v] = False
+    assert c1[v] == 0 and np.all(c1[mask] >= omega)
+    ids = np.unique(np.linspace(0, omega - 1, 12).astype(np.int64))
+    for i in ids:
+        c = oracle.sample(g.row_ptr, g.col, v, 2024, int(i), 1)
+        assert c.y1[0] == y1[i] and c.y2[0] == y2[i], i
+
+
+def test_small_workload_accuracy():
+    """Erdos-Renyi G(1000, 0.01): estimates from 10^4 samples against the dense
+    FP64 pseudo-inverse (loose bound; the time-to-1e-2 search is in bench.py)."""
+    import oracle.dense as D
+    g = I.er_1000()
+    r = gpu_run(g, 1, 10000)
+    ec = D.ecc(g.n, g.row_ptr, g.col)
+    kc = D.kemeny(g.n, g.row_ptr, g.col)
+    assert np.max(np.abs(r["ecc"] - ec) / ec) < 0.06
+    assert abs(r["kc"] - kc) / kc < 0.02
