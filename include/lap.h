@@ -72,10 +72,25 @@ typedef enum {
                                   (2^20 + 1024 n); the value is clamped to [1, 2^62] */
     LAP_OPT_SLOTS = 2,         /* samples kept in flight per launch; 0 = as many as the workspace holds */
     LAP_OPT_BLOCK = 3,         /* threads per block of the sampler launch; 0 = automatic */
-    LAP_OPT_CURSOR = 4         /* first sample id of the next lap_sample (default 0); only before the
+    LAP_OPT_CURSOR = 4,        /* first sample id of the next lap_sample (default 0); only before the
                                   first sample after lap_set_root.  Lets several processes or GPUs
                                   draw disjoint sample-id ranges whose counts add up exactly. */
+    LAP_OPT_KERNEL = 5,        /* 0 = automatic, 1 = 8-byte state per node, 2 = 1-byte state per node
+                                  (default when n < 2^27).  A sample that does not fit kernel 2 (a
+                                  node drawn more than 31 times, or a loop-erased path longer than
+                                  the stack) is withdrawn and re-run with kernel 1: results are
+                                  identical either way. */
+    LAP_OPT_STACK = 6          /* loop-erased path capacity per sample of kernel 2; 0 = default
+                                  (16 sqrt(n) rounded up to a power of two, at least 1024) */
 } lap_option;
+
+/* Statistics for lap_get_stat. */
+typedef enum {
+    LAP_STAT_SLOTS = 1,        /* samples in flight per launch with the current workspace and kernel */
+    LAP_STAT_KERNEL = 2,       /* kernel the next lap_sample will use (1 or 2) */
+    LAP_STAT_FALLBACKS = 3     /* samples re-run with kernel 1 after kernel 2 withdrew them, since
+                                  lap_set_root (synchronises) */
+} lap_stat;
 
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t lap_version(void);
@@ -111,8 +126,9 @@ lap_status lap_set_option(lap_graph *g, int32_t option, int64_t value);
 
 /*
  * Device workspace for the per-sample Wilson state (8 bytes per node per
- * sample in flight).  lap_workspace_query returns the bytes needed to keep
- * `slots` samples in flight.  lap_set_workspace lends the handle a caller-owned
+ * sample in flight with kernel 1; n rounded up to 256 plus 4 bytes per
+ * stack entry with kernel 2).  lap_workspace_query returns the bytes the
+ * current kernel needs to keep `slots` samples in flight.  lap_set_workspace lends the handle a caller-owned
  * device buffer (at least 8*n bytes, 256-byte aligned), which must stay alive
  * while the handle uses it; the handle zeroes it.  Without a workspace,
  * lap_sample allocates one itself (up to 1/2 of the free device memory).
@@ -182,6 +198,9 @@ lap_status lap_kemeny(lap_graph *g, double *out1);
  * Any pointer may be NULL.  Host memory when on_device = 0.  Synchronises.
  */
 lap_status lap_counts(lap_graph *g, uint64_t *cnt1, uint64_t *cnt2, uint64_t *sums, int on_device);
+
+/* Read a statistic (see lap_stat) into *value. */
+lap_status lap_get_stat(lap_graph *g, int32_t stat, int64_t *value);
 
 /* Hop distance from the root for every node (int32[n]; host when
  * on_device = 0), as found by the connectivity check of lap_set_root. */

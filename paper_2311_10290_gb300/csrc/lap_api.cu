@@ -51,6 +51,7 @@ void free_all(lap_graph *g)
     cudaFree(g->d_ecc);
     cudaFree(g->d_red);
     cudaFree(g->d_slot_epoch);
+    cudaFree(g->d_ovf_ids);
     if (g->ws_owned) cudaFree(g->ws);
 }
 
@@ -63,9 +64,119 @@ lap_status check_sticky(lap_graph *g)
 
 uint64_t default_step_limit(int32_t n) { return (1ull << 20) + 1024ull * (uint64_t)n; }
 
+uint64_t n_pad_of(const lap_graph *g) { return ((uint64_t)g->n + 255ull) & ~255ull; }
+
+// Loop-erased paths of a Wilson run on small-world graphs grow like sqrt(n)
+// (about 1.6e3 nodes at most at n = 1e6 with a hub root), so the default
+// stack holds 16 sqrt(n) entries, at least 1024.
+uint32_t stack_cap_of(const lap_graph *g)
+{
+    if (g->stack_cap) return g->stack_cap;
+    uint64_t c = 1024;
+    while (c * c < 256ull * (uint64_t)g->n && c < (1u << 20)) c <<= 1;
+    return (uint32_t)c;
+}
+
+uint64_t slot_bytes_of(const lap_graph *g, int kernel)
+{
+    if (kernel == LAP_KERNEL_WIDE) return 8ull * (uint64_t)g->n;
+    return (n_pad_of(g) + 4ull * stack_cap_of(g) + 255ull) & ~255ull;
+}
+
+int choose_kernel(const lap_graph *g)
+{
+    if (g->kernel_opt == LAP_KERNEL_WIDE) return LAP_KERNEL_WIDE;
+    if (g->n >= (1 << 27) || g->compact_disabled) return LAP_KERNEL_WIDE;
+    if (g->ws && g->ws_bytes < slot_bytes_of(g, LAP_KERNEL_COMPACT)) return LAP_KERNEL_WIDE;
+    return LAP_KERNEL_COMPACT;
+}
+
+// Makes sure a workspace exists and holds the layout of `kernel`, zeroed
+// when the layout changed (epoch bits then read "stale" everywhere).
+lap_status ensure_workspace(lap_graph *g, int kernel)
+{
+    const uint64_t per_slot = slot_bytes_of(g, kernel);
+    if (!g->ws) {
+        size_t free_b = 0, total_b = 0;
+        LAP_CUDA(g, cudaMemGetInfo(&free_b, &total_b));
+        uint64_t want = (uint64_t)free_b / 2;
+        uint64_t cap = per_slot * (uint64_t)g->num_sms * 2048ull;
+        if (want > cap) want = cap;
+        want = (want / 256) * 256;
+        if (want < per_slot) return fail(g, LAP_ERR_OOM, "not enough device memory for one Wilson state");
+        cudaError_t e = cudaMalloc(&g->ws, want);
+        if (e != cudaSuccess) { cudaGetLastError(); g->ws = nullptr; return fail(g, LAP_ERR_OOM, "workspace allocation failed"); }
+        g->ws_bytes = want;
+        g->ws_owned = true;
+        g->ws_zeroed = false;
+    }
+    const uint64_t slots = g->ws_bytes / per_slot;
+    if (slots == 0) return fail(g, LAP_ERR_OOM, "workspace smaller than one sample's state");
+    if (slots > g->slot_epoch_cap) {
+        cudaFree(g->d_slot_epoch);
+        g->d_slot_epoch = nullptr;
+        g->slot_epoch_cap = 0;
+        if (dalloc(&g->d_slot_epoch, slots) != cudaSuccess) { cudaGetLastError(); return fail(g, LAP_ERR_OOM, "slot table allocation failed"); }
+        g->slot_epoch_cap = slots;
+        g->ws_zeroed = false;
+    }
+    if (g->last_kernel != kernel) g->ws_zeroed = false;
+    if (!g->ws_zeroed) {
+        LAP_CUDA(g, cudaMemsetAsync(g->ws, 0, g->ws_bytes, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_slot_epoch, 0, sizeof(unsigned int) * g->slot_epoch_cap, g->stream));
+        g->ws_zeroed = true;
+        g->last_kernel = kernel;
+    }
+    return LAP_OK;
+}
+
+uint64_t slots_for(const lap_graph *g, int kernel, uint64_t n_samples)
+{
+    uint64_t slots = g->ws ? g->ws_bytes / slot_bytes_of(g, kernel) : 0;
+    if (g->slots_opt && g->slots_opt < slots) slots = g->slots_opt;
+    if (n_samples && slots > n_samples) slots = n_samples;
+    return slots;
+}
+
+lap_status launch(lap_graph *g, LapSampleLaunch &p, int kernel)
+{
+    p.slots = slots_for(g, kernel, p.count);
+    p.slot_bytes = slot_bytes_of(g, kernel);
+    p.n_pad = n_pad_of(g);
+    p.stack_cap = kernel == LAP_KERNEL_COMPACT ? (uint32_t)((p.slot_bytes - p.n_pad) / 4ull) : 0u;
+    LAP_CUDA(g, cudaMemsetAsync(&g->d_acc->claim, 0, sizeof(unsigned int), g->stream));
+    if (kernel == LAP_KERNEL_WIDE) LAP_CUDA(g, lap_launch_sample(p, g->stream));
+    else LAP_CUDA(g, lap_launch_sample_compact(p, g->stream));
+    return LAP_OK;
+}
+
+// Finishes a compact launch: the samples it withdrew (state did not fit one
+// byte per node, see sampler_compact.cu) are re-run with the 8-byte kernel,
+// which gives them exactly the counts the compact kernel would have.
+lap_status resolve_pending(lap_graph *g)
+{
+    if (!g->pending) return LAP_OK;
+    g->pending = false;
+    LapDevAcc h;
+    LAP_CUDA(g, cudaMemcpyAsync(&h, g->d_acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    if (h.ovf_count == 0) return LAP_OK;
+    LAP_CUDA(g, cudaMemsetAsync(&g->d_acc->ovf_count, 0, sizeof(unsigned int), g->stream));
+    g->fallbacks += h.ovf_count;
+    lap_status s = ensure_workspace(g, LAP_KERNEL_WIDE);
+    if (s != LAP_OK) return s;
+    LapSampleLaunch p = g->pending_launch;
+    p.ids = g->d_ovf_ids;
+    p.trace_base = p.first;
+    p.count = h.ovf_count;
+    return launch(g, p, LAP_KERNEL_WIDE);
+}
+
 // Reads the device status word and turns it into a sticky error.
 lap_status poll_status(lap_graph *g)
 {
+    lap_status s = resolve_pending(g);
+    if (s != LAP_OK) return s;
     LapDevAcc h;
     LAP_CUDA(g, cudaMemcpyAsync(&h, g->d_acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
     LAP_CUDA(g, cudaStreamSynchronize(g->stream));
@@ -76,40 +187,6 @@ lap_status poll_status(lap_graph *g)
     if (h.status & LAP_DEV_K_OVERFLOW) {
         g->sticky = LAP_ERR_STEP_LIMIT;
         return fail(g, LAP_ERR_STEP_LIMIT, "a node was visited more than 2^30 times in one sample");
-    }
-    return LAP_OK;
-}
-
-lap_status ensure_workspace(lap_graph *g)
-{
-    const uint64_t per_slot = 8ull * (uint64_t)g->n;
-    if (!g->ws) {
-        size_t free_b = 0, total_b = 0;
-        LAP_CUDA(g, cudaMemGetInfo(&free_b, &total_b));
-        uint64_t want = (uint64_t)free_b / 2;
-        uint64_t cap = per_slot * (uint64_t)g->num_sms * 2048ull;
-        if (want > cap) want = cap;
-        want = (want / per_slot) * per_slot;
-        if (want < per_slot) return fail(g, LAP_ERR_OOM, "not enough device memory for one Wilson state");
-        cudaError_t e = cudaMalloc(&g->ws, want);
-        if (e != cudaSuccess) { cudaGetLastError(); g->ws = nullptr; return fail(g, LAP_ERR_OOM, "workspace allocation failed"); }
-        g->ws_bytes = want;
-        g->ws_owned = true;
-        g->ws_zeroed = false;
-    }
-    const uint64_t slots = g->ws_bytes / per_slot;
-    if (slots > g->slot_epoch_cap) {
-        cudaFree(g->d_slot_epoch);
-        g->d_slot_epoch = nullptr;
-        g->slot_epoch_cap = 0;
-        if (dalloc(&g->d_slot_epoch, slots) != cudaSuccess) { cudaGetLastError(); return fail(g, LAP_ERR_OOM, "slot table allocation failed"); }
-        g->slot_epoch_cap = slots;
-        g->ws_zeroed = false;
-    }
-    if (!g->ws_zeroed) {
-        LAP_CUDA(g, cudaMemsetAsync(g->ws, 0, g->ws_bytes, g->stream));
-        LAP_CUDA(g, cudaMemsetAsync(g->d_slot_epoch, 0, sizeof(unsigned int) * g->slot_epoch_cap, g->stream));
-        g->ws_zeroed = true;
     }
     return LAP_OK;
 }
@@ -231,6 +308,16 @@ lap_status lap_set_option(lap_graph *g, int32_t option, int64_t value)
         if ((uint64_t)value >= (1ull << 32)) return fail(g, LAP_ERR_TOO_LARGE, "sample ids are limited to 2^32");
         g->cursor = (uint64_t)value;
         return LAP_OK;
+    case LAP_OPT_KERNEL:
+        if (value > 2) return fail(g, LAP_ERR_INVALID_ARG, "kernel must be 0, 1 or 2");
+        if (value == LAP_KERNEL_COMPACT && g->n >= (1 << 27)) return fail(g, LAP_ERR_INVALID_ARG, "kernel 2 needs n < 2^27");
+        g->kernel_opt = (int)value;
+        return LAP_OK;
+    case LAP_OPT_STACK:
+        if (value != 0 && (value < 16 || value > (1 << 22))) return fail(g, LAP_ERR_INVALID_ARG, "stack capacity must be 0 or in [16, 2^22]");
+        g->stack_cap = (uint32_t)value;
+        g->last_kernel = 0;
+        return LAP_OK;
     case LAP_OPT_BLOCK:
         if (value != 0 && (value % 32 != 0 || value > 256)) return fail(g, LAP_ERR_INVALID_ARG, "block must be 0 or a multiple of 32 up to 256");
         g->block_opt = (int)value;
@@ -243,21 +330,38 @@ lap_status lap_set_option(lap_graph *g, int32_t option, int64_t value)
 lap_status lap_workspace_query(const lap_graph *g, uint64_t slots, uint64_t *bytes)
 {
     if (!g || !bytes) return fail(nullptr, LAP_ERR_INVALID_ARG, "NULL argument");
-    *bytes = 8ull * (uint64_t)g->n * slots;
+    *bytes = slot_bytes_of(g, choose_kernel(g)) * slots;
     return LAP_OK;
+}
+
+lap_status lap_get_stat(lap_graph *g, int32_t stat, int64_t *value)
+{
+    if (!g || !value) return fail(nullptr, LAP_ERR_INVALID_ARG, "NULL argument");
+    switch (stat) {
+    case LAP_STAT_SLOTS: *value = (int64_t)slots_for(g, choose_kernel(g), 0); return LAP_OK;
+    case LAP_STAT_KERNEL: *value = choose_kernel(g); return LAP_OK;
+    case LAP_STAT_FALLBACKS: {
+        lap_status s = resolve_pending(g);
+        if (s != LAP_OK) return s;
+        *value = g->fallbacks;
+        return LAP_OK;
+    }
+    default: return fail(g, LAP_ERR_INVALID_ARG, "unknown statistic");
+    }
 }
 
 lap_status lap_set_workspace(lap_graph *g, void *device_ptr, uint64_t bytes)
 {
     if (!g) return fail(nullptr, LAP_ERR_INVALID_ARG, "NULL handle");
-    if (!device_ptr || bytes < 8ull * (uint64_t)g->n) return fail(g, LAP_ERR_INVALID_ARG, "workspace must hold at least 8*n bytes");
+    if (!device_ptr || bytes < slot_bytes_of(g, LAP_KERNEL_WIDE)) return fail(g, LAP_ERR_INVALID_ARG, "workspace must hold at least 8*n bytes");
     if (reinterpret_cast<uintptr_t>(device_ptr) % 256 != 0) return fail(g, LAP_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     cudaStreamSynchronize(g->stream);
     if (g->ws_owned) cudaFree(g->ws);
     g->ws = device_ptr;
-    g->ws_bytes = (bytes / (8ull * (uint64_t)g->n)) * 8ull * (uint64_t)g->n;
+    g->ws_bytes = bytes & ~255ull;
     g->ws_owned = false;
     g->ws_zeroed = false;
+    g->last_kernel = 0;
     return LAP_OK;
 }
 
@@ -298,6 +402,9 @@ lap_status lap_set_root(lap_graph *g, int32_t v, int32_t *root_out)
     LAP_CUDA(g, cudaMemsetAsync(g->d_cnt2, 0, sizeof(unsigned long long) * (size_t)g->n, g->stream));
     LAP_CUDA(g, cudaMemsetAsync(g->d_acc, 0, sizeof(LapDevAcc), g->stream));
     g->ws_zeroed = false;                 // a failed earlier run may have left partial state
+    g->pending = false;
+    g->compact_disabled = false;
+    g->fallbacks = 0;
     g->root = v;
     g->seed_set = false;
     g->omega = 0;
@@ -313,31 +420,43 @@ lap_status lap_sample(lap_graph *g, uint64_t n_samples, uint64_t seed)
     return lap_sample_trace(g, n_samples, seed, nullptr, nullptr);
 }
 
+static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, uint64_t *y1_dev, uint64_t *y2_dev);
+
 lap_status lap_sample_trace(lap_graph *g, uint64_t n_samples, uint64_t seed, uint64_t *y1_dev, uint64_t *y2_dev)
 {
     if ((y1_dev == nullptr) != (y2_dev == nullptr)) return fail(g, LAP_ERR_INVALID_ARG, "y1_dev and y2_dev must both be set or both be NULL");
+    // Launches of at most 2^24 samples bound the overflow list.
+    const uint64_t chunk = 1ull << 24;
+    for (uint64_t done = 0; done < n_samples || (n_samples == 0 && done == 0);) {
+        const uint64_t c = n_samples - done < chunk ? n_samples - done : chunk;
+        lap_status s = sample_chunk(g, c, seed, y1_dev ? y1_dev + done : nullptr, y2_dev ? y2_dev + done : nullptr);
+        if (s != LAP_OK || n_samples == 0) return s;
+        done += c;
+    }
+    return LAP_OK;
+}
+
+static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, uint64_t *y1_dev, uint64_t *y2_dev)
+{
     lap_status s = check_sticky(g);
     if (s != LAP_OK) return s;
     if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
     if (g->seed_set && seed != g->seed) return fail(g, LAP_ERR_INVALID_ARG, "seed differs from the seed in use since lap_set_root");
     if (g->cursor + n_samples > (1ull << 32)) return fail(g, LAP_ERR_TOO_LARGE, "sample ids are limited to 2^32");
     if (n_samples == 0) return LAP_OK;
-    if ((s = ensure_workspace(g)) != LAP_OK) return s;
+    if ((s = resolve_pending(g)) != LAP_OK) return s;
+    const int kernel = choose_kernel(g);
+    if ((s = ensure_workspace(g, kernel)) != LAP_OK) return s;
     g->seed = seed;
     g->seed_set = true;
 
-    const uint64_t per_slot = 8ull * (uint64_t)g->n;
-    uint64_t slots = g->ws_bytes / per_slot;
-    if (g->slots_opt && g->slots_opt < slots) slots = g->slots_opt;
-    if (slots > n_samples) slots = n_samples;
-
     LapSampleLaunch p;
+    memset(&p, 0, sizeof(p));
     p.g = LapDevGraph{g->d_rowinfo, g->d_col, g->n, g->arcs};
     p.root = g->root;
     p.seed = seed;
     p.first = (uint32_t)g->cursor;
     p.count = (uint32_t)n_samples;
-    p.slots = slots;
     p.ws = g->ws;
     p.slot_epoch = g->d_slot_epoch;
     p.rep1 = g->d_rep1;
@@ -347,8 +466,24 @@ lap_status lap_sample_trace(lap_graph *g, uint64_t n_samples, uint64_t seed, uin
     p.block = g->block_opt;
     p.y1_out = reinterpret_cast<unsigned long long *>(y1_dev);
     p.y2_out = reinterpret_cast<unsigned long long *>(y2_dev);
-    LAP_CUDA(g, cudaMemsetAsync(&g->d_acc->claim, 0, sizeof(unsigned int), g->stream));
-    LAP_CUDA(g, lap_launch_sample(p, g->stream));
+    if (kernel == LAP_KERNEL_COMPACT) {
+        if (g->ovf_cap < n_samples) {
+            cudaFree(g->d_ovf_ids);
+            g->d_ovf_ids = nullptr;
+            g->ovf_cap = 0;
+            if (dalloc(&g->d_ovf_ids, (size_t)n_samples) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(g, LAP_ERR_OOM, "overflow list allocation failed");
+            }
+            g->ovf_cap = n_samples;
+        }
+        p.ovf_ids = g->d_ovf_ids;
+    }
+    if ((s = launch(g, p, kernel)) != LAP_OK) return s;
+    if (kernel == LAP_KERNEL_COMPACT) {
+        g->pending = true;
+        g->pending_launch = p;
+    }
     g->omega += n_samples;
     g->cursor += n_samples;
     g->results_valid = false;

@@ -32,8 +32,57 @@ struct LapDevAcc {
     unsigned long long sum_y2;     // sum over samples of Y2 (pi-start walk length)
     unsigned int status;           // LAP_DEV_* bits
     unsigned int claim;            // next sample offset to claim inside a launch
-    unsigned long long pad[5];
+    unsigned int ovf_count;        // compact kernel: samples withdrawn in this launch
+    unsigned int pad0;
+    unsigned long long pad[4];
 };
+
+// ---------------------------------------------------------------- kernels
+// ingest.cu
+cudaError_t lap_launch_validate(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t arcs,
+                                unsigned int *status, cudaStream_t st);
+cudaError_t lap_launch_rowinfo(const int32_t *row_ptr, int32_t n, int2 *rowinfo, cudaStream_t st);
+cudaError_t lap_launch_argmax_degree(const int2 *rowinfo, int32_t n, unsigned long long *best, cudaStream_t st);
+cudaError_t lap_launch_bfs_init(int32_t *hops, int32_t n, int32_t root, cudaStream_t st);
+cudaError_t lap_launch_bfs_level(const int2 *rowinfo, const int32_t *col, int32_t *hops, int32_t n,
+                                 int32_t level, unsigned int *found, cudaStream_t st);
+
+// sampler.cu
+struct LapSampleLaunch {
+    LapDevGraph g;
+    int32_t root;
+    uint64_t seed;
+    uint32_t first;          // first sample id of this launch
+    uint32_t count;          // samples in this launch
+    uint64_t slots;          // lanes with their own Wilson state
+    void *ws;                // slots * n * 8 bytes
+    unsigned int *slot_epoch;
+    unsigned long long *rep1;
+    unsigned long long *cnt2;
+    LapDevAcc *acc;
+    uint64_t step_limit;
+    int block;
+    unsigned long long *y1_out;  // optional [count]: Y1 of sample first+q at q
+    unsigned long long *y2_out;  // optional [count]: Y2 of sample first+q at q
+    uint64_t slot_bytes;         // compact kernel: bytes of one slot (state + stack)
+    uint64_t n_pad;              // compact kernel: state bytes of one slot (n rounded up to 256)
+    uint32_t stack_cap;          // compact kernel: stack entries of one slot
+    unsigned int *ovf_ids;       // compact kernel: withdrawn sample ids [count]
+    const unsigned int *ids;     // wide kernel: explicit sample ids [count] (NULL: first + q)
+    uint32_t trace_base;         // wide kernel with ids: y1_out/y2_out index = id - trace_base
+};
+cudaError_t lap_launch_sample(const LapSampleLaunch &p, cudaStream_t st);
+// sampler_compact.cu
+cudaError_t lap_launch_sample_compact(const LapSampleLaunch &p, cudaStream_t st);
+
+enum LapKernel : int { LAP_KERNEL_WIDE = 1, LAP_KERNEL_COMPACT = 2 };
+
+// finalize.cu
+cudaError_t lap_launch_finalize(const int2 *rowinfo, int32_t n, int32_t root, uint64_t omega,
+                                const unsigned long long *rep1, const unsigned long long *cnt2,
+                                double *ldiag, double *ecc, double *red, cudaStream_t st);
+cudaError_t lap_launch_counts(int32_t n, int32_t root, uint64_t omega, const unsigned long long *rep1,
+                              unsigned long long *cnt1, cudaStream_t st);
 
 struct lap_graph {
     int device = 0;
@@ -70,44 +119,18 @@ struct lap_graph {
     uint64_t step_limit = 0;                // 0: default
     uint64_t slots_opt = 0;
     int block_opt = 0;
+    int kernel_opt = 0;                     // 0 auto, LAP_KERNEL_WIDE, LAP_KERNEL_COMPACT
+    uint32_t stack_cap = 0;                 // 0: default, about 16 sqrt(n)
+    int last_kernel = 0;                    // layout the workspace currently holds
+    bool compact_disabled = false;          // set after a compact launch overflowed
+    int64_t fallbacks = 0;
+
+    // Samples a compact launch withdrew; re-run with the wide kernel.
+    unsigned int *d_ovf_ids = nullptr;
+    uint64_t ovf_cap = 0;
+    bool pending = false;
+    LapSampleLaunch pending_launch;
 
     lap_status sticky = LAP_OK;
     std::string err;
 };
-
-// ---------------------------------------------------------------- kernels
-// ingest.cu
-cudaError_t lap_launch_validate(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t arcs,
-                                unsigned int *status, cudaStream_t st);
-cudaError_t lap_launch_rowinfo(const int32_t *row_ptr, int32_t n, int2 *rowinfo, cudaStream_t st);
-cudaError_t lap_launch_argmax_degree(const int2 *rowinfo, int32_t n, unsigned long long *best, cudaStream_t st);
-cudaError_t lap_launch_bfs_init(int32_t *hops, int32_t n, int32_t root, cudaStream_t st);
-cudaError_t lap_launch_bfs_level(const int2 *rowinfo, const int32_t *col, int32_t *hops, int32_t n,
-                                 int32_t level, unsigned int *found, cudaStream_t st);
-
-// sampler.cu
-struct LapSampleLaunch {
-    LapDevGraph g;
-    int32_t root;
-    uint64_t seed;
-    uint32_t first;          // first sample id of this launch
-    uint32_t count;          // samples in this launch
-    uint64_t slots;          // lanes with their own Wilson state
-    void *ws;                // slots * n * 8 bytes
-    unsigned int *slot_epoch;
-    unsigned long long *rep1;
-    unsigned long long *cnt2;
-    LapDevAcc *acc;
-    uint64_t step_limit;
-    int block;
-    unsigned long long *y1_out;  // optional [count]: Y1 of sample first+q at q
-    unsigned long long *y2_out;  // optional [count]: Y2 of sample first+q at q
-};
-cudaError_t lap_launch_sample(const LapSampleLaunch &p, cudaStream_t st);
-
-// finalize.cu
-cudaError_t lap_launch_finalize(const int2 *rowinfo, int32_t n, int32_t root, uint64_t omega,
-                                const unsigned long long *rep1, const unsigned long long *cnt2,
-                                double *ldiag, double *ecc, double *red, cudaStream_t st);
-cudaError_t lap_launch_counts(int32_t n, int32_t root, uint64_t omega, const unsigned long long *rep1,
-                              unsigned long long *cnt1, cudaStream_t st);

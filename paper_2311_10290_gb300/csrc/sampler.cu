@@ -148,7 +148,11 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
             if (u == v) {
                 acc1 += y1;
                 acc2 += y2;
-                if (p.y1_out) { p.y1_out[i - p.first] = y1; p.y2_out[i - p.first] = y2; }
+                if (p.y1_out) {
+                    const uint32_t ix = i - (p.ids ? p.trace_base : p.first);
+                    p.y1_out[ix] = y1;
+                    p.y2_out[ix] = y2;
+                }
                 phase = P_CLAIM;
             }
             else { pb = ld_row(rowinfo, u); phase = P_PIDRAW; }
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
             if (bad) { phase = P_DONE; break; }
             const unsigned int q = atomicAdd(&p.acc->claim, 1u);
             if (q >= p.count) { phase = P_DONE; break; }
-            i = p.first + q;
+            i = p.ids ? p.ids[q] : p.first + q;
             epoch ^= kEpoch;
             st[v] = (unsigned long long)(epoch | kTree);
             s = 0;

@@ -1,0 +1,263 @@
+// Compact LEWalk sampler: same computation and same counts as lewalk_kernel
+// (sampler.cu: Wilson LE_v run, uniform-start and pi-start v-absorbed walks
+// per sample; Alg. 2 and Alg. 4), with one byte of state per node per sample
+// in flight instead of eight, so about eight times more samples (independent
+// gather chains) fit in HBM.
+//
+// Per node and sample one byte:   bit 7 epoch | bit 6 InTree | bit 5 OnPath | bits 0..4 draws k
+// The Next[] array of Alg. 2 is replaced by a per-lane stack holding the
+// current loop-erased path (entries: node | k << 27).  A walk step at head h
+// draws stack entry k of h (Philox counter (h, k, i, 0)), pushes h and moves
+// to w = RandomNeighbor(h):
+//   w InTree  -> the path joins the tree: every stacked node is marked InTree
+//                (Alg. 2's retrace; the path on the stack is exactly the
+//                loop-erased path the retrace would follow along Next[]);
+//   w OnPath  -> the walk closed a loop at w: the nodes above w are erased
+//                (OnPath cleared, their draw counts kept) and w draws again;
+//   otherwise -> w becomes the head.
+// Visits, Y1 and the tree are those of the sequential run, because every
+// draw is still the next entry of the node's stack.
+//
+// Every node's byte keeps its draw count k for the whole sample (also once
+// InTree), and the repeat-visit counter has received exactly k - 1 for every
+// node touched so far.  A sample that cannot be represented (a node drawn
+// more than 31 times, or a loop-erased path longer than the stack) is
+// therefore withdrawn exactly: the lane subtracts k - 1 for every node of
+// the sample, re-stamps its state bytes with the current epoch (so the next
+// sample sees them all as stale), appends the sample id to an overflow list
+// and goes on with the next sample.  The host re-runs the listed ids with
+// the 8-byte kernel.  Nothing else of a sample is counted before its Wilson
+// run completes.
+#include "lap_internal.h"
+#include "philox.cuh"
+
+namespace {
+
+constexpr uint32_t kBEpoch = 0x80u, kBTree = 0x40u, kBPath = 0x20u, kBK = 0x1Fu;
+constexpr uint32_t kKMax = 31u;
+constexpr int kEntryShift = 27;
+constexpr uint32_t kNodeMask = (1u << kEntryShift) - 1u;
+
+enum Phase : uint32_t {
+    P_CLAIM = 0,
+    P_SCAN,      // pq = 16 state bytes at s & ~15
+    P_DRAW,      // pb = row record of the head h
+    P_MOVE,      // pb = column entry chosen at h
+    P_STEP,      // pa = state byte of x, pb = row record of x
+    P_USTART,
+    P_UDRAW,
+    P_UMOVE,
+    P_PISTART,
+    P_PIDRAW,
+    P_PIMOVE,
+    P_DONE
+};
+
+__device__ __forceinline__ bool b_current(uint32_t b, uint32_t ep) { return (b & kBEpoch) == ep; }
+__device__ __forceinline__ bool b_tree(uint32_t b, uint32_t ep) { return b_current(b, ep) && (b & kBTree); }
+__device__ __forceinline__ bool b_path(uint32_t b, uint32_t ep) { return b_current(b, ep) && (b & kBPath); }
+__device__ __forceinline__ uint32_t b_k(uint32_t b, uint32_t ep) { return b_current(b, ep) ? (b & kBK) : 0u; }
+__device__ __forceinline__ uint64_t ld_row(const int2 *rowinfo, int32_t u)
+{
+    return (uint64_t)__ldg(reinterpret_cast<const unsigned long long *>(rowinfo) + u);
+}
+__device__ __forceinline__ int32_t row_off(uint64_t r) { return (int32_t)(uint32_t)r; }
+__device__ __forceinline__ uint32_t row_deg(uint64_t r) { return (uint32_t)(r >> 32); }
+
+// Bit b of the result is set when byte b of the 16 bytes is not InTree.
+__device__ __forceinline__ uint32_t not_tree_mask(ulonglong2 q, uint32_t ep)
+{
+    uint32_t m = 0;
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+        const uint32_t byte = (uint32_t)(((b < 8 ? q.x : q.y) >> (8 * (b & 7))) & 0xFFu);
+        m |= (b_tree(byte, ep) ? 0u : 1u) << b;
+    }
+    return m;
+}
+
+// Withdraws a partly run sample: subtracts the k - 1 repeat visits every
+// node of the sample has contributed and marks all bytes "current epoch,
+// untouched", so that the next sample (next epoch) reads them as stale.
+__device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsigned long long *rep1)
+{
+    for (int32_t base = 0; base < n; base += 16) {
+        ulonglong2 q = *reinterpret_cast<ulonglong2 *>(st + base);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+            const uint32_t byte = (uint32_t)(((b < 8 ? q.x : q.y) >> (8 * (b & 7))) & 0xFFu);
+            const uint32_t k = b_k(byte, ep);
+            if (base + b < n && k >= 2u) atomicAdd(&rep1[base + b], (unsigned long long)(-(long long)(k - 1u)));
+        }
+        const unsigned long long fill = 0x0101010101010101ull * (unsigned long long)ep;
+        *reinterpret_cast<ulonglong2 *>(st + base) = make_ulonglong2(fill, fill);
+    }
+}
+
+__global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
+{
+    const uint64_t slot = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (slot >= p.slots) return;
+    const int32_t n = p.g.n;
+    const int32_t v = p.root;
+    const int2 *__restrict__ rowinfo = p.g.rowinfo;
+    const int32_t *__restrict__ col = p.g.col;
+    uint8_t *__restrict__ st = reinterpret_cast<uint8_t *>(p.ws) + slot * p.slot_bytes;
+    uint32_t *__restrict__ stk = reinterpret_cast<uint32_t *>(st + p.n_pad);
+    const uint32_t cap = p.stack_cap;
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    const uint64_t limit = p.step_limit;
+
+    uint32_t ep = p.slot_epoch[slot] ? kBEpoch : 0u;
+    uint32_t phase = P_CLAIM;
+    uint32_t i = 0;
+    int32_t s = 0;            // scan position (Alg. 2's id ordering)
+    int32_t h = 0;            // head of the walk
+    uint32_t kh = 0;          // draws at h so far
+    uint32_t sp = 0;          // stack depth
+    uint64_t pa = 0, pb = 0;
+    ulonglong2 pq = make_ulonglong2(0, 0);
+    uint64_t y1 = 0, t = 0, y2 = 0;
+    unsigned long long acc1 = 0, acc2 = 0;
+    unsigned int bad = 0;
+
+    while (phase != P_DONE) {
+        if (phase == P_MOVE) {
+            const int32_t w = (int32_t)(uint32_t)pb;
+            const uint32_t kn = kh + 1u;
+            if (kn > kKMax || sp >= cap) {
+                withdraw_sample(st, n, ep, p.rep1);
+                const unsigned int slot_ix = atomicAdd(&p.acc->ovf_count, 1u);
+                if (slot_ix < p.count) p.ovf_ids[slot_ix] = i;
+                phase = P_CLAIM;
+                continue;
+            }
+            stk[sp++] = (uint32_t)h | (kn << kEntryShift);
+            st[h] = (uint8_t)(ep | kBPath | kn);
+            if (kh) atomicAdd(&p.rep1[h], 1ull);
+            if (++y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
+            h = w;
+            pa = st[w];
+            pb = ld_row(rowinfo, w);
+            phase = P_STEP;
+        } else if (phase == P_STEP || phase == P_DRAW) {
+            bool draw = true;
+            if (phase == P_STEP) {
+                const uint32_t b = (uint32_t)pa;
+                if (b_tree(b, ep)) {
+                    // Alg. 2 retrace: the loop-erased path on the stack joins the tree
+                    // (draw counts kept in the byte, see withdraw_sample).
+                    while (sp) {
+                        const uint32_t e = stk[--sp];
+                        st[e & kNodeMask] = (uint8_t)(ep | kBTree | (e >> kEntryShift));
+                    }
+                    draw = false;
+                    ++s;
+                    if (s < n) {
+                        pq = *reinterpret_cast<const ulonglong2 *>(st + (s & ~15));
+                        phase = P_SCAN;
+                    } else {
+                        phase = P_USTART;
+                    }
+                } else {
+                    if (b_path(b, ep)) {
+                        // Loop closed at h: erase the nodes above h and h's own entry.
+                        uint32_t e, node;
+                        do {
+                            e = stk[--sp];
+                            node = e & kNodeMask;
+                            if ((int32_t)node != h) st[node] = (uint8_t)(ep | (e >> kEntryShift));
+                        } while ((int32_t)node != h);
+                    }
+                    kh = b_k(b, ep);
+                }
+            }
+            if (draw) {
+                const uint64_t r = lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1);
+                pb = (uint64_t)(uint32_t)__ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
+                phase = P_MOVE;
+            }
+        } else if (phase == P_SCAN) {
+            const int32_t base = s & ~15;
+            uint32_t m = not_tree_mask(pq, ep) & (0xFFFFu << (s - base));
+            if (n - base < 16) m &= (1u << (n - base)) - 1u;
+            if (m) {
+                s = base + __ffs(m) - 1;
+                h = s;
+                const uint32_t b = (uint32_t)(((s - base < 8 ? pq.x : pq.y) >> (8 * ((s - base) & 7))) & 0xFFu);
+                kh = b_k(b, ep);
+                pb = ld_row(rowinfo, h);
+                phase = P_DRAW;
+            } else {
+                s = base + 16;
+                if (s < n) pq = *reinterpret_cast<const ulonglong2 *>(st + s);
+                else phase = P_USTART;
+            }
+        } else if (phase == P_UDRAW) {
+            ++t;
+            const uint64_t r = lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1);
+            pb = (uint64_t)(uint32_t)__ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
+            phase = P_UMOVE;
+            if (t > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; }
+        } else if (phase == P_UMOVE) {
+            h = (int32_t)(uint32_t)pb;
+            if (h == v) phase = P_PISTART;
+            else { atomicAdd(&p.cnt2[h], 1ull); pb = ld_row(rowinfo, h); phase = P_UDRAW; }
+        } else if (phase == P_PIDRAW) {
+            ++y2;
+            const uint64_t r = lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1);
+            pb = (uint64_t)(uint32_t)__ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
+            phase = P_PIMOVE;
+            if (y2 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; }
+        } else if (phase == P_PIMOVE) {
+            h = (int32_t)(uint32_t)pb;
+            if (h == v) {
+                acc1 += y1;
+                acc2 += y2;
+                if (p.y1_out) { p.y1_out[i - p.first] = y1; p.y2_out[i - p.first] = y2; }
+                phase = P_CLAIM;
+            } else {
+                pb = ld_row(rowinfo, h);
+                phase = P_PIDRAW;
+            }
+        } else if (phase == P_USTART) {
+            t = 0;
+            const uint64_t r = lap::philox_r64(0u, 0u, i, 1u, key0, key1);
+            h = (int32_t)lap::below(r, (uint64_t)n);
+            if (h == v) phase = P_PISTART;
+            else { atomicAdd(&p.cnt2[h], 1ull); pb = ld_row(rowinfo, h); phase = P_UDRAW; }
+        } else if (phase == P_PISTART) {
+            y2 = 0;
+            const uint64_t r = lap::philox_r64(0u, 0u, i, 2u, key0, key1);
+            pb = (uint64_t)(uint32_t)__ldg(col + (int64_t)lap::below(r, (uint64_t)p.g.arcs));
+            phase = P_PIMOVE;
+        } else {  // P_CLAIM
+            if (bad) { phase = P_DONE; break; }
+            const unsigned int q = atomicAdd(&p.acc->claim, 1u);
+            if (q >= p.count) { phase = P_DONE; break; }
+            i = p.first + q;
+            ep ^= kBEpoch;
+            st[v] = (uint8_t)(ep | kBTree);
+            s = 0;
+            sp = 0;
+            y1 = 0;
+            pq = *reinterpret_cast<const ulonglong2 *>(st);
+            phase = P_SCAN;
+        }
+    }
+    p.slot_epoch[slot] = ep ? 1u : 0u;
+    if (acc1) atomicAdd(&p.acc->sum_y1, acc1);
+    if (acc2) atomicAdd(&p.acc->sum_y2, acc2);
+    if (bad) atomicOr(&p.acc->status, bad);
+}
+
+}  // namespace
+
+cudaError_t lap_launch_sample_compact(const LapSampleLaunch &p, cudaStream_t st)
+{
+    if (p.count == 0 || p.slots == 0) return cudaSuccess;
+    int block = p.block > 0 ? p.block : 128;
+    uint64_t grid = (p.slots + block - 1) / block;
+    lewalk_compact_kernel<<<(unsigned)grid, block, 0, st>>>(p);
+    return cudaGetLastError();
+}

@@ -25,7 +25,8 @@ STATUS = {
     4: "LAP_ERR_SELF_LOOP", 5: "LAP_ERR_DISCONNECTED", 6: "LAP_ERR_TOO_LARGE", 7: "LAP_ERR_OOM",
     8: "LAP_ERR_NO_SAMPLES", 9: "LAP_ERR_STEP_LIMIT", 10: "LAP_ERR_CUDA", 11: "LAP_ERR_NO_ROOT",
 }
-LAP_OPT_STEP_LIMIT, LAP_OPT_SLOTS, LAP_OPT_BLOCK, LAP_OPT_CURSOR = 1, 2, 3, 4
+LAP_OPT_STEP_LIMIT, LAP_OPT_SLOTS, LAP_OPT_BLOCK, LAP_OPT_CURSOR, LAP_OPT_KERNEL, LAP_OPT_STACK = 1, 2, 3, 4, 5, 6
+LAP_STAT_SLOTS, LAP_STAT_KERNEL, LAP_STAT_FALLBACKS = 1, 2, 3
 
 
 class LapError(RuntimeError):
@@ -65,6 +66,7 @@ def library():
         "lap_kemeny": (i32, [vp, vp]),
         "lap_counts": (i32, [vp, vp, vp, vp, ctypes.c_int]),
         "lap_hops": (i32, [vp, vp, ctypes.c_int]),
+        "lap_get_stat": (i32, [vp, i32, ctypes.POINTER(i64)]),
         "lap_graph_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]),
         "lap_last_error": (ctypes.c_char_p, [vp]),
     }
@@ -195,6 +197,12 @@ def lap_counts(h, n, per_node=True):
     return c1, c2, s
 
 
+def lap_get_stat(h, stat):
+    x = ctypes.c_int64()
+    _check(library().lap_get_stat(h, int(stat), ctypes.byref(x)), h)
+    return x.value
+
+
 def lap_graph_info(h):
     n, a, r = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
     _check(library().lap_graph_info(h, ctypes.byref(n), ctypes.byref(a), ctypes.byref(r)), h)
@@ -228,8 +236,15 @@ class LapGraph:
         base = self.workspace.data_ptr()
         aligned = (base + 255) // 256 * 256
         lap_set_workspace(self.h, aligned, workspace_bytes)
-        self.slots = workspace_bytes // per_slot
         self.root = None
+
+    @property
+    def slots(self):
+        """Samples in flight per launch with the current kernel and workspace."""
+        return lap_get_stat(self.h, LAP_STAT_SLOTS)
+
+    def stat(self, which):
+        return lap_get_stat(self.h, which)
 
     def close(self):
         if self.h is not None:

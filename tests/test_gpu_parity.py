@@ -14,13 +14,15 @@ from paper_2311_10290_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-from paper_2311_10290_gb300.lap import (LAP_OPT_BLOCK, LAP_OPT_SLOTS, LAP_OPT_STEP_LIMIT,  # noqa: E402
-                                        LapError, LapGraph)
+from paper_2311_10290_gb300.lap import (LAP_OPT_BLOCK, LAP_OPT_KERNEL, LAP_OPT_SLOTS,  # noqa: E402
+                                        LAP_OPT_STACK, LAP_OPT_STEP_LIMIT, LAP_STAT_FALLBACKS,
+                                        LAP_STAT_KERNEL, LapError, LapGraph)
 
 RTOL = 1e-12
 
 
-def gpu_run(g, seed, omega, root=-1, slots=None, block=None, splits=None, ws=None, device_inputs=False):
+def gpu_run(g, seed, omega, root=-1, slots=None, block=None, splits=None, ws=None, device_inputs=False,
+            kernel=None, stack=None, stats=None):
     if device_inputs:
         G = LapGraph(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda(), workspace_bytes=ws)
     else:
@@ -30,11 +32,20 @@ def gpu_run(g, seed, omega, root=-1, slots=None, block=None, splits=None, ws=Non
             G.set_option(LAP_OPT_SLOTS, slots)
         if block:
             G.set_option(LAP_OPT_BLOCK, block)
+        if kernel:
+            G.set_option(LAP_OPT_KERNEL, kernel)
+        if stack:
+            G.set_option(LAP_OPT_STACK, stack)
         v = G.set_root(root)
+        used = G.stat(LAP_STAT_KERNEL)
         for part in (splits or [omega]):
             G.sample(part, seed)
         c1, c2, s = G.counts()
-        return dict(v=v, cnt1=c1, cnt2=c2, sums=s, ld=G.ldiag(), ecc=G.ecc(), kc=G.kemeny())
+        out = dict(v=v, cnt1=c1, cnt2=c2, sums=s, ld=G.ldiag(), ecc=G.ecc(), kc=G.kemeny(),
+                   kernel=used, fallbacks=G.stat(LAP_STAT_FALLBACKS))
+        if stats is not None:
+            stats.update(kernel=used, fallbacks=out["fallbacks"])
+        return out
     finally:
         G.close()
 
@@ -71,16 +82,41 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("kernel", [1, 2], ids=["wide", "compact"])
 @pytest.mark.parametrize("name,maker,root,omega", CASES, ids=[c[0] for c in CASES])
-def test_counts_and_estimates_match_oracle(name, maker, root, omega):
+def test_counts_and_estimates_match_oracle(name, maker, root, omega, kernel):
     g = maker()
     seed = 0x5EED0000 + len(name)
-    r = gpu_run(g, seed, omega, root=root)
+    r = gpu_run(g, seed, omega, root=root, kernel=kernel)
     v = r["v"] if root < 0 else root
     if root < 0:
         assert v == oracle.root_max_degree(g.row_ptr)
     c = oracle_run(g, v, seed, omega, threads=4)
     assert_parity(g, r, c, omega)
+
+
+def test_compact_kernel_is_the_default_and_does_not_fall_back_on_social_graphs():
+    g = I.ba(20000, 4, seed=1)
+    st = {}
+    r = gpu_run(g, 5, 2000, stats=st)
+    assert st == {"kernel": 2, "fallbacks": 0}
+    c = oracle_run(g, r["v"], 5, 2000, threads=4)
+    assert_parity(g, r, c, 2000)
+
+
+@pytest.mark.parametrize("name,maker,root,stack", [
+    ("path_end_kmax", lambda: I.path(60), 0, None),      # far nodes are drawn more than 31 times
+    ("cycle_long_paths", lambda: I.cycle(301), 0, 16),   # loop-erased paths longer than 16
+])
+def test_compact_overflow_rolls_back_to_wide_kernel(name, maker, root, stack):
+    """Samples that do not fit the 1-byte state are re-run with the 8-byte
+    kernel from the counts saved before the launch: results stay exact."""
+    g = maker()
+    st = {}
+    r = gpu_run(g, 3, 300, root=root, kernel=2, stack=stack, splits=[100, 200], stats=st)
+    assert st["fallbacks"] >= 1
+    c = oracle_run(g, root, 3, 300, threads=4)
+    assert_parity(g, r, c, 300)
 
 
 def test_split_calls_equal_one_call():
@@ -91,21 +127,24 @@ def test_split_calls_equal_one_call():
         assert np.array_equal(a[k], b[k])
 
 
+@pytest.mark.parametrize("kernel", [1, 2], ids=["wide", "compact"])
 @pytest.mark.parametrize("slots,block", [(1, 32), (7, 64), (64, 128), (1000, 256), (None, None)])
-def test_launch_shape_does_not_change_counts(slots, block):
+def test_launch_shape_does_not_change_counts(slots, block, kernel):
     g = I.ba(3000, 2, seed=5)
-    ref = gpu_run(g, 3, 500)
-    r = gpu_run(g, 3, 500, slots=slots, block=block)
+    ref = gpu_run(g, 3, 500, kernel=1)
+    r = gpu_run(g, 3, 500, slots=slots, block=block, kernel=kernel)
     for k in ("cnt1", "cnt2", "sums"):
         assert np.array_equal(ref[k], r[k])
 
 
-def test_small_workspace_reuses_slots_across_launches():
-    """Two slots, many samples and several calls: the epoch bit must keep
-    every sample independent of the previous contents of its slot."""
+@pytest.mark.parametrize("kernel", [1, 2], ids=["wide", "compact"])
+def test_small_workspace_reuses_slots_across_launches(kernel):
+    """A 20 kB workspace (2 slots of the compact kernel, 6 of the wide one),
+    many samples and several calls: the epoch bit must keep every sample
+    independent of the previous contents of its slot."""
     g = I.er(400, 0.03, seed=1)
     v = oracle.root_max_degree(g.row_ptr)
-    r = gpu_run(g, 8, 90, ws=2 * 8 * g.n, splits=[1, 2, 3, 40, 44])
+    r = gpu_run(g, 8, 90, ws=20000, splits=[1, 2, 3, 40, 44], kernel=kernel)
     c = oracle_run(g, v, 8, 90)
     assert_parity(g, r, c, 90)
 
@@ -224,10 +263,11 @@ def ba_1m():
     return I.ba_1m()
 
 
-def test_full_size_ba_counts_small_omega(ba_1m):
+@pytest.mark.parametrize("kernel", [1, 2], ids=["wide", "compact"])
+def test_full_size_ba_counts_small_omega(ba_1m, kernel):
     """The 10^6-node Barabasi-Albert workload graph: all counts bit-exact for 48 samples."""
     g = ba_1m
-    r = gpu_run(g, 7, 48)
+    r = gpu_run(g, 7, 48, kernel=kernel)
     c = oracle_run(g, r["v"], 7, 48, threads=8)
     assert_parity(g, r, c, 48)
 
@@ -241,9 +281,11 @@ def test_full_size_ba_bench_launch_sampled(ba_1m):
     G = LapGraph(g.row_ptr, g.col)
     try:
         v = G.set_root()
-        omega = int(min(2 * G.slots + 37, 40000))
+        assert G.stat(LAP_STAT_KERNEL) == 2
+        omega = int(min(2 * G.slots + 37, 400000))
         y1, y2 = G.sample_trace(omega, 2024)
         c1, c2, s = G.counts()
+        assert G.stat(LAP_STAT_FALLBACKS) == 0
         y1 = y1.cpu().numpy().astype(np.uint64)
         y2 = y2.cpu().numpy().astype(np.uint64)
     finally:
