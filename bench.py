@@ -246,6 +246,8 @@ def run_ours(args, rank, world):
     free, _ = torch.cuda.mem_get_info()
     G = LapGraph(g.row_ptr, g.col, workspace_bytes=int(free * args.ws_frac))
     v = G.set_root()
+    from paper_2311_10290_gb300.lap import LAP_STAT_KERNEL
+    kernel_name = {1: "lewalk_kernel (8-byte state)", 2: "lewalk_compact_kernel (1-byte state)"}[G.stat(LAP_STAT_KERNEL)]
     B = args.batch
     total_steps = args.warmup + args.steps
     G.set_option(LAP_OPT_CURSOR, rank * total_steps * B)
@@ -310,7 +312,8 @@ def run_ours(args, rank, world):
                    if args.workload == "ba_1m" else g.name,
                    "n": g.n, "arcs": g.arcs, "root": v, "samples_per_step": B,
                    "samples_timed": samples * world, "slots": G.slots,
-                   "wilson_state_gb": round(G.slots * 8 * g.n / 1e9, 1),
+                   "workspace_gb": round(G.workspace.numel() / 1e9, 1),
+                   "kernel": kernel_name,
                    "l2": "256 MB buffer written between timed steps (outside the events); "
                          "Wilson state working set far above L2",
                    "parallelism": "sample ids sharded over %d GPU(s)" % world},
@@ -318,7 +321,7 @@ def run_ours(args, rank, world):
                        "wilson_steps_per_node_per_sample": wilson / max(1, samples) / g.n},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": float(traffic) if traffic else None,
-                     "kernel": "lewalk_kernel", "kernel_ms": kernel_s * 1e3,
+                     "kernel": kernel_name.split()[0], "kernel_ms": kernel_s * 1e3,
                      "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind},
         "gpu_launches": args.steps * 7,
     }

@@ -464,6 +464,7 @@ static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, 
     p.acc = g->d_acc;
     p.step_limit = g->step_limit ? g->step_limit : default_step_limit(g->n);
     p.block = g->block_opt;
+    p.num_sms = g->num_sms;
     p.y1_out = reinterpret_cast<unsigned long long *>(y1_dev);
     p.y2_out = reinterpret_cast<unsigned long long *>(y2_dev);
     if (kernel == LAP_KERNEL_COMPACT) {

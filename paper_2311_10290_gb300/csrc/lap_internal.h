@@ -61,7 +61,8 @@ struct LapSampleLaunch {
     unsigned long long *cnt2;
     LapDevAcc *acc;
     uint64_t step_limit;
-    int block;
+    int block;                   // threads per block; 0 = pick_block()
+    int num_sms;
     unsigned long long *y1_out;  // optional [count]: Y1 of sample first+q at q
     unsigned long long *y2_out;  // optional [count]: Y2 of sample first+q at q
     uint64_t slot_bytes;         // compact kernel: bytes of one slot (state + stack)
@@ -74,6 +75,17 @@ struct LapSampleLaunch {
 cudaError_t lap_launch_sample(const LapSampleLaunch &p, cudaStream_t st);
 // sampler_compact.cu
 cudaError_t lap_launch_sample_compact(const LapSampleLaunch &p, cudaStream_t st);
+
+// Threads per block for `lanes` persistent lanes: the smallest warp multiple
+// (up to 256) that keeps at most 16 blocks per SM, so that the blocks, and
+// the lanes with them, spread evenly over all SMs.
+inline int lap_pick_block(uint64_t lanes, int num_sms)
+{
+    int block = 32;
+    const uint64_t sms = num_sms > 0 ? (uint64_t)num_sms : 1ull;
+    while (block < 256 && lanes > 16ull * sms * (uint64_t)block) block *= 2;
+    return block;
+}
 
 enum LapKernel : int { LAP_KERNEL_WIDE = 1, LAP_KERNEL_COMPACT = 2 };
 

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
 cudaError_t lap_launch_sample(const LapSampleLaunch &p, cudaStream_t st)
 {
     if (p.count == 0 || p.slots == 0) return cudaSuccess;
-    int block = p.block > 0 ? p.block : 128;
+    int block = p.block > 0 ? p.block : lap_pick_block(p.slots, p.num_sms);
     uint64_t lanes = p.slots;
     uint64_t grid = (lanes + block - 1) / block;
     lewalk_kernel<<<(unsigned)grid, block, 0, st>>>(p);

@@ -38,18 +38,18 @@ constexpr uint32_t kKMax = 31u;
 constexpr int kEntryShift = 27;
 constexpr uint32_t kNodeMask = (1u << kEntryShift) - 1u;
 
+// Phases of a lane.  Each loop iteration issues at most one round of
+// dependent loads per lane; the *_IMMEDIATE phases are transitions that need
+// no load and run in the same iteration.
 enum Phase : uint32_t {
     P_CLAIM = 0,
-    P_SCAN,      // pq = 16 state bytes at s & ~15
-    P_DRAW,      // pb = row record of the head h
-    P_MOVE,      // pb = column entry chosen at h
-    P_STEP,      // pa = state byte of x, pb = row record of x
-    P_USTART,
-    P_UDRAW,
-    P_UMOVE,
-    P_PISTART,
-    P_PIDRAW,
-    P_PIMOVE,
+    P_WALK,                // pa = state byte of the head h, pb = row record of h
+    P_SCAN,                // pq = 16 state bytes at s & ~15
+    P_USTART_IMMEDIATE,
+    P_UWALK,               // pb = row record of u (uniform-start walk)
+    P_PISTART_IMMEDIATE,
+    P_PIWALK,              // pb = row record of u (pi-start walk)
+    P_FINISH_IMMEDIATE,
     P_DONE
 };
 
@@ -64,16 +64,17 @@ __device__ __forceinline__ uint64_t ld_row(const int2 *rowinfo, int32_t u)
 __device__ __forceinline__ int32_t row_off(uint64_t r) { return (int32_t)(uint32_t)r; }
 __device__ __forceinline__ uint32_t row_deg(uint64_t r) { return (uint32_t)(r >> 32); }
 
-// Bit b of the result is set when byte b of the 16 bytes is not InTree.
+// Bit b of the result is set when byte b of the 16 bytes is not InTree
+// (InTree bytes have top bits == epoch | InTree).  Per 4-byte word: SIMD byte
+// compare, then bit 7 of each byte gathered into 4 bits by one multiply.
+__device__ __forceinline__ uint32_t gather4(uint32_t eq) { return ((((eq >> 7) & 0x01010101u) * 0x01020408u) >> 24) & 0xFu; }
 __device__ __forceinline__ uint32_t not_tree_mask(ulonglong2 q, uint32_t ep)
 {
-    uint32_t m = 0;
-#pragma unroll
-    for (int b = 0; b < 16; ++b) {
-        const uint32_t byte = (uint32_t)(((b < 8 ? q.x : q.y) >> (8 * (b & 7))) & 0xFFu);
-        m |= (b_tree(byte, ep) ? 0u : 1u) << b;
-    }
-    return m;
+    const uint32_t want = (ep | kBTree) * 0x01010101u;
+    const uint32_t w0 = (uint32_t)q.x, w1 = (uint32_t)(q.x >> 32), w2 = (uint32_t)q.y, w3 = (uint32_t)(q.y >> 32);
+    const uint32_t t = gather4(__vcmpeq4(w0 & 0xC0C0C0C0u, want)) | (gather4(__vcmpeq4(w1 & 0xC0C0C0C0u, want)) << 4) |
+                       (gather4(__vcmpeq4(w2 & 0xC0C0C0C0u, want)) << 8) | (gather4(__vcmpeq4(w3 & 0xC0C0C0C0u, want)) << 12);
+    return ~t & 0xFFFFu;
 }
 
 // Withdraws a partly run sample: subtracts the k - 1 repeat visits every
@@ -112,8 +113,7 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
     uint32_t phase = P_CLAIM;
     uint32_t i = 0;
     int32_t s = 0;            // scan position (Alg. 2's id ordering)
-    int32_t h = 0;            // head of the walk
-    uint32_t kh = 0;          // draws at h so far
+    int32_t h = 0;            // head of the walk / current node of an absorbed walk
     uint32_t sp = 0;          // stack depth
     uint64_t pa = 0, pb = 0;
     ulonglong2 pq = make_ulonglong2(0, 0);
@@ -122,119 +122,109 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
     unsigned int bad = 0;
 
     while (phase != P_DONE) {
-        if (phase == P_MOVE) {
-            const int32_t w = (int32_t)(uint32_t)pb;
-            const uint32_t kn = kh + 1u;
-            if (kn > kKMax || sp >= cap) {
-                withdraw_sample(st, n, ep, p.rep1);
-                const unsigned int slot_ix = atomicAdd(&p.acc->ovf_count, 1u);
-                if (slot_ix < p.count) p.ovf_ids[slot_ix] = i;
-                phase = P_CLAIM;
+        if (phase == P_WALK) {
+            // One Wilson step per iteration, so walking lanes stay converged.
+            const uint32_t b = (uint32_t)pa;
+            if (b_tree(b, ep)) {
+                // Alg. 2 retrace: the loop-erased path on the stack joins the tree
+                // (draw counts kept in the byte, see withdraw_sample).
+                while (sp) {
+                    const uint32_t e = stk[--sp];
+                    st[e & kNodeMask] = (uint8_t)(ep | kBTree | (e >> kEntryShift));
+                }
+                ++s;
+                if (s < n) { pq = *reinterpret_cast<const ulonglong2 *>(st + (s & ~15)); phase = P_SCAN; }
+                else phase = P_USTART_IMMEDIATE;
+                if (phase != P_USTART_IMMEDIATE) continue;
+            } else {
+                if (b_path(b, ep)) {
+                    // Loop closed at h: erase the nodes above h and h's own entry.
+                    uint32_t e, node;
+                    do {
+                        e = stk[--sp];
+                        node = e & kNodeMask;
+                        if ((int32_t)node != h) st[node] = (uint8_t)(ep | (e >> kEntryShift));
+                    } while ((int32_t)node != h);
+                }
+                const uint32_t kh = b_k(b, ep);
+                const uint64_t r = lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1);
+                const int32_t w = __ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
+                const uint32_t kn = kh + 1u;
+                if (kn > kKMax || sp >= cap) {
+                    withdraw_sample(st, n, ep, p.rep1);
+                    const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
+                    if (ix < p.count) p.ovf_ids[ix] = i;
+                    phase = P_CLAIM;
+                    continue;
+                }
+                stk[sp++] = (uint32_t)h | (kn << kEntryShift);
+                st[h] = (uint8_t)(ep | kBPath | kn);
+                if (kh) atomicAdd(&p.rep1[h], 1ull);
+                if (++y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
+                h = w;
+                pa = st[w];
+                pb = ld_row(rowinfo, w);
                 continue;
             }
-            stk[sp++] = (uint32_t)h | (kn << kEntryShift);
-            st[h] = (uint8_t)(ep | kBPath | kn);
-            if (kh) atomicAdd(&p.rep1[h], 1ull);
-            if (++y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
-            h = w;
-            pa = st[w];
-            pb = ld_row(rowinfo, w);
-            phase = P_STEP;
-        } else if (phase == P_STEP || phase == P_DRAW) {
-            bool draw = true;
-            if (phase == P_STEP) {
-                const uint32_t b = (uint32_t)pa;
-                if (b_tree(b, ep)) {
-                    // Alg. 2 retrace: the loop-erased path on the stack joins the tree
-                    // (draw counts kept in the byte, see withdraw_sample).
-                    while (sp) {
-                        const uint32_t e = stk[--sp];
-                        st[e & kNodeMask] = (uint8_t)(ep | kBTree | (e >> kEntryShift));
-                    }
-                    draw = false;
-                    ++s;
-                    if (s < n) {
-                        pq = *reinterpret_cast<const ulonglong2 *>(st + (s & ~15));
-                        phase = P_SCAN;
-                    } else {
-                        phase = P_USTART;
-                    }
-                } else {
-                    if (b_path(b, ep)) {
-                        // Loop closed at h: erase the nodes above h and h's own entry.
-                        uint32_t e, node;
-                        do {
-                            e = stk[--sp];
-                            node = e & kNodeMask;
-                            if ((int32_t)node != h) st[node] = (uint8_t)(ep | (e >> kEntryShift));
-                        } while ((int32_t)node != h);
-                    }
-                    kh = b_k(b, ep);
-                }
-            }
-            if (draw) {
-                const uint64_t r = lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1);
-                pb = (uint64_t)(uint32_t)__ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
-                phase = P_MOVE;
-            }
-        } else if (phase == P_SCAN) {
+        }
+        if (phase == P_SCAN) {
             const int32_t base = s & ~15;
             uint32_t m = not_tree_mask(pq, ep) & (0xFFFFu << (s - base));
             if (n - base < 16) m &= (1u << (n - base)) - 1u;
             if (m) {
                 s = base + __ffs(m) - 1;
                 h = s;
-                const uint32_t b = (uint32_t)(((s - base < 8 ? pq.x : pq.y) >> (8 * ((s - base) & 7))) & 0xFFu);
-                kh = b_k(b, ep);
+                pa = (((s - base) < 8 ? pq.x : pq.y) >> (8 * ((s - base) & 7))) & 0xFFu;
                 pb = ld_row(rowinfo, h);
-                phase = P_DRAW;
-            } else {
-                s = base + 16;
-                if (s < n) pq = *reinterpret_cast<const ulonglong2 *>(st + s);
-                else phase = P_USTART;
+                phase = P_WALK;
+                continue;
             }
-        } else if (phase == P_UDRAW) {
-            ++t;
-            const uint64_t r = lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1);
-            pb = (uint64_t)(uint32_t)__ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
-            phase = P_UMOVE;
-            if (t > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; }
-        } else if (phase == P_UMOVE) {
-            h = (int32_t)(uint32_t)pb;
-            if (h == v) phase = P_PISTART;
-            else { atomicAdd(&p.cnt2[h], 1ull); pb = ld_row(rowinfo, h); phase = P_UDRAW; }
-        } else if (phase == P_PIDRAW) {
-            ++y2;
-            const uint64_t r = lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1);
-            pb = (uint64_t)(uint32_t)__ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
-            phase = P_PIMOVE;
-            if (y2 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; }
-        } else if (phase == P_PIMOVE) {
-            h = (int32_t)(uint32_t)pb;
-            if (h == v) {
-                acc1 += y1;
-                acc2 += y2;
-                if (p.y1_out) { p.y1_out[i - p.first] = y1; p.y2_out[i - p.first] = y2; }
-                phase = P_CLAIM;
-            } else {
-                pb = ld_row(rowinfo, h);
-                phase = P_PIDRAW;
-            }
-        } else if (phase == P_USTART) {
+            s = base + 16;
+            if (s < n) { pq = *reinterpret_cast<const ulonglong2 *>(st + s); continue; }
+            phase = P_USTART_IMMEDIATE;
+        }
+        if (phase == P_USTART_IMMEDIATE) {
+            // Alg. 2: uniformly sample s in V; walk until v, counting passes.
             t = 0;
             const uint64_t r = lap::philox_r64(0u, 0u, i, 1u, key0, key1);
             h = (int32_t)lap::below(r, (uint64_t)n);
-            if (h == v) phase = P_PISTART;
-            else { atomicAdd(&p.cnt2[h], 1ull); pb = ld_row(rowinfo, h); phase = P_UDRAW; }
-        } else if (phase == P_PISTART) {
+            if (h != v) { atomicAdd(&p.cnt2[h], 1ull); pb = ld_row(rowinfo, h); phase = P_UWALK; continue; }
+            phase = P_PISTART_IMMEDIATE;
+        }
+        if (phase == P_UWALK) {
+            ++t;
+            const uint64_t r = lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1);
+            h = __ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
+            if (t > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
+            if (h != v) { atomicAdd(&p.cnt2[h], 1ull); pb = ld_row(rowinfo, h); continue; }
+            phase = P_PISTART_IMMEDIATE;
+        }
+        if (phase == P_PISTART_IMMEDIATE) {
+            // Alg. 4: s ~ pi is the head of a uniformly drawn arc.
             y2 = 0;
             const uint64_t r = lap::philox_r64(0u, 0u, i, 2u, key0, key1);
-            pb = (uint64_t)(uint32_t)__ldg(col + (int64_t)lap::below(r, (uint64_t)p.g.arcs));
-            phase = P_PIMOVE;
-        } else {  // P_CLAIM
-            if (bad) { phase = P_DONE; break; }
+            h = __ldg(col + (int64_t)lap::below(r, (uint64_t)p.g.arcs));
+            if (h != v) { pb = ld_row(rowinfo, h); phase = P_PIWALK; continue; }
+            phase = P_FINISH_IMMEDIATE;
+        }
+        if (phase == P_PIWALK) {
+            ++y2;
+            const uint64_t r = lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1);
+            h = __ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
+            if (y2 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
+            if (h != v) { pb = ld_row(rowinfo, h); continue; }
+            phase = P_FINISH_IMMEDIATE;
+        }
+        if (phase == P_FINISH_IMMEDIATE) {
+            acc1 += y1;
+            acc2 += y2;
+            if (p.y1_out) { p.y1_out[i - p.first] = y1; p.y2_out[i - p.first] = y2; }
+            phase = P_CLAIM;
+        }
+        if (phase == P_CLAIM) {
+            if (bad) break;
             const unsigned int q = atomicAdd(&p.acc->claim, 1u);
-            if (q >= p.count) { phase = P_DONE; break; }
+            if (q >= p.count) break;
             i = p.first + q;
             ep ^= kBEpoch;
             st[v] = (uint8_t)(ep | kBTree);
@@ -256,7 +246,7 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
 cudaError_t lap_launch_sample_compact(const LapSampleLaunch &p, cudaStream_t st)
 {
     if (p.count == 0 || p.slots == 0) return cudaSuccess;
-    int block = p.block > 0 ? p.block : 128;
+    int block = p.block > 0 ? p.block : lap_pick_block(p.slots, p.num_sms);
     uint64_t grid = (p.slots + block - 1) / block;
     lewalk_compact_kernel<<<(unsigned)grid, block, 0, st>>>(p);
     return cudaGetLastError();
