@@ -77,6 +77,51 @@ __device__ __forceinline__ uint32_t not_tree_mask(ulonglong2 q, uint32_t ep)
     return ~t & 0xFFFFu;
 }
 
+// Marks every node on the stack InTree, keeping its draw count.  The order
+// does not matter, so entries are read 16 at a time with independent vector
+// loads (the stack is 16-byte aligned) instead of one dependent pop each.
+__device__ __forceinline__ void commit_path(uint8_t *st, const uint32_t *stk, uint32_t sp, uint32_t ep)
+{
+    uint32_t j = 0;
+    for (; j + 16u <= sp; j += 16u) {
+        uint4 e[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e[q] = *reinterpret_cast<const uint4 *>(stk + j + 4u * q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            st[e[q].x & kNodeMask] = (uint8_t)(ep | kBTree | (e[q].x >> kEntryShift));
+            st[e[q].y & kNodeMask] = (uint8_t)(ep | kBTree | (e[q].y >> kEntryShift));
+            st[e[q].z & kNodeMask] = (uint8_t)(ep | kBTree | (e[q].z >> kEntryShift));
+            st[e[q].w & kNodeMask] = (uint8_t)(ep | kBTree | (e[q].w >> kEntryShift));
+        }
+    }
+    for (; j < sp; ++j) {
+        const uint32_t e = stk[j];
+        st[e & kNodeMask] = (uint8_t)(ep | kBTree | (e >> kEntryShift));
+    }
+}
+
+// Loop closed at head h (h is on the stack): erases the entries above h
+// (OnPath cleared, draw counts kept) and removes h's own entry; returns the
+// new depth.  Reads the stack top down, one aligned group of 4 per load.
+__device__ __forceinline__ uint32_t erase_loop(uint8_t *st, const uint32_t *stk, uint32_t sp, uint32_t ep, uint32_t h)
+{
+    for (;;) {
+        const uint32_t top = sp - 1u;
+        const uint32_t g0 = top & ~3u;
+        const uint4 e4 = *reinterpret_cast<const uint4 *>(stk + g0);
+        const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+        for (int q = 3; q >= 0; --q) {
+            if ((uint32_t)q > top - g0) continue;
+            const uint32_t node = e[q] & kNodeMask;
+            if (node == h) return g0 + (uint32_t)q;
+            st[node] = (uint8_t)(ep | (e[q] >> kEntryShift));
+        }
+        sp = g0;
+    }
+}
+
 // Withdraws a partly run sample: subtracts the k - 1 repeat visits every
 // node of the sample has contributed and marks all bytes "current epoch,
 // untouched", so that the next sample (next epoch) reads them as stale.
@@ -128,24 +173,14 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
             if (b_tree(b, ep)) {
                 // Alg. 2 retrace: the loop-erased path on the stack joins the tree
                 // (draw counts kept in the byte, see withdraw_sample).
-                while (sp) {
-                    const uint32_t e = stk[--sp];
-                    st[e & kNodeMask] = (uint8_t)(ep | kBTree | (e >> kEntryShift));
-                }
+                commit_path(st, stk, sp, ep);
+                sp = 0;
                 ++s;
                 if (s < n) { pq = *reinterpret_cast<const ulonglong2 *>(st + (s & ~15)); phase = P_SCAN; }
                 else phase = P_USTART_IMMEDIATE;
                 if (phase != P_USTART_IMMEDIATE) continue;
             } else {
-                if (b_path(b, ep)) {
-                    // Loop closed at h: erase the nodes above h and h's own entry.
-                    uint32_t e, node;
-                    do {
-                        e = stk[--sp];
-                        node = e & kNodeMask;
-                        if ((int32_t)node != h) st[node] = (uint8_t)(ep | (e >> kEntryShift));
-                    } while ((int32_t)node != h);
-                }
+                if (b_path(b, ep)) sp = erase_loop(st, stk, sp, ep, (uint32_t)h);
                 const uint32_t kh = b_k(b, ep);
                 const uint64_t r = lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1);
                 const int32_t w = __ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
