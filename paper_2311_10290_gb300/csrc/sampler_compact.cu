@@ -44,23 +44,54 @@ constexpr uint32_t kNodeMask = (1u << kEntryShift) - 1u;
 enum Phase : uint32_t {
     P_CLAIM = 0,
     P_WALK,                // pa = state byte of the head h, pb = row record of h
-    P_SCAN,                // pq = 16 state bytes at s & ~15
+    P_SCAN,                // pq = 16 state bytes at `chunk`
     P_USTART_IMMEDIATE,
-    P_UWALK,               // pb = row record of u (uniform-start walk)
+    P_UWALK,               // pb = row record of the walk's node (uniform start)
     P_PISTART_IMMEDIATE,
-    P_PIWALK,              // pb = row record of u (pi-start walk)
-    P_FINISH_IMMEDIATE,
-    P_DONE
+    P_PIWALK,              // pb = row record of the walk's node (pi start)
+    P_FINISH_IMMEDIATE
 };
+
+// L2 eviction policies (sm_80+ createpolicy) and loads/stores that use them.
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint32_t ld_state(const uint8_t *a, uint64_t pol)
+{
+    uint16_t v;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(pol) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_state(uint8_t *a, uint32_t v, uint64_t pol)
+{
+    asm volatile("st.global.L1::no_allocate.L2::cache_hint.u8 [%0], %1, %2;" ::"l"(a), "h"((uint16_t)v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ int32_t ld_col(const int32_t *a, uint64_t pol)
+{
+    int32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint64_t ld_row(const int2 *rowinfo, int32_t u, uint64_t pol)
+{
+    uint64_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(rowinfo + u), "l"(pol));
+    return v;
+}
 
 __device__ __forceinline__ bool b_current(uint32_t b, uint32_t ep) { return (b & kBEpoch) == ep; }
 __device__ __forceinline__ bool b_tree(uint32_t b, uint32_t ep) { return b_current(b, ep) && (b & kBTree); }
 __device__ __forceinline__ bool b_path(uint32_t b, uint32_t ep) { return b_current(b, ep) && (b & kBPath); }
 __device__ __forceinline__ uint32_t b_k(uint32_t b, uint32_t ep) { return b_current(b, ep) ? (b & kBK) : 0u; }
-__device__ __forceinline__ uint64_t ld_row(const int2 *rowinfo, int32_t u)
-{
-    return (uint64_t)__ldg(reinterpret_cast<const unsigned long long *>(rowinfo) + u);
-}
 __device__ __forceinline__ int32_t row_off(uint64_t r) { return (int32_t)(uint32_t)r; }
 __device__ __forceinline__ uint32_t row_deg(uint64_t r) { return (uint32_t)(r >> 32); }
 
@@ -153,37 +184,40 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
     const uint32_t cap = p.stack_cap;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
     const uint64_t limit = p.step_limit;
+    // The graph (row records, columns) should stay in L2; the per-sample
+    // state bytes are touched about once per step and should not evict it.
+    const uint64_t keep = policy_evict_last();
+    const uint64_t stream = policy_evict_first();
 
     uint32_t ep = p.slot_epoch[slot] ? kBEpoch : 0u;
     uint32_t phase = P_CLAIM;
     uint32_t i = 0;
     int32_t s = 0;            // scan position (Alg. 2's id ordering)
+    int32_t chunk = -1;       // base of the 16 state bytes held in pq (-1: none)
     int32_t h = 0;            // head of the walk / current node of an absorbed walk
     uint32_t sp = 0;          // stack depth
-    uint64_t pa = 0, pb = 0;
+    uint32_t e0 = 0;          // stack entry 0 (the walk's start), kept in a register
+    uint32_t pa = 0;          // state byte of h (in flight)
+    uint64_t pb = 0;          // row record of h (in flight)
     ulonglong2 pq = make_ulonglong2(0, 0);
     uint64_t y1 = 0, t = 0, y2 = 0;
     unsigned long long acc1 = 0, acc2 = 0;
     unsigned int bad = 0;
 
-    while (phase != P_DONE) {
+    for (;;) {
         if (phase == P_WALK) {
             // One Wilson step per iteration, so walking lanes stay converged.
-            const uint32_t b = (uint32_t)pa;
-            if (b_tree(b, ep)) {
-                // Alg. 2 retrace: the loop-erased path on the stack joins the tree
-                // (draw counts kept in the byte, see withdraw_sample).
-                commit_path(st, stk, sp, ep);
-                sp = 0;
-                ++s;
-                if (s < n) { pq = *reinterpret_cast<const ulonglong2 *>(st + (s & ~15)); phase = P_SCAN; }
-                else phase = P_USTART_IMMEDIATE;
-                if (phase != P_USTART_IMMEDIATE) continue;
-            } else {
+            // The column entry for draw index 0 (the usual case: the first
+            // visit of h) is requested as soon as h's row record arrives,
+            // overlapping the state-byte read; it is redone if h was drawn before.
+            const int32_t off = row_off(pb);
+            const uint32_t deg = row_deg(pb);
+            int32_t w = ld_col(col + off + (int64_t)lap::below(lap::philox_r64((uint32_t)h, 0u, i, 0u, key0, key1), deg), keep);
+            const uint32_t b = pa;
+            if (!b_tree(b, ep)) {
                 if (b_path(b, ep)) sp = erase_loop(st, stk, sp, ep, (uint32_t)h);
                 const uint32_t kh = b_k(b, ep);
-                const uint64_t r = lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1);
-                const int32_t w = __ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
+                if (kh) w = ld_col(col + off + (int64_t)lap::below(lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1), deg), keep);
                 const uint32_t kn = kh + 1u;
                 if (kn > kKMax || sp >= cap) {
                     withdraw_sample(st, n, ep, p.rep1);
@@ -192,62 +226,84 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
                     phase = P_CLAIM;
                     continue;
                 }
-                stk[sp++] = (uint32_t)h | (kn << kEntryShift);
-                st[h] = (uint8_t)(ep | kBPath | kn);
+                const uint32_t e = (uint32_t)h | (kn << kEntryShift);
+                if (sp == 0) e0 = e;
+                stk[sp++] = e;
+                st_state(st + h, ep | kBPath | kn, stream);
                 if (kh) atomicAdd(&p.rep1[h], 1ull);
                 if (++y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
                 h = w;
-                pa = st[w];
-                pb = ld_row(rowinfo, w);
+                pa = ld_state(st + w, stream);
+                pb = ld_row(rowinfo, w, keep);
                 continue;
             }
+            // h is InTree: Alg. 2's retrace adds the loop-erased path on the
+            // stack to the tree (draw counts kept, see withdraw_sample).  With
+            // sp == 0 the start came from a stale chunk and is skipped.
+            if (sp == 1) st_state(st + (e0 & kNodeMask), ep | kBTree | (e0 >> kEntryShift), stream);
+            else if (sp > 1) commit_path(st, stk, sp, ep);
+            sp = 0;
+            ++s;
+            phase = P_SCAN;
         }
         if (phase == P_SCAN) {
-            const int32_t base = s & ~15;
-            uint32_t m = not_tree_mask(pq, ep) & (0xFFFFu << (s - base));
-            if (n - base < 16) m &= (1u << (n - base)) - 1u;
-            if (m) {
-                s = base + __ffs(m) - 1;
-                h = s;
-                pa = (((s - base) < 8 ? pq.x : pq.y) >> (8 * ((s - base) & 7))) & 0xFFu;
-                pb = ld_row(rowinfo, h);
-                phase = P_WALK;
-                continue;
+            // Next start: the first node >= s not InTree, read from the chunk
+            // of 16 state bytes in registers (a chunk may be stale; the start's
+            // byte is re-read before use).
+            if (s < n) {
+                const int32_t base = s & ~15;
+                if (base != chunk) {
+                    pq = *reinterpret_cast<const ulonglong2 *>(st + base);
+                    chunk = base;
+                    continue;
+                }
+                uint32_t m = not_tree_mask(pq, ep) & (0xFFFFu << (s - base));
+                if (n - base < 16) m &= (1u << (n - base)) - 1u;
+                if (m) {
+                    s = base + __ffs(m) - 1;
+                    h = s;
+                    pa = ld_state(st + h, stream);
+                    pb = ld_row(rowinfo, h, keep);
+                    phase = P_WALK;
+                    continue;
+                }
+                s = base + 16;
+                if (s < n) {
+                    pq = *reinterpret_cast<const ulonglong2 *>(st + s);
+                    chunk = s;
+                    continue;
+                }
             }
-            s = base + 16;
-            if (s < n) { pq = *reinterpret_cast<const ulonglong2 *>(st + s); continue; }
             phase = P_USTART_IMMEDIATE;
         }
         if (phase == P_USTART_IMMEDIATE) {
             // Alg. 2: uniformly sample s in V; walk until v, counting passes.
             t = 0;
-            const uint64_t r = lap::philox_r64(0u, 0u, i, 1u, key0, key1);
-            h = (int32_t)lap::below(r, (uint64_t)n);
-            if (h != v) { atomicAdd(&p.cnt2[h], 1ull); pb = ld_row(rowinfo, h); phase = P_UWALK; continue; }
+            h = (int32_t)lap::below(lap::philox_r64(0u, 0u, i, 1u, key0, key1), (uint64_t)n);
+            if (h != v) { atomicAdd(&p.cnt2[h], 1ull); pb = ld_row(rowinfo, h, keep); phase = P_UWALK; continue; }
             phase = P_PISTART_IMMEDIATE;
         }
         if (phase == P_UWALK) {
             ++t;
             const uint64_t r = lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1);
-            h = __ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
+            h = ld_col(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)), keep);
             if (t > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
-            if (h != v) { atomicAdd(&p.cnt2[h], 1ull); pb = ld_row(rowinfo, h); continue; }
+            if (h != v) { atomicAdd(&p.cnt2[h], 1ull); pb = ld_row(rowinfo, h, keep); continue; }
             phase = P_PISTART_IMMEDIATE;
         }
         if (phase == P_PISTART_IMMEDIATE) {
             // Alg. 4: s ~ pi is the head of a uniformly drawn arc.
             y2 = 0;
-            const uint64_t r = lap::philox_r64(0u, 0u, i, 2u, key0, key1);
-            h = __ldg(col + (int64_t)lap::below(r, (uint64_t)p.g.arcs));
-            if (h != v) { pb = ld_row(rowinfo, h); phase = P_PIWALK; continue; }
+            h = ld_col(col + (int64_t)lap::below(lap::philox_r64(0u, 0u, i, 2u, key0, key1), (uint64_t)p.g.arcs), keep);
+            if (h != v) { pb = ld_row(rowinfo, h, keep); phase = P_PIWALK; continue; }
             phase = P_FINISH_IMMEDIATE;
         }
         if (phase == P_PIWALK) {
             ++y2;
             const uint64_t r = lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1);
-            h = __ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
+            h = ld_col(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)), keep);
             if (y2 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
-            if (h != v) { pb = ld_row(rowinfo, h); continue; }
+            if (h != v) { pb = ld_row(rowinfo, h, keep); continue; }
             phase = P_FINISH_IMMEDIATE;
         }
         if (phase == P_FINISH_IMMEDIATE) {
@@ -266,7 +322,7 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
             s = 0;
             sp = 0;
             y1 = 0;
-            pq = *reinterpret_cast<const ulonglong2 *>(st);
+            chunk = -1;
             phase = P_SCAN;
         }
     }
