@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ba_1m", choices=["ba_1m", "er_1000", "rmat_22", "ba_200k"])
+    ap.add_argument("--workload", default="ba_1m", choices=["ba_1m", "er_1000", "rmat_22", "ba_200k", "ba_100k"])
     ap.add_argument("--batch", type=int, default=65536, help="samples per step")
     ap.add_argument("--seed", type=int, default=20231117)
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-tta", action="store_true", help="skip the time-to-accuracy run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ws-frac", type=float, default=0.6, help="fraction of free HBM lent as Wilson state")
+    ap.add_argument("--ws-gb", type=float, default=0.0, help="cap on the Wilson-state workspace in GB (profiler runs)")
     return ap.parse_args()
 
 
@@ -75,9 +76,9 @@ def peaks():
 
 def load_graph(name):
     from paper_2311_10290_gb300 import inputs
-    if name == "ba_200k":          # small case of the same family, for profiler captures
-        g = inputs.ba(200_000, 5, seed=0)
-        g.name = "ba_n2e5_m5"
+    if name in ("ba_200k", "ba_100k"):   # smaller cases of the same family, for profiler captures
+        g = inputs.ba(200_000 if name == "ba_200k" else 100_000, 5, seed=0)
+        g.name = "ba_n%s_m5" % ("2e5" if name == "ba_200k" else "1e5")
         return g
     return {"ba_1m": inputs.ba_1m, "er_1000": inputs.er_1000, "rmat_22": inputs.rmat_22}[name]()
 
@@ -244,14 +245,17 @@ def run_ours(args, rank, world):
         dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
     g = load_graph(args.workload)
     free, _ = torch.cuda.mem_get_info()
-    G = LapGraph(g.row_ptr, g.col, workspace_bytes=int(free * args.ws_frac))
+    ws = int(free * args.ws_frac)
+    if args.ws_gb > 0:
+        ws = min(ws, int(args.ws_gb * 1e9))
+    G = LapGraph(g.row_ptr, g.col, workspace_bytes=ws)
     v = G.set_root()
     from paper_2311_10290_gb300.lap import LAP_STAT_KERNEL
     kernel_name = {1: "lewalk_kernel (8-byte state)", 2: "lewalk_compact_kernel (1-byte state)"}[G.stat(LAP_STAT_KERNEL)]
     B = args.batch
     total_steps = args.warmup + args.steps
     G.set_option(LAP_OPT_CURSOR, rank * total_steps * B)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # larger than the 126 MB L2
     out = torch.empty(g.n, dtype=torch.float64, device="cuda")
 
     def step():

@@ -59,21 +59,24 @@ __device__ __forceinline__ uint64_t policy_evict_last()
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
-__device__ __forceinline__ uint64_t policy_evict_first()
-{
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-__device__ __forceinline__ uint32_t ld_state(const uint8_t *a, uint64_t pol)
+// State bytes: default L2 priority (a sector read at one step is written at
+// the next step and again at the retrace, so it should stay in L2 meanwhile;
+// evicting it early turns those writes into partial-sector fills), no L1
+// allocation (no reuse within a lane at L1 time scales).
+__device__ __forceinline__ uint32_t ld_state(const uint8_t *a)
 {
     uint16_t v;
-    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(pol) : "memory");
+    asm volatile("ld.global.L1::no_allocate.u8 %0, [%1];" : "=h"(v) : "l"(a) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_state(uint8_t *a, uint32_t v, uint64_t pol)
+__device__ __forceinline__ void st_state(uint8_t *a, uint32_t v)
 {
-    asm volatile("st.global.L1::no_allocate.L2::cache_hint.u8 [%0], %1, %2;" ::"l"(a), "h"((uint16_t)v), "l"(pol) : "memory");
+    asm volatile("st.global.L1::no_allocate.u8 [%0], %1;" ::"l"(a), "h"((uint16_t)v) : "memory");
+}
+// Path-stack entries: kept in L2 with the graph (they are re-read at the retrace).
+__device__ __forceinline__ void st_stack(uint32_t *a, uint32_t v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
 }
 __device__ __forceinline__ int32_t ld_col(const int32_t *a, uint64_t pol)
 {
@@ -108,10 +111,31 @@ __device__ __forceinline__ uint32_t not_tree_mask(ulonglong2 q, uint32_t ep)
     return ~t & 0xFFFFu;
 }
 
+// The lane keeps the 16 state bytes at `chunk` in registers (pq) as an exact
+// copy: it is the only writer of its state, so every byte it writes inside
+// the chunk is also written into pq.  Starts found in pq need no re-read.
+__device__ __forceinline__ void pq_set(ulonglong2 &pq, int32_t chunk, uint32_t u, uint32_t b)
+{
+    const uint32_t off = u - (uint32_t)chunk;
+    if (off < 16u) {
+        const uint32_t sh = 8u * (off & 7u);
+        const unsigned long long m = ~(0xFFull << sh), v = (unsigned long long)(b & 0xFFu) << sh;
+        if (off < 8u) pq.x = (pq.x & m) | v;
+        else pq.y = (pq.y & m) | v;
+    }
+}
+
 // Marks every node on the stack InTree, keeping its draw count.  The order
 // does not matter, so entries are read 16 at a time with independent vector
 // loads (the stack is 16-byte aligned) instead of one dependent pop each.
-__device__ __forceinline__ void commit_path(uint8_t *st, const uint32_t *stk, uint32_t sp, uint32_t ep)
+__device__ __forceinline__ void commit_one(uint8_t *st, uint32_t e, uint32_t ep, ulonglong2 &pq, int32_t chunk)
+{
+    const uint32_t b = ep | kBTree | (e >> kEntryShift);
+    st[e & kNodeMask] = (uint8_t)b;
+    pq_set(pq, chunk, e & kNodeMask, b);
+}
+__device__ __forceinline__ void commit_path(uint8_t *st, const uint32_t *stk, uint32_t sp, uint32_t ep,
+                                            ulonglong2 &pq, int32_t chunk)
 {
     uint32_t j = 0;
     for (; j + 16u <= sp; j += 16u) {
@@ -120,22 +144,20 @@ __device__ __forceinline__ void commit_path(uint8_t *st, const uint32_t *stk, ui
         for (int q = 0; q < 4; ++q) e[q] = *reinterpret_cast<const uint4 *>(stk + j + 4u * q);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            st[e[q].x & kNodeMask] = (uint8_t)(ep | kBTree | (e[q].x >> kEntryShift));
-            st[e[q].y & kNodeMask] = (uint8_t)(ep | kBTree | (e[q].y >> kEntryShift));
-            st[e[q].z & kNodeMask] = (uint8_t)(ep | kBTree | (e[q].z >> kEntryShift));
-            st[e[q].w & kNodeMask] = (uint8_t)(ep | kBTree | (e[q].w >> kEntryShift));
+            commit_one(st, e[q].x, ep, pq, chunk);
+            commit_one(st, e[q].y, ep, pq, chunk);
+            commit_one(st, e[q].z, ep, pq, chunk);
+            commit_one(st, e[q].w, ep, pq, chunk);
         }
     }
-    for (; j < sp; ++j) {
-        const uint32_t e = stk[j];
-        st[e & kNodeMask] = (uint8_t)(ep | kBTree | (e >> kEntryShift));
-    }
+    for (; j < sp; ++j) commit_one(st, stk[j], ep, pq, chunk);
 }
 
 // Loop closed at head h (h is on the stack): erases the entries above h
 // (OnPath cleared, draw counts kept) and removes h's own entry; returns the
 // new depth.  Reads the stack top down, one aligned group of 4 per load.
-__device__ __forceinline__ uint32_t erase_loop(uint8_t *st, const uint32_t *stk, uint32_t sp, uint32_t ep, uint32_t h)
+__device__ __forceinline__ uint32_t erase_loop(uint8_t *st, const uint32_t *stk, uint32_t sp, uint32_t ep, uint32_t h,
+                                               ulonglong2 &pq, int32_t chunk)
 {
     for (;;) {
         const uint32_t top = sp - 1u;
@@ -148,6 +170,7 @@ __device__ __forceinline__ uint32_t erase_loop(uint8_t *st, const uint32_t *stk,
             const uint32_t node = e[q] & kNodeMask;
             if (node == h) return g0 + (uint32_t)q;
             st[node] = (uint8_t)(ep | (e[q] >> kEntryShift));
+            pq_set(pq, chunk, node, ep | (e[q] >> kEntryShift));
         }
         sp = g0;
     }
@@ -184,10 +207,8 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
     const uint32_t cap = p.stack_cap;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
     const uint64_t limit = p.step_limit;
-    // The graph (row records, columns) should stay in L2; the per-sample
-    // state bytes are touched about once per step and should not evict it.
+    // The graph (row records, columns) and the path stacks should stay in L2.
     const uint64_t keep = policy_evict_last();
-    const uint64_t stream = policy_evict_first();
 
     uint32_t ep = p.slot_epoch[slot] ? kBEpoch : 0u;
     uint32_t phase = P_CLAIM;
@@ -215,7 +236,7 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
             int32_t w = ld_col(col + off + (int64_t)lap::below(lap::philox_r64((uint32_t)h, 0u, i, 0u, key0, key1), deg), keep);
             const uint32_t b = pa;
             if (!b_tree(b, ep)) {
-                if (b_path(b, ep)) sp = erase_loop(st, stk, sp, ep, (uint32_t)h);
+                if (b_path(b, ep)) sp = erase_loop(st, stk, sp, ep, (uint32_t)h, pq, chunk);
                 const uint32_t kh = b_k(b, ep);
                 if (kh) w = ld_col(col + off + (int64_t)lap::below(lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1), deg), keep);
                 const uint32_t kn = kh + 1u;
@@ -228,28 +249,32 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
                 }
                 const uint32_t e = (uint32_t)h | (kn << kEntryShift);
                 if (sp == 0) e0 = e;
-                stk[sp++] = e;
-                st_state(st + h, ep | kBPath | kn, stream);
+                st_stack(stk + sp, e, keep);
+                ++sp;
+                st_state(st + h, ep | kBPath | kn);
+                pq_set(pq, chunk, (uint32_t)h, ep | kBPath | kn);
                 if (kh) atomicAdd(&p.rep1[h], 1ull);
                 if (++y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
                 h = w;
-                pa = ld_state(st + w, stream);
+                pa = ld_state(st + w);
                 pb = ld_row(rowinfo, w, keep);
                 continue;
             }
             // h is InTree: Alg. 2's retrace adds the loop-erased path on the
-            // stack to the tree (draw counts kept, see withdraw_sample).  With
-            // sp == 0 the start came from a stale chunk and is skipped.
-            if (sp == 1) st_state(st + (e0 & kNodeMask), ep | kBTree | (e0 >> kEntryShift), stream);
-            else if (sp > 1) commit_path(st, stk, sp, ep);
+            // stack to the tree (draw counts kept, see withdraw_sample).
+            if (sp == 1) {
+                st_state(st + (e0 & kNodeMask), ep | kBTree | (e0 >> kEntryShift));
+                pq_set(pq, chunk, e0 & kNodeMask, ep | kBTree | (e0 >> kEntryShift));
+            } else if (sp > 1) {
+                commit_path(st, stk, sp, ep, pq, chunk);
+            }
             sp = 0;
             ++s;
             phase = P_SCAN;
         }
         if (phase == P_SCAN) {
-            // Next start: the first node >= s not InTree, read from the chunk
-            // of 16 state bytes in registers (a chunk may be stale; the start's
-            // byte is re-read before use).
+            // Next start: the first node >= s not InTree, read from the exact
+            // copy of the 16 state bytes at `chunk` held in pq.
             if (s < n) {
                 const int32_t base = s & ~15;
                 if (base != chunk) {
@@ -262,7 +287,7 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
                 if (m) {
                     s = base + __ffs(m) - 1;
                     h = s;
-                    pa = ld_state(st + h, stream);
+                    pa = (uint32_t)((((s - base) < 8 ? pq.x : pq.y) >> (8 * ((s - base) & 7))) & 0xFFu);
                     pb = ld_row(rowinfo, h, keep);
                     phase = P_WALK;
                     continue;
