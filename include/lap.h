@@ -209,6 +209,53 @@ lap_status lap_hops(lap_graph *g, int32_t *out, int on_device);
 /* Number of nodes, arcs (2m) and the current root (-1 when unset). */
 lap_status lap_graph_info(const lap_graph *g, int32_t *n, int64_t *arcs, int32_t *root);
 
+/*
+ * lap_sample_static - the sampler for callers that must not allocate device
+ * memory.  The paper has no counterpart: this entry point exists for code that
+ * runs where cudaMalloc is unavailable or forbidden, such as a plug-in whose
+ * host application owns all device memory through its own pool, a real-time
+ * service that must keep a fixed memory footprint after start-up, or a thread
+ * that must not trigger the device-wide synchronisation cudaMalloc/cudaFree can
+ * cause.  It computes exactly what lap_graph_create + lap_set_root +
+ * lap_sample + lap_counts compute for the same graph, root, seed and sample ids,
+ * but takes the graph and the outputs as caller-owned device buffers and keeps
+ * all of its scratch (row records, counters, per-sample Wilson state) in one
+ * fixed array of lap_static_scratch_bytes() = 32 MiB that the library holds
+ * on every GPU that loads it, until the process exits.  It never calls
+ * cudaMalloc, cudaFree or any allocating library routine.
+ *
+ *   n, row_ptr, col_idx  CSR as for lap_graph_create, in DEVICE memory
+ *                        (not validated here: pass a valid, connected graph)
+ *   root                 landmark v, or < 0 for the highest-degree node
+ *   seed, first_id       Philox seed and first sample id; ids
+ *                        [first_id, first_id + n_samples) are drawn
+ *   cnt1, cnt2           device uint64[n], overwritten with the visit and
+ *                        uniform-walk pass counts (as lap_counts)
+ *   sums2                device uint64[2], overwritten with {sum Y1, sum Y2}
+ *   cuda_stream          stream to run on (NULL: legacy default stream)
+ *
+ * The graph must fit the scratch with at least one sample in flight
+ * (24 n + 512 bytes, so n up to about 1.39 million): larger graphs return
+ * LAP_ERR_TOO_LARGE.  Smaller graphs keep up to (32 MiB - 16 n) / (8 n)
+ * samples in flight.  The call
+ * synchronises the stream before returning.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make it before any stream capture.  All calls share the one array
+ * and each clears what it needs, so calls that overlap on the GPU (other
+ * streams or threads) race and give wrong results: serialise them.
+ * Errors (LAP_ERR_INVALID_ARG, LAP_ERR_TOO_LARGE, LAP_ERR_STEP_LIMIT,
+ * LAP_ERR_CUDA) are explained by lap_static_last_error().
+ */
+lap_status lap_sample_static(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32_t root,
+                             uint64_t seed, uint64_t first_id, uint64_t n_samples,
+                             uint64_t *cnt1, uint64_t *cnt2, uint64_t *sums2, void *cuda_stream);
+
+/* Size in bytes of the fixed scratch array used by lap_sample_static. */
+uint64_t lap_static_scratch_bytes(void);
+
+/* One-line description of the last lap_sample_static error of this thread. */
+const char *lap_static_last_error(void);
+
 /* One-line description of the last error on this handle (or of the last
  * failed lap_graph_create when g is NULL).  Never NULL. */
 const char *lap_last_error(const lap_graph *g);

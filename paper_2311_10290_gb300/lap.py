@@ -69,6 +69,9 @@ def library():
         "lap_get_stat": (i32, [vp, i32, ctypes.POINTER(i64)]),
         "lap_graph_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]),
         "lap_last_error": (ctypes.c_char_p, [vp]),
+        "lap_sample_static": (i32, [i32, vp, vp, i32, u64, u64, u64, vp, vp, vp, vp]),
+        "lap_static_scratch_bytes": (u64, []),
+        "lap_static_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -207,6 +210,27 @@ def lap_graph_info(h):
     n, a, r = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
     _check(library().lap_graph_info(h, ctypes.byref(n), ctypes.byref(a), ctypes.byref(r)), h)
     return n.value, a.value, r.value
+
+
+def lap_static_scratch_bytes():
+    return library().lap_static_scratch_bytes()
+
+
+def lap_static_last_error():
+    m = library().lap_static_last_error()
+    return m.decode() if m else ""
+
+
+def lap_sample_static(n, row_ptr, col_idx, root, seed, first_id, n_samples, cnt1, cnt2, sums2, stream=0):
+    """Allocation-free sampler (see include/lap.h).  row_ptr/col_idx: int32
+    CUDA tensors; cnt1/cnt2: 64-bit CUDA tensors of n entries; sums2: 64-bit
+    CUDA tensor of 2 entries; stream: a cudaStream_t as an integer."""
+    st = library().lap_sample_static(int(n), ctypes.c_void_p(row_ptr.data_ptr()), ctypes.c_void_p(col_idx.data_ptr()),
+                                     int(root), int(seed), int(first_id), int(n_samples),
+                                     ctypes.c_void_p(cnt1.data_ptr()), ctypes.c_void_p(cnt2.data_ptr()),
+                                     ctypes.c_void_p(sums2.data_ptr()), ctypes.c_void_p(int(stream)))
+    if st != 0:
+        raise LapError(st, lap_static_last_error())
 
 
 # ------------------------------------------------------------ convenience
