@@ -49,6 +49,9 @@ def _load():
             lib.oracle_finalize.restype = None
             lib.oracle_finalize.argtypes = [ctypes.c_int32, p, ctypes.c_int32, ctypes.c_uint64,
                                             p, p, ctypes.c_uint64, ctypes.c_uint64, p, p, p]
+            lib.oracle_sample_cv.restype = ctypes.c_int
+            lib.oracle_sample_cv.argtypes = [ctypes.c_int32, p, p, ctypes.c_int32, ctypes.c_uint64,
+                                             ctypes.c_uint64, ctypes.c_uint64, p, p, p, p, p, p, p, p, p, p]
             lib.oracle_philox_block.restype = None
             lib.oracle_philox_block.argtypes = [p, p, p]
             _lib = lib
@@ -107,6 +110,33 @@ def sample(row_ptr, col, v, seed, first, count, order=None, keep_per_sample=True
     if keep_tree:
         out.tree = tree.reshape(count, n)
     return out
+
+
+def sample_cv(row_ptr, col, v, seed, first, count, h1=None, h2=None):
+    """oracle.sample plus the control-variate sums: returns (Counts, a1, a2, p2,
+    m2 per sample).  h1, h2: int64 potentials (or None)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    n = rp.size - 1
+    out = Counts(n)
+    y1 = np.zeros(count, dtype=np.uint64)
+    y2 = np.zeros(count, dtype=np.uint64)
+    m2 = np.zeros(count, dtype=np.float64)
+    a1 = np.zeros(n, dtype=np.int64)
+    a2 = np.zeros(n, dtype=np.int64)
+    p2 = np.zeros(n, dtype=np.int64)
+    H1 = None if h1 is None else np.ascontiguousarray(h1, dtype=np.int64)
+    H2 = None if h2 is None else np.ascontiguousarray(h2, dtype=np.int64)
+    rc = _load().oracle_sample_cv(n, _ptr(rp), _ptr(cl), int(v), int(seed), int(first), int(count),
+                                  _ptr(out.cnt1), _ptr(out.cnt2), _ptr(y1), _ptr(y2), _ptr(H1), _ptr(H2),
+                                  _ptr(a1), _ptr(a2), _ptr(p2), _ptr(m2))
+    if rc != 0:
+        raise RuntimeError("oracle_sample_cv failed with code %d" % rc)
+    out.y1, out.y2 = y1, y2
+    out.sum_y1 = int(y1.sum(dtype=np.uint64))
+    out.sum_y2 = int(y2.sum(dtype=np.uint64))
+    out.omega = count
+    return out, a1, a2, p2, m2
 
 
 def sample_threads(row_ptr, col, v, seed, first, count, threads):

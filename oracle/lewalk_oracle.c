@@ -100,12 +100,24 @@ static int32_t oracle_neighbor(const int32_t *row_ptr, const int32_t *col, int32
  * scratch of n entries; intree[] of n bytes.  order: the n-1 (or n; v is
  * skipped) start nodes in the order Alg. 2 takes them; NULL means id order.
  * Returns 0, or -1 if the step budget (max_steps, 0 = none) ran out. */
+/* Control-variate sums (all optional, NULL = off): with integer potentials
+ * h1[n], h2[n] and S1[u] = sum of h1 over N(u), S2 likewise,
+ *   a1[u] += h1[w] for every Wilson draw at u choosing w,
+ *   a2[u] += h2[w] and p2[u] += 1 for every pi-walk step at u choosing w,
+ *   *m2_out = sum over the pi-walk steps of (d_u h2[w] - S2[u]) / d_u.
+ * Each increment d_u h[w] - S[u] has mean zero given u, because
+ * sum over w in N(u) of (d_u h[w] - S[u]) = d_u S[u] - d_u S[u] = 0. */
+typedef struct {
+    const int64_t *h1, *h2, *S1, *S2;
+    int64_t *a1, *a2, *p2;
+} oracle_cv;
+
 static int oracle_one_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t v,
                              uint64_t seed, uint32_t i, const int32_t *order, int32_t n_order,
                              uint32_t *draws, int32_t *next, uint8_t *intree,
                              uint64_t *cnt1, uint64_t *cnt2,
                              uint64_t *y1_out, uint64_t *y2_out, int32_t *tree_out,
-                             uint64_t max_steps)
+                             uint64_t max_steps, const oracle_cv *cv, double *m2_out)
 {
     /* Alg. 2: InTree[u] = false, Next[u] = -1 for all u; InTree[v] = true. */
     for (int32_t u = 0; u < n; ++u) { intree[u] = 0; next[u] = -1; draws[u] = 0; }
@@ -125,6 +137,7 @@ static int oracle_one_sample(int32_t n, const int32_t *row_ptr, const int32_t *c
             uint64_t x = oracle_r64(seed, (uint32_t)u, draws[u], i, 0u);
             draws[u] += 1;
             next[u] = oracle_neighbor(row_ptr, col, u, x);
+            if (cv && cv->h1) cv->a1[u] += cv->h1[next[u]];
             u = next[u];
         }
         /* Retrace from the walk's own start: the loop-erased path joins the tree. */
@@ -151,15 +164,24 @@ static int oracle_one_sample(int32_t n, const int32_t *row_ptr, const int32_t *c
     /* v-absorbed walk from s ~ pi (Alg. 4): the head of a uniformly drawn arc
      * is distributed as pi(w) = d_w / 2m. */
     uint64_t y2 = 0;
+    double m2 = 0.0;
     {
         int64_t arcs = row_ptr[n];
         int32_t u = col[oracle_below(oracle_r64(seed, 0u, 0u, i, 2u), (uint64_t)arcs)];
         while (u != v) {
             y2 += 1;
             if (max_steps && y2 > max_steps) return -1;
-            u = oracle_neighbor(row_ptr, col, u, oracle_r64(seed, (uint32_t)y2, 0u, i, 2u));
+            int32_t w = oracle_neighbor(row_ptr, col, u, oracle_r64(seed, (uint32_t)y2, 0u, i, 2u));
+            if (cv && cv->h2) {
+                int64_t d = (int64_t)row_ptr[u + 1] - row_ptr[u];
+                cv->a2[u] += cv->h2[w];
+                cv->p2[u] += 1;
+                m2 += (double)(d * cv->h2[w] - cv->S2[u]) / (double)d;
+            }
+            u = w;
         }
     }
+    if (m2_out) *m2_out = m2;
     *y1_out = y1;
     *y2_out = y2;
     return 0;
@@ -187,12 +209,49 @@ int oracle_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t
         uint64_t a = 0, b = 0;
         rc = oracle_one_sample(n, row_ptr, col, v, seed, (uint32_t)(first + q), order, n_order,
                                draws, next, intree, cnt1, cnt2, &a, &b,
-                               tree ? tree + (size_t)q * (size_t)n : NULL, max_steps);
+                               tree ? tree + (size_t)q * (size_t)n : NULL, max_steps, NULL, NULL);
         if (rc) break;
         if (y1) y1[q] = a;
         if (y2) y2[q] = b;
     }
     free(draws); free(next); free(intree);
+    return rc;
+}
+
+/*
+ * oracle_sample with the control-variate sums (see oracle_cv): potentials
+ * h1 (Wilson draws) and h2 (pi walk), either may be NULL.  a1, a2, p2 are
+ * ADDED to; m2[count] (optional) receives the per-sample pi-walk martingale.
+ */
+int oracle_sample_cv(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t v,
+                     uint64_t seed, uint64_t first, uint64_t count,
+                     uint64_t *cnt1, uint64_t *cnt2, uint64_t *y1, uint64_t *y2,
+                     const int64_t *h1, const int64_t *h2, int64_t *a1, int64_t *a2, int64_t *p2, double *m2)
+{
+    if (n <= 0 || v < 0 || v >= n || first + count > 0x100000000ull) return -2;
+    int64_t *S1 = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    int64_t *S2 = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    uint32_t *draws = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    int32_t *next = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    uint8_t *intree = (uint8_t *)malloc((size_t)n);
+    for (int32_t u = 0; u < n; ++u)
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            if (h1) S1[u] += h1[col[e]];
+            if (h2) S2[u] += h2[col[e]];
+        }
+    oracle_cv cv = {h1, h2, S1, S2, a1, a2, p2};
+    int rc = 0;
+    for (uint64_t q = 0; q < count; ++q) {
+        uint64_t a = 0, b = 0;
+        double mm = 0.0;
+        rc = oracle_one_sample(n, row_ptr, col, v, seed, (uint32_t)(first + q), NULL, 0,
+                               draws, next, intree, cnt1, cnt2, &a, &b, NULL, 0, &cv, &mm);
+        if (rc) break;
+        if (y1) y1[q] = a;
+        if (y2) y2[q] = b;
+        if (m2) m2[q] = mm;
+    }
+    free(S1); free(S2); free(draws); free(next); free(intree);
     return rc;
 }
 

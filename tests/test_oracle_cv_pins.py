@@ -1,0 +1,144 @@
+"""Pins for the control-variate oracle (oracle/cv.py and oracle_sample_cv):
+BF16 rounding, MLP gradients (finite differences), AdamW, features on hand
+checked graphs, the zero-mean identity of the martingale increments, and the
+variance cancellation the hitting-time potential must produce.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.cv as CV
+import oracle.dense as D
+from paper_2311_10290_gb300 import inputs as I
+
+
+def test_bf16_rounding():
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -2.5, 3.0e-3, 65504.0, 1.0 + 2 ** -7])
+    want = np.array([1.0, 1.0, 1.0 + 2 ** -7, -2.5, None, None, 1.0 + 2 ** -7], dtype=object)
+    got = CV.bf16(x)
+    for g, w in zip(got, want):
+        if w is not None:
+            assert g == w
+    torch = pytest.importorskip("torch")
+    r = np.random.default_rng(0).standard_normal(10000) * 10
+    ref = torch.from_numpy(r.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(CV.bf16(r), ref)
+
+
+def test_mlp_gradients_match_finite_differences():
+    rng = np.random.default_rng(1)
+    p = CV.init_params(3)
+    for k in p:
+        p[k] = p[k] + 0.05 * rng.standard_normal(p[k].shape)
+    x = rng.standard_normal((37, CV.N_FEAT))
+    t = rng.standard_normal((37, CV.N_OUT))
+    loss, g = CV.loss_and_grads(p, x, t, w=(1.0, 0.5), quantize=False)
+    eps = 1e-6
+    for k in p:
+        flat = p[k].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + eps
+            lp, _ = CV.loss_and_grads(p, x, t, w=(1.0, 0.5), quantize=False)
+            flat[idx] = old - eps
+            lm, _ = CV.loss_and_grads(p, x, t, w=(1.0, 0.5), quantize=False)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * eps)
+            an = g[k].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), (k, idx, fd, an)
+
+
+def test_adamw_first_step_closed_form():
+    w = np.array([0.5, -1.0, 2.0])
+    g = np.array([0.3, -0.001, 0.0])
+    w1, m, v = CV.adamw_step(w, np.zeros(3), np.zeros(3), g, 1, lr=0.01, wd=0.1, eps=1e-8)
+    # first step: m_hat = g, v_hat = g^2, so the step is lr*(g/(|g|+eps) + wd*w)
+    want = w - 0.01 * (g / (np.abs(g) + 1e-8) + 0.1 * w)
+    assert np.allclose(w1, want, rtol=1e-12, atol=1e-15)
+
+
+def test_features_on_a_path_rooted_at_an_end():
+    g = I.path(5)                      # 0-1-2-3-4, root 0
+    f = CV.features(g.row_ptr, g.col, 0)
+    d = np.array([1, 2, 2, 2, 1.0])
+    assert np.allclose(f[:, 0], np.log(d)) and np.allclose(f[:, 1], 1 / d)
+    assert np.allclose(f[:, 2], np.log1p([0, 1, 2, 3, 4]))
+    assert np.array_equal(f[:, 3], [0, 1, 0, 0, 0])
+    assert np.allclose(f[:, 4], np.log([2, 1.5, 2, 1.5, 2]))      # mean neighbour degree
+    assert np.allclose(f[:, 5], [0, 0.5, 0, 0.5, 0.0])            # share of degree-1 neighbours (nodes 0, 4)
+    # two-hop degree sums: s1 = [2,3,4,3,2]; s2 = [3,6,6,6,3]
+    assert np.allclose(f[:, 6], np.log(np.array([3, 6, 6, 6, 3.0]) / np.array([2, 3, 4, 3, 2.0])))
+    # P(hit 0 within 8 steps): node 1 -> 1/2 + 1/4*... computed by brute force on the chain
+    P = np.zeros((5, 5))
+    for u in range(1, 5):
+        for w in g.col[g.row_ptr[u]:g.row_ptr[u + 1]]:
+            P[u, w] = 1 / d[u]
+    P[0, 0] = 1.0
+    hit = np.linalg.matrix_power(P, 8)[:, 0]
+    assert np.allclose(f[:, 7], hit)
+
+
+def test_martingale_increments_sum_to_zero_over_neighbours():
+    g = I.ba(300, 3, seed=2)
+    h = np.random.default_rng(0).integers(-2 ** 30, 2 ** 30, size=g.n)
+    s = CV.neighbour_sums(g.row_ptr, g.col, h)
+    for u in range(g.n):
+        nb = g.col[g.row_ptr[u]:g.row_ptr[u + 1]]
+        assert int(np.sum(len(nb) * h[nb] - s[u])) == 0
+
+
+def test_constant_potential_gives_zero_terms_and_plain_estimates():
+    g = I.er(200, 0.04, seed=3)
+    v = oracle.root_max_degree(g.row_ptr)
+    c = np.full(g.n, 12345, dtype=np.int64)
+    cnt, a1, a2, p2, m2 = oracle.sample_cv(g.row_ptr, g.col, v, 9, 0, 300, h1=c, h2=c)
+    z1 = CV.martingale_z1(g.row_ptr, g.col, c, cnt.cnt1, a1)
+    assert np.all(z1 == 0) and np.all(m2 == 0.0)
+    assert CV.martingale_m2(g.row_ptr, g.col, c, a2, p2) == 0.0
+    plain = oracle.sample(g.row_ptr, g.col, v, 9, 0, 300)
+    assert np.array_equal(plain.cnt1, cnt.cnt1) and np.array_equal(plain.cnt2, cnt.cnt2)
+    ld0, ec0, kc0 = oracle.finalize(g.row_ptr, v, 300, cnt.cnt1, cnt.cnt2, cnt.sum_y1, cnt.sum_y2)
+    ld1, ec1, kc1 = CV.finalize_cv(g.row_ptr, v, 300, cnt.cnt1, cnt.cnt2, cnt.sum_y1, cnt.sum_y2, z1, 0.0, 0.7, 0.9)
+    assert np.allclose(ld0, ld1, rtol=1e-13) and np.allclose(ec0, ec1, rtol=1e-13) and kc0 == pytest.approx(kc1, rel=1e-14)
+
+
+def test_per_sample_m2_adds_up_to_the_node_totals():
+    g = I.ba(500, 2, seed=5)
+    v = oracle.root_max_degree(g.row_ptr)
+    h2 = np.random.default_rng(1).integers(0, 2 ** 26, size=g.n)
+    cnt, a1, a2, p2, m2 = oracle.sample_cv(g.row_ptr, g.col, v, 4, 0, 400, h2=h2)
+    total = CV.martingale_m2(g.row_ptr, g.col, h2, a2, p2)
+    assert math.fsum(m2.tolist()) == pytest.approx(total, rel=1e-9, abs=1e-3)
+    assert int(p2.sum()) == cnt.sum_y2          # one pi-walk step per pass before absorption
+
+
+def test_martingale_terms_have_mean_zero():
+    g = I.rmat(8, 6, seed=4)
+    v = oracle.root_max_degree(g.row_ptr)
+    rng = np.random.default_rng(2)
+    h = rng.integers(0, 2 ** 24, size=g.n)
+    zs, ms = [], []
+    for b in range(30):
+        cnt, a1, a2, p2, m2 = oracle.sample_cv(g.row_ptr, g.col, v, 11, 500 * b, 500, h1=h, h2=h)
+        zs.append(CV.martingale_z1(g.row_ptr, g.col, h, cnt.cnt1, a1).sum() / 2 ** 24 / 500)
+        ms.append(m2.sum() / 2 ** 24 / 500)
+    for x in (np.array(zs), np.array(ms)):
+        assert abs(x.mean()) < 6 * x.std(ddof=1) / np.sqrt(len(x))
+
+
+def test_hitting_time_potential_cancels_the_pi_walk_variance():
+    """With h2 = hitting time h(., v), Y2 - M2 = h(start, v): the walk's own
+    randomness cancels, so its variance drops to that of the start's hitting
+    time (here below 10% of Var(Y2)); a sign or index error breaks this."""
+    g = I.ba(400, 2, seed=7)
+    v = oracle.root_max_degree(g.row_ptr)
+    hit = D.hitting_times_to(g.n, g.row_ptr, g.col, v)
+    h2 = CV.quantize_potential(hit)
+    cnt, a1, a2, p2, m2 = oracle.sample_cv(g.row_ptr, g.col, v, 3, 0, 4000, h2=h2)
+    y2 = cnt.y2.astype(np.float64)
+    resid = y2 - m2 / 2.0 ** CV.FIXED_POINT_BITS
+    pi = g.degree / g.degree.sum()
+    var_start = float(pi @ hit ** 2 - (pi @ hit) ** 2)
+    assert np.var(resid) < 0.1 * np.var(y2)
+    assert np.var(resid) == pytest.approx(var_start, rel=0.2)
