@@ -199,6 +199,73 @@ lap_status lap_kemeny(lap_graph *g, double *out1);
  */
 lap_status lap_counts(lap_graph *g, uint64_t *cnt1, uint64_t *cnt2, uint64_t *sums, int on_device);
 
+/* ------------------------------------------------------------------------
+ * Learned control variate.  The paper has no control variate; these entry
+ * points add one that keeps every estimator unbiased.  For an integer
+ * potential h on nodes and S[u] = sum of h over N(u), each random step
+ * u -> w contributes d_u h[w] - S[u], which has mean exactly zero given u.
+ *   Wilson draws (potential h1):  Z1[u] = d_u A1[u] - cnt1[u] S1[u],
+ *       A1[u] = sum of h1[w] over the draws at u;
+ *       ECC uses y1_cv(u) = (cnt1[u] - beta1 Z1[u] / d_u) / (omega d_u).
+ *   pi-start walks (potential h2): M2 = sum_u (d_u A2[u] - P2[u] S2[u]) / d_u,
+ *       A2[u] = sum of h2[w] over the pi-walk steps at u, P2[u] = their number;
+ *       Kemeny uses kappa_cv = (sum Y1 - sum Y2 + beta2 M2) / omega.
+ * With h2 = the hitting time h(., v) (Section 3.2, v-absorbed walks), Y2 - M2
+ * equals the hitting time of the walk's start: the walk's own randomness
+ * cancels.  Potentials come from the MLP (8 -> 64 -> 64 -> 2) over the node
+ * features below; beta1, beta2 must be chosen independently of the samples
+ * they are applied to (e.g. from a pilot run) for unbiasedness.
+ * ------------------------------------------------------------------------ */
+
+/* Packed FP32 MLP parameters: W1[64][8] b1[64] W2[64][64] b2[64] W3[2][64] b3[2]. */
+#define LAP_MLP_PARAMS 4866
+
+/* 8 features per node into feat_dev[n][8] (device, float):
+ * ln d_u, 1/d_u, ln(1 + hop distance to v), [u adjacent to v], ln(mean
+ * neighbour degree), share of degree-1 neighbours, ln(two-hop degree sum /
+ * one-hop degree sum), P(walk from u hits v within 8 steps).  Needs the root. */
+lap_status lap_features(lap_graph *g, float *feat_dev);
+
+/* Hitting-time targets: for every node u, `reps` v-absorbed walks from u
+ * (step t of repetition r uses Philox counter (t, u, r, 3)); sums_dev[n]
+ * (device uint64) is overwritten with the total lengths, so sums/reps
+ * estimates h(u, v) = (L_v^{-1} d)_u.  Synchronises. */
+lap_status lap_hitting_walks(lap_graph *g, uint32_t reps, uint64_t seed, uint64_t *sums_dev);
+
+/* Potentials phi1 (Wilson draws, ECC) and phi2 (pi walks, Kemeny) as device
+ * double[n]; either may be NULL (that term off).  They are quantised to
+ * h = round(2^16 phi).  Only before the first sample after lap_set_root;
+ * lap_set_root clears the sums and keeps the potentials. */
+lap_status lap_cv_set_potentials(lap_graph *g, const double *phi1_dev, const double *phi2_dev);
+
+/* Raw control-variate sums a1[n], a2[n], p2[n] (int64; NULL skips). */
+lap_status lap_cv_sums(lap_graph *g, int64_t *a1, int64_t *a2, int64_t *p2, int on_device);
+
+/* Control-variate estimates: ldiag[n], ecc[n] (either may be NULL), kemeny[1]
+ * and m2_total[1] (host doubles; may be NULL).  Synchronises. */
+lap_status lap_cv_estimates(lap_graph *g, double beta1, double beta2, double *ldiag, double *ecc, int on_device,
+                            double *kemeny, double *m2_total);
+
+/* lap_sample_trace that also writes each sample's M2 to m2_dev[n_samples]
+ * (device double).  Needs phi2 set. */
+lap_status lap_sample_trace_cv(lap_graph *g, uint64_t n_samples, uint64_t seed, uint64_t *y1_dev, uint64_t *y2_dev,
+                               double *m2_dev);
+
+/* MLP forward on rows x[rows][8] -> y[rows][2] (device float), BF16 tensor
+ * cores with FP32 accumulation; params: LAP_MLP_PARAMS device floats. */
+lap_status lap_mlp_forward(const float *params_dev, const float *x_dev, int64_t rows, float *y_dev, void *cuda_stream);
+
+/* MSE loss (1/rows) sum_i (w0 (y_i0 - t_i0)^2 + w1 (y_i1 - t_i1)^2) and its
+ * gradient w.r.t. the packed parameters; grad_dev[LAP_MLP_PARAMS] and
+ * loss_dev[1] (device float) are overwritten. */
+lap_status lap_mlp_loss_grad(const float *params_dev, const float *x_dev, const float *t_dev, int64_t rows, float w0,
+                             float w1, float *grad_dev, float *loss_dev, void *cuda_stream);
+
+/* One AdamW step (decoupled weight decay) on count FP32 parameters in place;
+ * m_dev, v_dev are the moment buffers (zero before step 1); step >= 1. */
+lap_status lap_adamw(float *params_dev, float *m_dev, float *v_dev, const float *grad_dev, int64_t count, int32_t step,
+                     float lr, float beta1, float beta2, float eps, float weight_decay, void *cuda_stream);
+
 /* Read a statistic (see lap_stat) into *value. */
 lap_status lap_get_stat(lap_graph *g, int32_t stat, int64_t *value);
 

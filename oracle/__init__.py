@@ -52,6 +52,9 @@ def _load():
             lib.oracle_sample_cv.restype = ctypes.c_int
             lib.oracle_sample_cv.argtypes = [ctypes.c_int32, p, p, ctypes.c_int32, ctypes.c_uint64,
                                              ctypes.c_uint64, ctypes.c_uint64, p, p, p, p, p, p, p, p, p, p]
+            lib.oracle_hitting_walks.restype = ctypes.c_int
+            lib.oracle_hitting_walks.argtypes = [ctypes.c_int32, p, p, ctypes.c_int32, ctypes.c_uint64,
+                                                 ctypes.c_uint32, p, ctypes.c_uint64]
             lib.oracle_philox_block.restype = None
             lib.oracle_philox_block.argtypes = [p, p, p]
             _lib = lib
@@ -137,6 +140,18 @@ def sample_cv(row_ptr, col, v, seed, first, count, h1=None, h2=None):
     out.sum_y2 = int(y2.sum(dtype=np.uint64))
     out.omega = count
     return out, a1, a2, p2, m2
+
+
+def hitting_walks(row_ptr, col, v, seed, reps, max_steps=0):
+    """Per-node sums of `reps` v-absorbed walk lengths from every node (uint64)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    sums = np.zeros(rp.size - 1, dtype=np.uint64)
+    rc = _load().oracle_hitting_walks(rp.size - 1, _ptr(rp), _ptr(cl), int(v), int(seed), int(reps),
+                                      _ptr(sums), int(max_steps))
+    if rc != 0:
+        raise RuntimeError("oracle_hitting_walks failed with code %d" % rc)
+    return sums
 
 
 def sample_threads(row_ptr, col, v, seed, first, count, threads):

@@ -30,7 +30,7 @@ import numpy as np
 N_FEAT = 8
 HIDDEN = 64
 N_OUT = 2
-FIXED_POINT_BITS = 20
+FIXED_POINT_BITS = 16
 
 
 # ------------------------------------------------------------------- features
@@ -195,7 +195,7 @@ def finalize_cv(row_ptr, v, omega, cnt1, cnt2, sum_y1, sum_y2, z1, m2, beta1, be
     n = rp.size - 1
     d = (rp[1:] - rp[:-1]).astype(np.float64)
     w = float(omega)
-    c1 = np.asarray(cnt1, dtype=np.float64) - beta1 * np.asarray(z1, dtype=np.float64) / d
+    c1 = np.asarray(cnt1, dtype=np.float64) - beta1 * (np.asarray(z1, dtype=np.float64) / d)
     y1 = c1 / (w * d)
     y2 = np.asarray(cnt2, dtype=np.float64) / (w * d)
     lvv = math.fsum(y2.tolist()) / n

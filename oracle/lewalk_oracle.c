@@ -256,6 +256,31 @@ int oracle_sample_cv(int32_t n, const int32_t *row_ptr, const int32_t *col, int3
 }
 
 /*
+ * Hitting-time targets (Section 3.2, v-absorbed walk lemma: the expected
+ * length of a walk from u absorbed at v is h(u, v) = (L_v^{-1} d)_u).  For
+ * every node u and repetition r in [0, reps), one walk from u until v; step t
+ * (t = 1, 2, ...) uses Philox counter (t, u, r, 3).  sums[u] += total length.
+ */
+int oracle_hitting_walks(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t v,
+                         uint64_t seed, uint32_t reps, uint64_t *sums, uint64_t max_steps)
+{
+    if (n <= 0 || v < 0 || v >= n) return -2;
+    for (int32_t u = 0; u < n; ++u) {
+        for (uint32_t r = 0; r < reps; ++r) {
+            uint64_t t = 0;
+            int32_t x = u;
+            while (x != v) {
+                t += 1;
+                if (max_steps && t > max_steps) return -1;
+                x = oracle_neighbor(row_ptr, col, x, oracle_r64(seed, (uint32_t)t, (uint32_t)u, r, 3u));
+            }
+            sums[u] += t;
+        }
+    }
+    return 0;
+}
+
+/*
  * Cycle popping on Wilson's stacks (Section 3.4, stack representation): the
  * top of S[u] is the draw (u, pops[u], i, 0).  While the top-pointer graph on
  * the non-tree nodes has nodes whose top path reaches the tree, those paths

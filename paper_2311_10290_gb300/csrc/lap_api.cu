@@ -52,6 +52,14 @@ void free_all(lap_graph *g)
     cudaFree(g->d_red);
     cudaFree(g->d_slot_epoch);
     cudaFree(g->d_ovf_ids);
+    cudaFree(g->d_cv_h1);
+    cudaFree(g->d_cv_S1);
+    cudaFree(g->d_cv_h2);
+    cudaFree(g->d_cv_S2);
+    cudaFree(g->d_cv_a1);
+    cudaFree(g->d_cv_a2);
+    cudaFree(g->d_cv_p2);
+    cudaFree(g->d_feat_scratch);
     if (g->ws_owned) cudaFree(g->ws);
 }
 
@@ -233,7 +241,7 @@ lap_status lap_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *co
               dalloc(&g->d_rowinfo, nn) == cudaSuccess && dalloc(&g->d_hops, nn) == cudaSuccess &&
               dalloc(&g->d_rep1, nn) == cudaSuccess && dalloc(&g->d_cnt2, nn) == cudaSuccess &&
               dalloc(&g->d_acc, 1) == cudaSuccess && dalloc(&g->d_ldiag, nn) == cudaSuccess &&
-              dalloc(&g->d_ecc, nn) == cudaSuccess && dalloc(&g->d_red, 1024 + 8) == cudaSuccess;
+              dalloc(&g->d_ecc, nn) == cudaSuccess && dalloc(&g->d_red, 1024 + 16) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(g);
@@ -401,6 +409,12 @@ lap_status lap_set_root(lap_graph *g, int32_t v, int32_t *root_out)
     LAP_CUDA(g, cudaMemsetAsync(g->d_rep1, 0, sizeof(unsigned long long) * (size_t)g->n, g->stream));
     LAP_CUDA(g, cudaMemsetAsync(g->d_cnt2, 0, sizeof(unsigned long long) * (size_t)g->n, g->stream));
     LAP_CUDA(g, cudaMemsetAsync(g->d_acc, 0, sizeof(LapDevAcc), g->stream));
+    if (g->d_cv_a1) {
+        const size_t nb = sizeof(unsigned long long) * (size_t)g->n;
+        LAP_CUDA(g, cudaMemsetAsync(g->d_cv_a1, 0, nb, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_cv_a2, 0, nb, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_cv_p2, 0, nb, g->stream));
+    }
     g->ws_zeroed = false;                 // a failed earlier run may have left partial state
     g->pending = false;
     g->compact_disabled = false;
@@ -420,7 +434,8 @@ lap_status lap_sample(lap_graph *g, uint64_t n_samples, uint64_t seed)
     return lap_sample_trace(g, n_samples, seed, nullptr, nullptr);
 }
 
-static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, uint64_t *y1_dev, uint64_t *y2_dev);
+static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, uint64_t *y1_dev, uint64_t *y2_dev,
+                               double *m2_dev);
 
 lap_status lap_sample_trace(lap_graph *g, uint64_t n_samples, uint64_t seed, uint64_t *y1_dev, uint64_t *y2_dev)
 {
@@ -429,14 +444,26 @@ lap_status lap_sample_trace(lap_graph *g, uint64_t n_samples, uint64_t seed, uin
     const uint64_t chunk = 1ull << 24;
     for (uint64_t done = 0; done < n_samples || (n_samples == 0 && done == 0);) {
         const uint64_t c = n_samples - done < chunk ? n_samples - done : chunk;
-        lap_status s = sample_chunk(g, c, seed, y1_dev ? y1_dev + done : nullptr, y2_dev ? y2_dev + done : nullptr);
+        lap_status s = sample_chunk(g, c, seed, y1_dev ? y1_dev + done : nullptr, y2_dev ? y2_dev + done : nullptr,
+                                    nullptr);
         if (s != LAP_OK || n_samples == 0) return s;
         done += c;
     }
     return LAP_OK;
 }
 
-static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, uint64_t *y1_dev, uint64_t *y2_dev)
+lap_status lap_sample_trace_cv(lap_graph *g, uint64_t n_samples, uint64_t seed, uint64_t *y1_dev, uint64_t *y2_dev,
+                               double *m2_dev)
+{
+    if (!g) return fail(nullptr, LAP_ERR_INVALID_ARG, "NULL handle");
+    if (!y1_dev || !y2_dev || !m2_dev) return fail(g, LAP_ERR_INVALID_ARG, "y1_dev, y2_dev and m2_dev must be set");
+    if (!g->cv2) return fail(g, LAP_ERR_INVALID_ARG, "the pi-walk potential (phi2) is not set");
+    if (n_samples > (1ull << 24)) return fail(g, LAP_ERR_TOO_LARGE, "at most 2^24 samples per traced call");
+    return sample_chunk(g, n_samples, seed, y1_dev, y2_dev, m2_dev);
+}
+
+static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, uint64_t *y1_dev, uint64_t *y2_dev,
+                               double *m2_dev)
 {
     lap_status s = check_sticky(g);
     if (s != LAP_OK) return s;
@@ -467,9 +494,28 @@ static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, 
     p.num_sms = g->num_sms;
     p.y1_out = reinterpret_cast<unsigned long long *>(y1_dev);
     p.y2_out = reinterpret_cast<unsigned long long *>(y2_dev);
+    p.m2_out = m2_dev;
+    if (g->cv1) {
+        p.cv_h1 = g->d_cv_h1;
+        p.cv_a1 = g->d_cv_a1;
+    }
+    if (g->cv2) {
+        p.cv_h2 = g->d_cv_h2;
+        p.cv_S2 = g->d_cv_S2;
+        p.cv_a2 = g->d_cv_a2;
+        p.cv_p2 = g->d_cv_p2;
+    }
     if (kernel == LAP_KERNEL_COMPACT) {
         if (g->ovf_cap < n_samples) {
             cudaFree(g->d_ovf_ids);
+    cudaFree(g->d_cv_h1);
+    cudaFree(g->d_cv_S1);
+    cudaFree(g->d_cv_h2);
+    cudaFree(g->d_cv_S2);
+    cudaFree(g->d_cv_a1);
+    cudaFree(g->d_cv_a2);
+    cudaFree(g->d_cv_p2);
+    cudaFree(g->d_feat_scratch);
             g->d_ovf_ids = nullptr;
             g->ovf_cap = 0;
             if (dalloc(&g->d_ovf_ids, (size_t)n_samples) != cudaSuccess) {
@@ -585,6 +631,146 @@ lap_status lap_hops(lap_graph *g, int32_t *out, int on_device)
     if (s != LAP_OK) return s;
     if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
     return copy_out(g, out, g->d_hops, sizeof(int32_t) * (size_t)g->n, on_device);
+}
+
+lap_status lap_features(lap_graph *g, float *feat_dev)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (!feat_dev) return fail(g, LAP_ERR_INVALID_ARG, "feat_dev is NULL");
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (!g->d_feat_scratch && dalloc(&g->d_feat_scratch, 5 * (size_t)g->n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(g, LAP_ERR_OOM, "feature scratch allocation failed");
+    }
+    LAP_CUDA(g, lap_launch_features(g->d_rowinfo, g->d_col, g->d_hops, g->n, g->root, g->d_feat_scratch, feat_dev,
+                                    g->stream));
+    return LAP_OK;
+}
+
+lap_status lap_hitting_walks(lap_graph *g, uint32_t reps, uint64_t seed, uint64_t *sums_dev)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (!sums_dev || reps == 0) return fail(g, LAP_ERR_INVALID_ARG, "sums_dev must be set and reps >= 1");
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if ((s = resolve_pending(g)) != LAP_OK) return s;
+    LAP_CUDA(g, cudaMemsetAsync(sums_dev, 0, sizeof(uint64_t) * (size_t)g->n, g->stream));
+    unsigned int *status = reinterpret_cast<unsigned int *>(g->d_red);
+    LAP_CUDA(g, cudaMemsetAsync(status, 0, sizeof(unsigned int), g->stream));
+    const uint64_t limit = g->step_limit ? g->step_limit : default_step_limit(g->n);
+    LAP_CUDA(g, lap_launch_hitting_walks(LapDevGraph{g->d_rowinfo, g->d_col, g->n, g->arcs}, g->root, seed, reps, limit,
+                                         reinterpret_cast<unsigned long long *>(sums_dev), status, g->num_sms,
+                                         g->stream));
+    unsigned int h = 0;
+    LAP_CUDA(g, cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    if (h & LAP_DEV_STEP_LIMIT) return fail(g, LAP_ERR_STEP_LIMIT, "a hitting walk exceeded the step budget");
+    return LAP_OK;
+}
+
+lap_status lap_cv_set_potentials(lap_graph *g, const double *phi1_dev, const double *phi2_dev)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (g->omega != 0) return fail(g, LAP_ERR_INVALID_ARG, "potentials can only be set before the first sample after lap_set_root");
+    const size_t n = (size_t)g->n;
+    if ((phi1_dev || phi2_dev) && !g->d_cv_a1) {
+        bool ok = dalloc(&g->d_cv_h1, n) == cudaSuccess && dalloc(&g->d_cv_S1, n) == cudaSuccess &&
+                  dalloc(&g->d_cv_h2, n) == cudaSuccess && dalloc(&g->d_cv_S2, n) == cudaSuccess &&
+                  dalloc(&g->d_cv_a1, n) == cudaSuccess && dalloc(&g->d_cv_a2, n) == cudaSuccess &&
+                  dalloc(&g->d_cv_p2, n) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return fail(g, LAP_ERR_OOM, "control-variate allocation failed");
+        }
+        const size_t nb = sizeof(unsigned long long) * n;
+        LAP_CUDA(g, cudaMemsetAsync(g->d_cv_a1, 0, nb, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_cv_a2, 0, nb, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_cv_p2, 0, nb, g->stream));
+    }
+    g->cv1 = phi1_dev != nullptr;
+    g->cv2 = phi2_dev != nullptr;
+    if (phi1_dev) LAP_CUDA(g, lap_launch_potential(g->d_rowinfo, g->d_col, g->n, phi1_dev, g->d_cv_h1, g->d_cv_S1, g->stream));
+    if (phi2_dev) LAP_CUDA(g, lap_launch_potential(g->d_rowinfo, g->d_col, g->n, phi2_dev, g->d_cv_h2, g->d_cv_S2, g->stream));
+    g->results_valid = false;
+    return LAP_OK;
+}
+
+lap_status lap_cv_sums(lap_graph *g, int64_t *a1, int64_t *a2, int64_t *p2, int on_device)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (!g->d_cv_a1) return fail(g, LAP_ERR_INVALID_ARG, "no potentials set");
+    if ((s = poll_status(g)) != LAP_OK) return s;
+    const size_t nb = sizeof(int64_t) * (size_t)g->n;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (a1) LAP_CUDA(g, cudaMemcpyAsync(a1, g->d_cv_a1, nb, kind, g->stream));
+    if (a2) LAP_CUDA(g, cudaMemcpyAsync(a2, g->d_cv_a2, nb, kind, g->stream));
+    if (p2) LAP_CUDA(g, cudaMemcpyAsync(p2, g->d_cv_p2, nb, kind, g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    return LAP_OK;
+}
+
+lap_status lap_cv_estimates(lap_graph *g, double beta1, double beta2, double *ldiag, double *ecc, int on_device,
+                            double *kemeny, double *m2_total)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (g->omega == 0) return fail(g, LAP_ERR_NO_SAMPLES, "no samples drawn");
+    if ((s = poll_status(g)) != LAP_OK) return s;
+    double *m2d = g->d_red + 1024 + 4;
+    LAP_CUDA(g, cudaMemsetAsync(m2d, 0, sizeof(double), g->stream));
+    LAP_CUDA(g, lap_launch_cv_finalize(g->d_rowinfo, g->n, g->root, g->omega, g->d_rep1, g->d_cnt2,
+                                       g->cv1 ? reinterpret_cast<const long long *>(g->d_cv_a1) : nullptr, g->d_cv_S1, beta1,
+                                       g->cv2 ? reinterpret_cast<const long long *>(g->d_cv_a2) : nullptr,
+                                       reinterpret_cast<const long long *>(g->d_cv_p2), g->d_cv_S2,
+                                       g->d_ldiag, g->d_ecc, g->d_red, m2d, g->stream));
+    g->results_valid = false;          // the plain results were overwritten
+    const size_t nb = sizeof(double) * (size_t)g->n;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (ldiag) LAP_CUDA(g, cudaMemcpyAsync(ldiag, g->d_ldiag, nb, kind, g->stream));
+    if (ecc) LAP_CUDA(g, cudaMemcpyAsync(ecc, g->d_ecc, nb, kind, g->stream));
+    double m2 = 0.0;
+    LAP_CUDA(g, cudaMemcpyAsync(&m2, m2d, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    LapDevAcc h;
+    LAP_CUDA(g, cudaMemcpyAsync(&h, g->d_acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    if (m2_total) *m2_total = m2;
+    // Alg. 4 with the control variate: kappa = (sum Y1 - sum Y2 + beta2 M2) / omega.
+    if (kemeny) *kemeny = (((double)h.sum_y1 - (double)h.sum_y2) + beta2 * m2) / (double)g->omega;
+    return LAP_OK;
+}
+
+lap_status lap_mlp_forward(const float *params_dev, const float *x_dev, int64_t rows, float *y_dev, void *cuda_stream)
+{
+    if (!params_dev || !x_dev || !y_dev || rows < 0) return fail(nullptr, LAP_ERR_INVALID_ARG, "bad MLP arguments");
+    cudaError_t e = lap_launch_mlp(params_dev, x_dev, nullptr, rows, 0.f, 0.f, y_dev, nullptr, nullptr,
+                                   reinterpret_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? LAP_OK : cuda_fail(nullptr, e, "lap_mlp_forward");
+}
+
+lap_status lap_mlp_loss_grad(const float *params_dev, const float *x_dev, const float *t_dev, int64_t rows, float w0,
+                             float w1, float *grad_dev, float *loss_dev, void *cuda_stream)
+{
+    if (!params_dev || !x_dev || !t_dev || !grad_dev || !loss_dev || rows <= 0)
+        return fail(nullptr, LAP_ERR_INVALID_ARG, "bad MLP arguments");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaMemsetAsync(grad_dev, 0, sizeof(float) * LAP_MLP_PARAMS, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(loss_dev, 0, sizeof(float), st);
+    if (e == cudaSuccess) e = lap_launch_mlp(params_dev, x_dev, t_dev, rows, w0, w1, nullptr, grad_dev, loss_dev, st);
+    return e == cudaSuccess ? LAP_OK : cuda_fail(nullptr, e, "lap_mlp_loss_grad");
+}
+
+lap_status lap_adamw(float *params_dev, float *m_dev, float *v_dev, const float *grad_dev, int64_t count, int32_t step,
+                     float lr, float beta1, float beta2, float eps, float weight_decay, void *cuda_stream)
+{
+    if (!params_dev || !m_dev || !v_dev || !grad_dev || count <= 0 || step < 1)
+        return fail(nullptr, LAP_ERR_INVALID_ARG, "bad AdamW arguments");
+    cudaError_t e = lap_launch_adamw(params_dev, m_dev, v_dev, grad_dev, count, step, lr, beta1, beta2, eps, weight_decay,
+                                     reinterpret_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? LAP_OK : cuda_fail(nullptr, e, "lap_adamw");
 }
 
 lap_status lap_graph_info(const lap_graph *g, int32_t *n, int64_t *arcs, int32_t *root)

@@ -71,6 +71,16 @@ struct LapSampleLaunch {
     unsigned int *ovf_ids;       // compact kernel: withdrawn sample ids [count]
     const unsigned int *ids;     // wide kernel: explicit sample ids [count] (NULL: first + q)
     uint32_t trace_base;         // wide kernel with ids: y1_out/y2_out index = id - trace_base
+    // Control variate (NULL pointers: off).  Wilson draws at u choosing w add
+    // h1[w] to a1[u]; pi-walk steps at u choosing w add h2[w] to a2[u] and 1
+    // to p2[u], and (d_u h2[w] - S2[u]) / d_u to the sample's M2.
+    const long long *cv_h1;
+    unsigned long long *cv_a1;
+    const long long *cv_h2;
+    const long long *cv_S2;
+    unsigned long long *cv_a2;
+    unsigned long long *cv_p2;
+    double *m2_out;              // optional [count]: per-sample M2 (with y1_out)
 };
 cudaError_t lap_launch_sample(const LapSampleLaunch &p, cudaStream_t st);
 // sampler_compact.cu
@@ -88,6 +98,25 @@ inline int lap_pick_block(uint64_t lanes, int num_sms)
 }
 
 enum LapKernel : int { LAP_KERNEL_WIDE = 1, LAP_KERNEL_COMPACT = 2 };
+
+// Control variate (cv.cu, mlp.cu).
+constexpr int LAP_CV_FIXED_POINT_BITS = 16;   // h = round(2^16 phi)
+constexpr int LAP_CV_ABSORB_ITERS = 8;        // feature f7: P(hit v within 8 steps)
+cudaError_t lap_launch_features(const int2 *rowinfo, const int32_t *col, const int32_t *hops, int32_t n, int32_t root,
+                                double *scratch, float *feat, cudaStream_t st);
+cudaError_t lap_launch_potential(const int2 *rowinfo, const int32_t *col, int32_t n, const double *phi, long long *h,
+                                 long long *S, cudaStream_t st);
+cudaError_t lap_launch_hitting_walks(const LapDevGraph &g, int32_t root, uint64_t seed, uint32_t reps, uint64_t limit,
+                                     unsigned long long *sums, unsigned int *status, int num_sms, cudaStream_t st);
+cudaError_t lap_launch_cv_finalize(const int2 *rowinfo, int32_t n, int32_t root, uint64_t omega,
+                                   const unsigned long long *rep1, const unsigned long long *cnt2,
+                                   const long long *a1, const long long *S1, double beta1,
+                                   const long long *a2, const long long *p2, const long long *S2,
+                                   double *ldiag, double *ecc, double *red, double *m2_out, cudaStream_t st);
+cudaError_t lap_launch_mlp(const float *P, const float *X, const float *T, int64_t n, float wk0, float wk1,
+                           float *Y, float *G, float *loss, cudaStream_t st);
+cudaError_t lap_launch_adamw(float *w, float *m, float *v, const float *g, int64_t count, int32_t step, float lr,
+                             float b1, float b2, float eps, float wd, cudaStream_t st);
 
 // finalize.cu
 cudaError_t lap_launch_finalize(const int2 *rowinfo, int32_t n, int32_t root, uint64_t omega,
@@ -136,6 +165,12 @@ struct lap_graph {
     int last_kernel = 0;                    // layout the workspace currently holds
     bool compact_disabled = false;          // set after a compact launch overflowed
     int64_t fallbacks = 0;
+
+    // Control variate.
+    long long *d_cv_h1 = nullptr, *d_cv_S1 = nullptr, *d_cv_h2 = nullptr, *d_cv_S2 = nullptr;
+    unsigned long long *d_cv_a1 = nullptr, *d_cv_a2 = nullptr, *d_cv_p2 = nullptr;
+    double *d_feat_scratch = nullptr;
+    bool cv1 = false, cv2 = false;
 
     // Samples a compact launch withdrew; re-run with the wide kernel.
     unsigned int *d_ovf_ids = nullptr;

@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
     uint32_t k = 0;          // draws at u so far
     uint64_t pa = 0, pb = 0; // loaded values consumed in the next iteration
     uint64_t y1 = 0, t = 0, y2 = 0;
+    double m2 = 0.0;          // control variate: the sample's pi-walk martingale
     unsigned long long acc1 = 0, acc2 = 0;
     unsigned int bad = 0;
 
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
             const int32_t w = (int32_t)(uint32_t)pb;
             st[u] = (unsigned long long)(epoch | ((uint64_t)(k + 1u) << 32) | (uint32_t)w);
             if (k) atomicAdd(&p.rep1[u], 1ull);
+            if (p.cv_h1) atomicAdd(&p.cv_a1[u], (unsigned long long)p.cv_h1[w]);
             if (k + 1u >= kKMax) bad |= LAP_DEV_K_OVERFLOW;
             ++y1;
             u = w;
@@ -140,7 +142,14 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
         } else if (phase == P_PIDRAW) {
             ++y2;
             const uint64_t r = lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1);
-            pb = (uint64_t)(uint32_t)__ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
+            const int32_t w = __ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
+            if (p.cv_h2) {
+                const long long d = (long long)row_deg(pb), hw = p.cv_h2[w], s2 = p.cv_S2[u];
+                atomicAdd(&p.cv_a2[u], (unsigned long long)hw);
+                atomicAdd(&p.cv_p2[u], 1ull);
+                m2 = __dadd_rn(m2, __ddiv_rn((double)(d * hw - s2), (double)d));
+            }
+            pb = (uint64_t)(uint32_t)w;
             phase = P_PIMOVE;
             if (y2 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; }
         } else if (phase == P_PIMOVE) {
@@ -152,6 +161,7 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
                     const uint32_t ix = i - (p.ids ? p.trace_base : p.first);
                     p.y1_out[ix] = y1;
                     p.y2_out[ix] = y2;
+                    if (p.m2_out) p.m2_out[ix] = m2;
                 }
                 phase = P_CLAIM;
             }
@@ -166,6 +176,7 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
         } else if (phase == P_PISTART) {
             // Alg. 4: s ~ pi is the head of a uniformly drawn arc.
             y2 = 0;
+            m2 = 0.0;
             const uint64_t r = lap::philox_r64(0u, 0u, i, 2u, key0, key1);
             pb = (uint64_t)(uint32_t)__ldg(col + (int64_t)lap::below(r, (uint64_t)p.g.arcs));
             phase = P_PIMOVE;

@@ -177,9 +177,13 @@ __device__ __forceinline__ uint32_t erase_loop(uint8_t *st, const uint32_t *stk,
 }
 
 // Withdraws a partly run sample: subtracts the k - 1 repeat visits every
-// node of the sample has contributed and marks all bytes "current epoch,
-// untouched", so that the next sample (next epoch) reads them as stale.
-__device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsigned long long *rep1)
+// node of the sample has contributed (and, with the control variate, the
+// potentials h1[w] of its k draws, recomputed from their Philox keys) and
+// marks all bytes "current epoch, untouched", so that the next sample (next
+// epoch) reads them as stale.
+__device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsigned long long *rep1, const int2 *rowinfo,
+                                const int32_t *col, const long long *h1, unsigned long long *a1, uint32_t i,
+                                uint32_t key0, uint32_t key1)
 {
     for (int32_t base = 0; base < n; base += 16) {
         ulonglong2 q = *reinterpret_cast<ulonglong2 *>(st + base);
@@ -187,13 +191,24 @@ __device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsigned lo
         for (int b = 0; b < 16; ++b) {
             const uint32_t byte = (uint32_t)(((b < 8 ? q.x : q.y) >> (8 * (b & 7))) & 0xFFu);
             const uint32_t k = b_k(byte, ep);
-            if (base + b < n && k >= 2u) atomicAdd(&rep1[base + b], (unsigned long long)(-(long long)(k - 1u)));
+            if (base + b >= n) continue;
+            if (k >= 2u) atomicAdd(&rep1[base + b], (unsigned long long)(-(long long)(k - 1u)));
+            if (h1 && k) {
+                const int2 r = rowinfo[base + b];
+                long long sub = 0;
+                for (uint32_t j = 0; j < k; ++j) {
+                    const uint64_t x = lap::philox_r64((uint32_t)(base + b), j, i, 0u, key0, key1);
+                    sub += h1[col[r.x + (int64_t)lap::below(x, (uint64_t)r.y)]];
+                }
+                atomicAdd(&a1[base + b], (unsigned long long)(-sub));
+            }
         }
         const unsigned long long fill = 0x0101010101010101ull * (unsigned long long)ep;
         *reinterpret_cast<ulonglong2 *>(st + base) = make_ulonglong2(fill, fill);
     }
 }
 
+template <bool CV>
 __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
 {
     const uint64_t slot = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -222,11 +237,20 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
     uint64_t pb = 0;          // row record of h (in flight)
     ulonglong2 pq = make_ulonglong2(0, 0);
     uint64_t y1 = 0, t = 0, y2 = 0;
+    double m2 = 0.0;          // control variate: the sample's pi-walk martingale
+    int32_t cv_u = -1;        // control variate: node of the draw whose potential is pending
+    long long cv_val = 0;
     unsigned long long acc1 = 0, acc2 = 0;
     unsigned int bad = 0;
 
     for (;;) {
         if (phase == P_WALK) {
+            // Control variate: add the previous draw's potential (its load was
+            // issued with that draw's state and row loads).
+            if (CV && cv_u >= 0) {
+                atomicAdd(&p.cv_a1[cv_u], (unsigned long long)cv_val);
+                cv_u = -1;
+            }
             // One Wilson step per iteration, so walking lanes stay converged.
             // The column entry for draw index 0 (the usual case: the first
             // visit of h) is requested as soon as h's row record arrives,
@@ -241,7 +265,7 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
                 if (kh) w = ld_col(col + off + (int64_t)lap::below(lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1), deg), keep);
                 const uint32_t kn = kh + 1u;
                 if (kn > kKMax || sp >= cap) {
-                    withdraw_sample(st, n, ep, p.rep1);
+                    withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1);
                     const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
                     if (ix < p.count) p.ovf_ids[ix] = i;
                     phase = P_CLAIM;
@@ -255,6 +279,10 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
                 pq_set(pq, chunk, (uint32_t)h, ep | kBPath | kn);
                 if (kh) atomicAdd(&p.rep1[h], 1ull);
                 if (++y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
+                if (CV && p.cv_h1) {
+                    cv_u = h;
+                    cv_val = p.cv_h1[w];
+                }
                 h = w;
                 pa = ld_state(st + w);
                 pb = ld_row(rowinfo, w, keep);
@@ -319,6 +347,7 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
         if (phase == P_PISTART_IMMEDIATE) {
             // Alg. 4: s ~ pi is the head of a uniformly drawn arc.
             y2 = 0;
+            m2 = 0.0;
             h = ld_col(col + (int64_t)lap::below(lap::philox_r64(0u, 0u, i, 2u, key0, key1), (uint64_t)p.g.arcs), keep);
             if (h != v) { pb = ld_row(rowinfo, h, keep); phase = P_PIWALK; continue; }
             phase = P_FINISH_IMMEDIATE;
@@ -326,7 +355,14 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
         if (phase == P_PIWALK) {
             ++y2;
             const uint64_t r = lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1);
-            h = ld_col(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)), keep);
+            const int32_t w = ld_col(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)), keep);
+            if (CV && p.cv_h2) {
+                const long long d = (long long)row_deg(pb), hw = p.cv_h2[w], s2 = p.cv_S2[h];
+                atomicAdd(&p.cv_a2[h], (unsigned long long)hw);
+                atomicAdd(&p.cv_p2[h], 1ull);
+                m2 = __dadd_rn(m2, __ddiv_rn((double)(d * hw - s2), (double)d));
+            }
+            h = w;
             if (y2 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
             if (h != v) { pb = ld_row(rowinfo, h, keep); continue; }
             phase = P_FINISH_IMMEDIATE;
@@ -334,7 +370,11 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
         if (phase == P_FINISH_IMMEDIATE) {
             acc1 += y1;
             acc2 += y2;
-            if (p.y1_out) { p.y1_out[i - p.first] = y1; p.y2_out[i - p.first] = y2; }
+            if (p.y1_out) {
+                p.y1_out[i - p.first] = y1;
+                p.y2_out[i - p.first] = y2;
+                if (CV && p.m2_out) p.m2_out[i - p.first] = m2;
+            }
             phase = P_CLAIM;
         }
         if (phase == P_CLAIM) {
@@ -364,6 +404,7 @@ cudaError_t lap_launch_sample_compact(const LapSampleLaunch &p, cudaStream_t st)
     if (p.count == 0 || p.slots == 0) return cudaSuccess;
     int block = p.block > 0 ? p.block : lap_pick_block(p.slots, p.num_sms);
     uint64_t grid = (p.slots + block - 1) / block;
-    lewalk_compact_kernel<<<(unsigned)grid, block, 0, st>>>(p);
+    if (p.cv_h1 || p.cv_h2) lewalk_compact_kernel<true><<<(unsigned)grid, block, 0, st>>>(p);
+    else lewalk_compact_kernel<false><<<(unsigned)grid, block, 0, st>>>(p);
     return cudaGetLastError();
 }

@@ -27,6 +27,7 @@ STATUS = {
 }
 LAP_OPT_STEP_LIMIT, LAP_OPT_SLOTS, LAP_OPT_BLOCK, LAP_OPT_CURSOR, LAP_OPT_KERNEL, LAP_OPT_STACK = 1, 2, 3, 4, 5, 6
 LAP_STAT_SLOTS, LAP_STAT_KERNEL, LAP_STAT_FALLBACKS = 1, 2, 3
+LAP_MLP_PARAMS = 4866
 
 
 class LapError(RuntimeError):
@@ -70,6 +71,16 @@ def library():
         "lap_graph_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]),
         "lap_last_error": (ctypes.c_char_p, [vp]),
         "lap_sample_static": (i32, [i32, vp, vp, i32, u64, u64, u64, vp, vp, vp, vp]),
+        "lap_features": (i32, [vp, vp]),
+        "lap_hitting_walks": (i32, [vp, ctypes.c_uint32, u64, vp]),
+        "lap_cv_set_potentials": (i32, [vp, vp, vp]),
+        "lap_cv_sums": (i32, [vp, vp, vp, vp, ctypes.c_int]),
+        "lap_cv_estimates": (i32, [vp, ctypes.c_double, ctypes.c_double, vp, vp, ctypes.c_int, vp, vp]),
+        "lap_sample_trace_cv": (i32, [vp, u64, u64, vp, vp, vp]),
+        "lap_mlp_forward": (i32, [vp, vp, i64, vp, vp]),
+        "lap_mlp_loss_grad": (i32, [vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp, vp, vp]),
+        "lap_adamw": (i32, [vp, vp, vp, vp, i64, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                            ctypes.c_float, ctypes.c_float, vp]),
         "lap_static_scratch_bytes": (u64, []),
         "lap_static_last_error": (ctypes.c_char_p, []),
     }
@@ -233,6 +244,62 @@ def lap_sample_static(n, row_ptr, col_idx, root, seed, first_id, n_samples, cnt1
         raise LapError(st, lap_static_last_error())
 
 
+def _dp(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def lap_features(h, feat_dev):
+    """feat_dev: float32 CUDA tensor [n, 8]."""
+    _check(library().lap_features(h, _dp(feat_dev)), h)
+
+
+def lap_hitting_walks(h, reps, seed, sums_dev):
+    """sums_dev: 64-bit CUDA tensor [n], overwritten with total walk lengths."""
+    _check(library().lap_hitting_walks(h, int(reps), int(seed), _dp(sums_dev)), h)
+
+
+def lap_cv_set_potentials(h, phi1_dev=None, phi2_dev=None):
+    """phi1_dev, phi2_dev: float64 CUDA tensors [n] or None."""
+    _check(library().lap_cv_set_potentials(h, _dp(phi1_dev), _dp(phi2_dev)), h)
+
+
+def lap_cv_sums(h, n):
+    a1, a2, p2 = (np.zeros(n, dtype=np.int64) for _ in range(3))
+    _check(library().lap_cv_sums(h, _host_ptr(a1), _host_ptr(a2), _host_ptr(p2), 0), h)
+    return a1, a2, p2
+
+
+def lap_cv_estimates(h, n, beta1, beta2):
+    """Returns (ldiag, ecc, kemeny, m2_total) of the control-variate estimators."""
+    ld = np.zeros(n)
+    ec = np.zeros(n)
+    kc = np.zeros(1)
+    m2 = np.zeros(1)
+    _check(library().lap_cv_estimates(h, float(beta1), float(beta2), _host_ptr(ld), _host_ptr(ec), 0,
+                                      _host_ptr(kc), _host_ptr(m2)), h)
+    return ld, ec, float(kc[0]), float(m2[0])
+
+
+def lap_sample_trace_cv(h, n_samples, seed, y1_dev, y2_dev, m2_dev):
+    _check(library().lap_sample_trace_cv(h, int(n_samples), int(seed), _dp(y1_dev), _dp(y2_dev), _dp(m2_dev)), h)
+
+
+def lap_mlp_forward(params_dev, x_dev, rows, y_dev, stream=0):
+    _check(library().lap_mlp_forward(_dp(params_dev), _dp(x_dev), int(rows), _dp(y_dev), ctypes.c_void_p(int(stream))))
+
+
+def lap_mlp_loss_grad(params_dev, x_dev, t_dev, rows, w0, w1, grad_dev, loss_dev, stream=0):
+    _check(library().lap_mlp_loss_grad(_dp(params_dev), _dp(x_dev), _dp(t_dev), int(rows), float(w0), float(w1),
+                                       _dp(grad_dev), _dp(loss_dev), ctypes.c_void_p(int(stream))))
+
+
+def lap_adamw(params_dev, m_dev, v_dev, grad_dev, count, step, lr, beta1=0.9, beta2=0.999, eps=1e-8,
+              weight_decay=0.0, stream=0):
+    _check(library().lap_adamw(_dp(params_dev), _dp(m_dev), _dp(v_dev), _dp(grad_dev), int(count), int(step),
+                               float(lr), float(beta1), float(beta2), float(eps), float(weight_decay),
+                               ctypes.c_void_p(int(stream))))
+
+
 # ------------------------------------------------------------ convenience
 
 class LapGraph:
@@ -246,6 +313,8 @@ class LapGraph:
     def __init__(self, row_ptr, col, workspace_bytes=None, stream=None):
         import torch
         self.n = int(len(row_ptr) - 1)
+        self.row_ptr_host = row_ptr.cpu().numpy() if _is_torch(row_ptr) else np.asarray(row_ptr)
+        self.col_host = col.cpu().numpy() if _is_torch(col) else np.asarray(col)
         self.h = lap_graph_create(self.n, row_ptr, col)
         self._torch = torch
         s = stream if stream is not None else torch.cuda.current_stream()
@@ -317,3 +386,30 @@ class LapGraph:
 
     def hops(self, out=None):
         return lap_hops(self.h, self.n, out)
+
+    def features(self):
+        f = self._torch.empty((self.n, 8), dtype=self._torch.float32, device="cuda")
+        lap_features(self.h, f)
+        return f
+
+    def hitting_walks(self, reps, seed):
+        out = self._torch.empty(self.n, dtype=self._torch.int64, device="cuda")
+        lap_hitting_walks(self.h, reps, seed, out)
+        return out
+
+    def cv_set_potentials(self, phi1=None, phi2=None):
+        lap_cv_set_potentials(self.h, phi1, phi2)
+
+    def cv_sums(self):
+        return lap_cv_sums(self.h, self.n)
+
+    def cv_estimates(self, beta1, beta2):
+        return lap_cv_estimates(self.h, self.n, beta1, beta2)
+
+    def sample_trace_cv(self, n_samples, seed):
+        t = self._torch
+        y1 = t.zeros(n_samples, dtype=t.int64, device="cuda")
+        y2 = t.zeros(n_samples, dtype=t.int64, device="cuda")
+        m2 = t.zeros(n_samples, dtype=t.float64, device="cuda")
+        lap_sample_trace_cv(self.h, n_samples, seed, y1, y2, m2)
+        return y1, y2, m2
