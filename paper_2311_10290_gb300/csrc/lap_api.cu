@@ -153,8 +153,15 @@ lap_status launch(lap_graph *g, LapSampleLaunch &p, int kernel)
     p.n_pad = n_pad_of(g);
     p.stack_cap = kernel == LAP_KERNEL_COMPACT ? (uint32_t)((p.slot_bytes - p.n_pad) / 4ull) : 0u;
     LAP_CUDA(g, cudaMemsetAsync(&g->d_acc->claim, 0, sizeof(unsigned int), g->stream));
-    if (kernel == LAP_KERNEL_WIDE) LAP_CUDA(g, lap_launch_sample(p, g->stream));
-    else LAP_CUDA(g, lap_launch_sample_compact(p, g->stream));
+    const cudaError_t e = kernel == LAP_KERNEL_WIDE ? lap_launch_sample(p, g->stream) : lap_launch_sample_compact(p, g->stream);
+    if (e != cudaSuccess) {
+        char buf[256];
+        snprintf(buf, sizeof(buf), "sampler launch (kernel %d, %llu lanes, block %d, cv %d): %s", kernel,
+                 (unsigned long long)p.slots, p.block > 0 ? p.block : lap_pick_block(p.slots, p.num_sms),
+                 (p.cv_h1 || p.cv_h2) ? 1 : 0, cudaGetErrorString(e));
+        g->sticky = LAP_ERR_CUDA;
+        return fail(g, LAP_ERR_CUDA, buf);
+    }
     return LAP_OK;
 }
 
@@ -195,6 +202,13 @@ lap_status poll_status(lap_graph *g)
     if (h.status & LAP_DEV_K_OVERFLOW) {
         g->sticky = LAP_ERR_STEP_LIMIT;
         return fail(g, LAP_ERR_STEP_LIMIT, "a node was visited more than 2^30 times in one sample");
+    }
+    if (h.status & LAP_DEV_BAD_INDEX) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "internal error: node index out of range caught in the sampler (%llx)",
+                 (unsigned long long)h.pad[0]);
+        g->sticky = LAP_ERR_CUDA;
+        return fail(g, LAP_ERR_CUDA, buf);
     }
     return LAP_OK;
 }
@@ -508,14 +522,6 @@ static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, 
     if (kernel == LAP_KERNEL_COMPACT) {
         if (g->ovf_cap < n_samples) {
             cudaFree(g->d_ovf_ids);
-    cudaFree(g->d_cv_h1);
-    cudaFree(g->d_cv_S1);
-    cudaFree(g->d_cv_h2);
-    cudaFree(g->d_cv_S2);
-    cudaFree(g->d_cv_a1);
-    cudaFree(g->d_cv_a2);
-    cudaFree(g->d_cv_p2);
-    cudaFree(g->d_feat_scratch);
             g->d_ovf_ids = nullptr;
             g->ovf_cap = 0;
             if (dalloc(&g->d_ovf_ids, (size_t)n_samples) != cudaSuccess) {

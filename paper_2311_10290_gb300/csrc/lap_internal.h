@@ -24,6 +24,7 @@ enum : unsigned int {
     LAP_DEV_NOT_SYMMETRIC = 4u,
     LAP_DEV_STEP_LIMIT = 8u,
     LAP_DEV_K_OVERFLOW = 16u,
+    LAP_DEV_BAD_INDEX = 64u,       // a node index out of range was caught (write skipped)
 };
 
 // Accumulators of a handle on the device (one cache line).

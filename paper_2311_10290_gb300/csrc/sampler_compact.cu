@@ -248,7 +248,8 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
             // Control variate: add the previous draw's potential (its load was
             // issued with that draw's state and row loads).
             if (CV && cv_u >= 0) {
-                atomicAdd(&p.cv_a1[cv_u], (unsigned long long)cv_val);
+                if ((uint32_t)cv_u < (uint32_t)n) atomicAdd(&p.cv_a1[cv_u], (unsigned long long)cv_val);
+                else bad |= LAP_DEV_BAD_INDEX;
                 cv_u = -1;
             }
             // One Wilson step per iteration, so walking lanes stay converged.
@@ -357,6 +358,12 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
             const uint64_t r = lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1);
             const int32_t w = ld_col(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)), keep);
             if (CV && p.cv_h2) {
+                if ((uint32_t)h >= (uint32_t)n || (uint32_t)w >= (uint32_t)n) {
+                    bad |= LAP_DEV_BAD_INDEX;
+                    p.acc->pad[0] = ((unsigned long long)(uint32_t)h << 32) | (uint32_t)w;
+                    phase = P_CLAIM;
+                    continue;
+                }
                 const long long d = (long long)row_deg(pb), hw = p.cv_h2[w], s2 = p.cv_S2[h];
                 atomicAdd(&p.cv_a2[h], (unsigned long long)hw);
                 atomicAdd(&p.cv_p2[h], 1ull);
