@@ -192,7 +192,7 @@ def test_trained_network_reduces_kemeny_variance():
     G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 28)
     try:
         v = G.set_root()
-        y1, y2, _ = G.sample_trace(1024, 5)       # plain pilot: mean Y2 for the potential's scale
+        y1, y2 = G.sample_trace(1024, 5)          # plain pilot: mean Y2 for the potential scale
         mean_y2 = y2.double().mean().item()
         G.set_root(v)
         phi1, phi2 = CVG.potentials(G, params, mean_y2)
