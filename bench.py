@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ws-frac", type=float, default=0.6, help="fraction of free HBM lent as Wilson state")
     ap.add_argument("--ws-gb", type=float, default=0.0, help="cap on the Wilson-state workspace in GB (profiler runs)")
+    ap.add_argument("--cv-graphs", type=int, default=200, help="training graphs for the learned control variate (0: skip)")
+    ap.add_argument("--cv-batch", type=int, default=16384, help="samples per batch in the CV-vs-plain measurement")
     return ap.parse_args()
 
 
@@ -178,11 +180,13 @@ def read_truth():
     return np.array(ecc), kc, meta
 
 
-def time_to_accuracy(torch, LapGraph, seeds=10, target=1e-2):
-    """Smallest omega (doubling from 2^8) at which the mean over seeds of the
-    ECC max relative error and of the Kemeny relative error are both <= 1e-2,
-    on Erdos-Renyi G(1000, 0.01) against its dense FP64 truth; then the GPU
-    time of one fresh run to that omega."""
+def time_to_accuracy(torch, LapGraph, seeds=10, target=1e-2, params=None):
+    """Smallest omega on the grid round(256 * 2^(k/4)) at which the mean over
+    seeds of the ECC max relative error and of the Kemeny relative error are
+    both <= 1e-2, on Erdos-Renyi G(1000, 0.01) against its dense FP64 truth;
+    then the GPU time of one fresh run to that omega.  With `params` the
+    estimates are the control-variate ones (potentials from the network,
+    coefficients from pilot samples with disjoint ids)."""
     import hashlib
     from paper_2311_10290_gb300 import inputs
     g = inputs.er_1000()
@@ -192,20 +196,30 @@ def time_to_accuracy(torch, LapGraph, seeds=10, target=1e-2):
     h.update(g.col.astype("<i4").tobytes())
     if h.hexdigest() != meta.get("sha1"):
         return {"error": "dense truth file does not match the generated graph"}
+    pilot = 4096
     handles = [LapGraph(g.row_ptr, g.col, workspace_bytes=8 * g.n * 65536) for _ in range(seeds)]
-    for H in handles:
+    betas = []
+    for s, H in enumerate(handles):
         H.set_root()
-    omega, done, curve = 0, 0, []
-    found = None
-    for lg in range(8, 22):
-        target_omega = 1 << lg
+        if params is not None:
+            betas.append(cv_prepare(H, params, 500 + s, pilot=pilot, batches=4)[2:])
+
+    def estimates(k, H):
+        if params is None:
+            return H.ecc(), H.kemeny()
+        _, ec, kc, _ = H.cv_estimates(*betas[k])
+        return ec, kc
+
+    done, curve, found = 0, [], None
+    for k in range(0, 53):
+        target_omega = int(round(256 * 2.0 ** (k / 4.0)))
         e1, e2 = [], []
         for s, H in enumerate(handles):
             H.sample(target_omega - done, 1000 + s)
-        for H in handles:
-            ec = H.ecc()
+        for s, H in enumerate(handles):
+            ec, kc = estimates(s, H)
             e1.append(float(np.max(np.abs(ec - ecc_t) / ecc_t)))
-            e2.append(abs(H.kemeny() - kc_t) / kc_t)
+            e2.append(abs(kc - kc_t) / kc_t)
         done = target_omega
         curve.append((target_omega, float(np.mean(e1)), float(np.mean(e2))))
         if np.mean(e1) <= target and np.mean(e2) <= target:
@@ -213,24 +227,168 @@ def time_to_accuracy(torch, LapGraph, seeds=10, target=1e-2):
             break
     for H in handles:
         H.close()
+    label = "er_1000 (Erdos-Renyi G(1000,0.01), dense FP64 truth)"
     if found is None:
-        return {"workload": "er_1000", "reached": False, "curve": curve}
+        return {"workload": label, "reached": False, "curve": curve}
     H = LapGraph(g.row_ptr, g.col, workspace_bytes=8 * g.n * 65536)
     H.set_root()
+    prep = 0.0
+    if params is not None:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b1, b2 = cv_prepare(H, params, 7777, pilot=pilot, batches=4)[2:]
+        torch.cuda.synchronize()
+        prep = time.perf_counter() - t0
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     H.sample(found, 7)
-    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
-    H.ecc(out)
-    kc = H.kemeny()
+    if params is None:
+        out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        H.ecc(out)
+        H.kemeny()
+    else:
+        H.cv_estimates(b1, b2)
     b.record()
     torch.cuda.synchronize()
     H.close()
-    return {"workload": "er_1000 (Erdos-Renyi G(1000,0.01), dense FP64 truth)", "seeds": seeds,
-            "omega": found, "gpu_seconds": a.elapsed_time(b) / 1e3,
-            "ecc_max_rel_err_mean": curve[-1][1], "kc_rel_err_mean": curve[-1][2],
-            "curve": [{"omega": o, "ecc_max_rel": round(x, 5), "kc_rel": round(y, 6)} for o, x, y in curve]}
+    res = {"workload": label, "seeds": seeds, "omega": found, "gpu_seconds": a.elapsed_time(b) / 1e3,
+           "ecc_max_rel_err_mean": curve[-1][1], "kc_rel_err_mean": curve[-1][2],
+           "curve": [{"omega": o, "ecc_max_rel": round(x, 5), "kc_rel": round(y, 6)} for o, x, y in curve]}
+    if params is not None:
+        res["pilot_samples"] = pilot + min(pilot, 4096)
+        res["prepare_seconds"] = round(prep, 3)
+        res["note"] = ("gpu_seconds: CV sampling + CV finalize at omega; prepare_seconds: pilot samples, "
+                       "features, MLP forward and coefficient fit (wall)")
+    return res
+
+
+def note(msg):
+    """Progress line on stderr (the JSON result goes alone to stdout)."""
+    print("[bench %.1fs] %s" % (time.perf_counter() - _T0, msg), file=sys.stderr, flush=True)
+
+
+_T0 = time.perf_counter()
+
+
+# ------------------------------------------------------------ learned CV
+
+def cv_training_set(count, seed0=1000):
+    """Training graphs: Barabasi-Albert (m in 3..10) and R-MAT, n log-uniform in [1e4, 1e5]."""
+    from paper_2311_10290_gb300 import inputs
+    out = []
+    for k in range(count):
+        s = seed0 + k
+        h = np.random.Generator(np.random.PCG64(s))
+        n = int(round(math.exp(h.uniform(math.log(1e4), math.log(1e5)))))
+        if k % 2 == 0:
+            out.append(inputs.ba(n, 3 + (k // 2) % 8, seed=s))
+        else:
+            out.append(inputs.rmat(max(10, int(math.ceil(math.log2(n)))), 8, seed=s))
+    return out
+
+
+def cv_train(torch, LapGraph, count):
+    """Targets from the sampler on `count` generated graphs, then AdamW training
+    of the MLP on the library's BF16 tensor-core kernels."""
+    from paper_2311_10290_gb300 import cv as CVG
+    t0 = time.perf_counter()
+    sets, rows = [], 0
+    for tg in cv_training_set(count):
+        G = LapGraph(tg.row_ptr, tg.col, workspace_bytes=int(4e9))
+        G.set_root()
+        sets.append(CVG.training_targets(G, omega=512, reps=16, seed=11))
+        rows += tg.n - 1
+        G.close()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    params, hist = CVG.train(sets, epochs=8, batch=8192)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return params, {"training_graphs": count, "training_rows": rows,
+                    "training": "BA (m 3..10) and R-MAT (edge factor 8), n log-uniform in [1e4, 1e5], seeds from 1000; "
+                                "targets from the sampler: 512 Wilson samples and 16 v-absorbed walks per node",
+                    "data_seconds": round(t1 - t0, 2), "train_seconds": round(t2 - t1, 2),
+                    "loss_first_last_epoch": [round(hist[0], 5), round(hist[-1], 5)]}
+
+
+def cv_prepare(G, params, seed, pilot, batches):
+    """Potentials from the network, coefficients from pilot samples (disjoint ids)."""
+    from paper_2311_10290_gb300 import cv as CVG
+    mean_y2 = CVG.pilot_mean_y2(G, seed + 1, samples=min(pilot, 4096))
+    phi1, phi2 = CVG.potentials(G, params, mean_y2)
+    beta1, beta2 = CVG.fit_betas(G, phi1, phi2, seed=seed, pilot=pilot, batches=batches)
+    G.cv_set_potentials(phi1, phi2)
+    return phi1, phi2, beta1, beta2
+
+
+def cv_measurement(torch, LapGraph, g, v, params, samples_per_batch, batches):
+    """Samples needed for the same variance, CV against plain, on one graph:
+    Kemeny from per-sample traces; ECC from per-node variances of the visit
+    estimator between `batches` independent batches.  The coefficients come
+    from separate pilot samples, so both estimators stay unbiased."""
+    from paper_2311_10290_gb300.cv import _neighbour_sum_host
+    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, lap_counts
+    free, _ = torch.cuda.mem_get_info()
+    G = LapGraph(g.row_ptr, g.col, workspace_bytes=int(free * 0.5))
+    try:
+        G.set_root(v)
+        t0 = time.perf_counter()
+        phi1, phi2, beta1, beta2 = cv_prepare(G, params, 4242, pilot=2 * samples_per_batch, batches=4)
+        t_prep = time.perf_counter() - t0
+        # Kemeny: per-sample Y1 - Y2 and M2 on fresh samples.
+        a, b, m = G.sample_trace_cv(samples_per_batch, 31337)
+        est = (a - b).double().cpu().numpy()
+        cvv = est + beta2 * m.cpu().numpy()
+        kc_ratio = float(np.var(cvv) / np.var(est))
+        # ECC: per-node visit estimator in `batches` batches (fresh ids).
+        G.set_root(v)
+        G.set_option(LAP_OPT_CURSOR, samples_per_batch)          # ids after the Kemeny trace's
+        d = np.diff(g.row_ptr.astype(np.int64)).astype(np.float64)
+        s1 = _neighbour_sum_host(G, phi1)
+        prev_c, prev_a = np.zeros(g.n), np.zeros(g.n)
+        V, Z = [], []
+        for _ in range(batches):
+            G.sample(samples_per_batch, 31337)
+            c1, _, _ = lap_counts(G.h, g.n)
+            a1, _, _ = G.cv_sums()
+            c1, a1 = c1.astype(np.float64), a1.astype(np.float64)
+            dc, da = c1 - prev_c, a1 - prev_a
+            prev_c, prev_a = c1, a1
+            V.append(dc)
+            Z.append((d * da - dc * s1) / d)
+        V, Z = np.array(V), np.array(Z)
+        keep = np.ones(g.n, bool)
+        keep[v] = False
+        vp = V.var(axis=0, ddof=1)[keep]
+        vc = (V - beta1 * Z).var(axis=0, ddof=1)[keep]
+        ok = vp > 0
+        per_node = vc[ok] / vp[ok]
+        # Sampler cost with and without the CV terms (same ids, same graph).
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        G.set_root(v)
+        ev[0].record()
+        G.sample(samples_per_batch, 5)
+        ev[1].record()
+        G.set_root(v)
+        G.cv_set_potentials(None, None)
+        ev[2].record()
+        G.sample(samples_per_batch, 5)
+        ev[3].record()
+        torch.cuda.synchronize()
+        t_cv, t_plain = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    finally:
+        G.close()
+    return {"workload": g.name, "beta1": beta1, "beta2": beta2, "prepare_seconds": round(t_prep, 2),
+            "pilot_samples": 2 * samples_per_batch + min(2 * samples_per_batch, 4096),
+            "kemeny_samples_ratio": kc_ratio,
+            "ecc_visit_samples_ratio_total": float(vc[ok].sum() / vp[ok].sum()),
+            "ecc_visit_samples_ratio_median_node": float(np.median(per_node)),
+            "cv_sampler_time_ratio": t_cv / t_plain,
+            "kemeny_time_ratio_same_error": kc_ratio * t_cv / t_plain,
+            "protocol": "%d fresh samples for Kemeny (per-sample variance); %d batches of %d for per-node "
+                        "visit-count variance; ratios CV/plain on the same samples" % (samples_per_batch, batches,
+                                                                                     samples_per_batch)}
 
 
 # ------------------------------------------------------------ ours
@@ -337,11 +495,24 @@ def run_ours(args, rank, world):
     # from pinned host memory (graph create), samples, finalizes and reads the
     # ECC vector and Kemeny's constant back to the host.
     if args.e2e_steps > 0:
+        note("end to end through host buffers")
         res["e2e"] = run_e2e(args, g, torch, LapGraph, rank, world)
     if rank == 0 and not args.no_cpu and world == 1:
+        note("CPU oracle baseline")
         res["cpu_baseline"] = cpu_oracle_rate(g, v, args.seed, args.cpu_seconds)
     if rank == 0 and not args.no_tta:
+        note("time to accuracy (plain)")
         res["time_to_accuracy"] = time_to_accuracy(torch, LapGraph)
+    if rank == 0 and args.cv_graphs > 0:
+        note("control variate: training data and training")
+        params, info = cv_train(torch, LapGraph, args.cv_graphs)
+        note("control variate: CV vs plain on %s" % g.name)
+        info["graphs"] = [cv_measurement(torch, LapGraph, g, v, params, args.cv_batch, 4)]
+        if not args.no_tta:
+            note("time to accuracy (CV)")
+            info["time_to_accuracy_cv"] = time_to_accuracy(torch, LapGraph, params=params)
+        res["cv_vs_plain"] = info
+        note("done")
     if world > 1:
         import torch.distributed as dist
         dist.barrier()

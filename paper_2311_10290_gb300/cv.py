@@ -115,6 +115,18 @@ def potentials(G: LapGraph, params, mean_y2):
     return phi1, phi2
 
 
+def pilot_mean_y2(G: LapGraph, seed, samples=2048):
+    """Mean pi-start walk length E[Y2] from pilot samples whose ids (from
+    PILOT_CURSOR + 2^30) are disjoint from both the estimate's and fit_betas';
+    resets the root (counts and cursor) afterwards."""
+    root = G.root
+    G.set_root(root)
+    G.set_option(LAP_OPT_CURSOR, PILOT_CURSOR + (1 << 30))
+    _, y2 = G.sample_trace(samples, seed)
+    G.set_root(root)
+    return float(y2.double().mean().item())
+
+
 def fit_betas(G: LapGraph, phi1, phi2, seed, pilot=4096, batches=8):
     """Coefficients from pilot samples (ids from PILOT_CURSOR, disjoint from the
     estimate's): beta2 minimises Var(Y1 - Y2 + beta2 M2) over per-sample
