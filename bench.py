@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--ws-gb", type=float, default=0.0, help="cap on the Wilson-state workspace in GB (profiler runs)")
     ap.add_argument("--cv-graphs", type=int, default=200, help="training graphs for the learned control variate (0: skip)")
     ap.add_argument("--cv-batch", type=int, default=16384, help="samples per batch in the CV-vs-plain measurement")
+    ap.add_argument("--batched-graphs", type=int, default=512, help="graphs of the uneven batch (0: skip)")
+    ap.add_argument("--batched-samples", type=int, default=4096, help="samples per graph of the uneven batch")
+    ap.add_argument("--batched-order", type=int, default=0, help="unit order: 0 largest first, 1 smallest first")
     return ap.parse_args()
 
 
@@ -391,6 +394,84 @@ def cv_measurement(torch, LapGraph, g, v, params, samples_per_batch, batches):
                                                                                      samples_per_batch)}
 
 
+# ------------------------------------------------------------ uneven batch
+
+def batched_measurement(torch, args):
+    """Uneven batch: graphs of the recipe in inputs.batch_spec (ER, BA, R-MAT;
+    n log-uniform in [1e3, 1e6]; average degree in [4, 32]; own root each),
+    all sampled in one persistent CUDA-graph launch with autotuned lanes and
+    claim size.  Times one run of `batched_samples` samples per graph after a
+    warm-up run of 1/16 of them."""
+    from paper_2311_10290_gb300 import inputs
+    from paper_2311_10290_gb300.lap import LAP_BOPT_ORDER, LAP_BSTAT_CLAIM, LAP_BSTAT_LANES, LAP_BSTAT_RERUNS, LapBatch
+    t0 = time.perf_counter()
+    spec = inputs.batch_spec(count=args.batched_graphs)
+    graphs = inputs.batch_graphs(spec)
+    t_gen = time.perf_counter() - t0
+    k, seed = args.batched_samples, args.seed
+    t0 = time.perf_counter()
+    B = LapBatch([(g.row_ptr, g.col) for g in graphs])
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    try:
+        B.set_option(LAP_BOPT_ORDER, args.batched_order)
+        t0 = time.perf_counter()
+        table = B.autotune(k, seed)
+        t_tune = time.perf_counter() - t0
+        B.run(max(1, k // 16), seed + 1)
+        B.sync()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        B.run(k, seed)
+        ev[1].record()
+        B.sync()
+        ev[2].record()
+        torch.cuda.synchronize()
+        t_launch = ev[0].elapsed_time(ev[1]) / 1e3
+        t_total = ev[0].elapsed_time(ev[2]) / 1e3
+        kc = B.kemeny()
+        done = B.completion()
+        wilson = uwalk = piwalk = inserts = 0
+        for j, g in enumerate(graphs):
+            _, c2, sums = B.counts(j)
+            wilson += int(sums[1])
+            piwalk += int(sums[2])
+            uwalk += int(c2.sum(dtype=np.uint64))
+            inserts += (g.n - 1) * k
+        steps = wilson + uwalk + piwalk
+        alg_bytes = BYTES_WILSON_STEP * wilson + BYTES_TREE_INSERT * inserts + BYTES_WALK_STEP * (uwalk + piwalk)
+        peak, peak_kind = peaks()
+        achieved = alg_bytes / t_launch / 1e9
+        res = {
+            "workload": "%d uneven graphs (ER/BA/R-MAT by seed mod 3, n log-uniform in [1e3, 1e6], average degree "
+                        "uniform in [4, 32], seeds 0..%d; root = each graph's max-degree node)"
+                        % (len(graphs), len(graphs) - 1),
+            "graphs": len(graphs), "total_nodes": int(sum(g.n for g in graphs)),
+            "total_arcs": int(sum(g.arcs for g in graphs)), "largest_n": int(max(g.n for g in graphs)),
+            "samples_per_graph": k, "seconds": t_total, "launch_seconds": t_launch,
+            "walk_steps": {"wilson": wilson, "uniform_walk": uwalk, "pi_walk": piwalk},
+            "value": steps / t_total, "unit": "walk steps/s",
+            "completion_seconds": {"p50": float(np.percentile(done, 50)), "p99": float(np.percentile(done, 99)),
+                                   "max": float(done.max()), "min": float(done.min())},
+            "order": ["largest first", "smallest first", "given"][args.batched_order],
+            "lanes": B.stat(LAP_BSTAT_LANES), "claim": B.stat(LAP_BSTAT_CLAIM), "reruns": B.stat(LAP_BSTAT_RERUNS),
+            "autotune": [{"lanes": a, "claim": c, "walk_steps_per_s": round(r, 1)} for a, c, r in table],
+            "autotune_seconds": round(t_tune, 2), "generate_seconds": round(t_gen, 2),
+            "create_seconds": round(t_create, 2),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "kernel": "lewalk_batch_kernel (+ batched finalize, in one CUDA graph)",
+                         "peak_kind": peak_kind},
+            "kemeny_first_graphs": [round(float(x), 3) for x in kc[:4]],
+            "note": "seconds: CUDA graph launch (resets, persistent sampler, finalize of every graph) to results "
+                    "ready, re-runs of withdrawn samples included; completion: from the sampler's start to each "
+                    "graph's last sample",
+        }
+    finally:
+        B.close()
+    return res
+
+
 # ------------------------------------------------------------ ours
 
 def run_ours(args, rank, world):
@@ -512,6 +593,10 @@ def run_ours(args, rank, world):
             note("time to accuracy (CV)")
             info["time_to_accuracy_cv"] = time_to_accuracy(torch, LapGraph, params=params)
         res["cv_vs_plain"] = info
+    if rank == 0 and args.batched_graphs > 0:
+        note("uneven batch: %d graphs" % args.batched_graphs)
+        res["batched"] = batched_measurement(torch, args)
+    if rank == 0:
         note("done")
     if world > 1:
         import torch.distributed as dist

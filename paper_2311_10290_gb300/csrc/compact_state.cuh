@@ -1,0 +1,191 @@
+// Per-lane Wilson state of the compact samplers (sampler_compact.cu for one
+// graph, sampler_batch.cu for a batch of graphs): one byte per node and
+// sample in flight plus a per-lane stack holding the loop-erased path.
+//
+// Per node and sample one byte:   bit 7 epoch | bit 6 InTree | bit 5 OnPath | bits 0..4 draws k
+// Stack entries: node | k << 27.
+#pragma once
+
+#include "lap_internal.h"
+#include "philox.cuh"
+
+namespace lap_compact {
+
+// Functions are static: every translation unit keeps its own copy.
+
+constexpr uint32_t kBEpoch = 0x80u, kBTree = 0x40u, kBPath = 0x20u, kBK = 0x1Fu;
+constexpr uint32_t kKMax = 31u;
+constexpr int kEntryShift = 27;
+constexpr uint32_t kNodeMask = (1u << kEntryShift) - 1u;
+
+// Phases of a lane.  Each loop iteration issues at most one round of
+// dependent loads per lane; the *_IMMEDIATE phases are transitions that need
+// no load and run in the same iteration.
+enum Phase : uint32_t {
+    P_CLAIM = 0,
+    P_WALK,                // pa = state byte of the head h, pb = row record of h
+    P_SCAN,                // pq = 16 state bytes at `chunk`
+    P_USTART_IMMEDIATE,
+    P_UWALK,               // pb = row record of the walk's node (uniform start)
+    P_PISTART_IMMEDIATE,
+    P_PIWALK,              // pb = row record of the walk's node (pi start)
+    P_FINISH_IMMEDIATE
+};
+
+// L2 eviction policies (sm_80+ createpolicy) and loads/stores that use them.
+static __device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// State bytes: default L2 priority (a sector read at one step is written at
+// the next step and again at the retrace, so it should stay in L2 meanwhile;
+// evicting it early turns those writes into partial-sector fills), no L1
+// allocation (no reuse within a lane at L1 time scales).
+static __device__ __forceinline__ uint32_t ld_state(const uint8_t *a)
+{
+    uint16_t v;
+    asm volatile("ld.global.L1::no_allocate.u8 %0, [%1];" : "=h"(v) : "l"(a) : "memory");
+    return v;
+}
+static __device__ __forceinline__ void st_state(uint8_t *a, uint32_t v)
+{
+    asm volatile("st.global.L1::no_allocate.u8 [%0], %1;" ::"l"(a), "h"((uint16_t)v) : "memory");
+}
+// Path-stack entries: kept in L2 with the graph (they are re-read at the retrace).
+static __device__ __forceinline__ void st_stack(uint32_t *a, uint32_t v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
+}
+static __device__ __forceinline__ int32_t ld_col(const int32_t *a, uint64_t pol)
+{
+    int32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+static __device__ __forceinline__ uint64_t ld_row(const int2 *rowinfo, int32_t u, uint64_t pol)
+{
+    uint64_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(rowinfo + u), "l"(pol));
+    return v;
+}
+
+static __device__ __forceinline__ bool b_current(uint32_t b, uint32_t ep) { return (b & kBEpoch) == ep; }
+static __device__ __forceinline__ bool b_tree(uint32_t b, uint32_t ep) { return b_current(b, ep) && (b & kBTree); }
+static __device__ __forceinline__ bool b_path(uint32_t b, uint32_t ep) { return b_current(b, ep) && (b & kBPath); }
+static __device__ __forceinline__ uint32_t b_k(uint32_t b, uint32_t ep) { return b_current(b, ep) ? (b & kBK) : 0u; }
+static __device__ __forceinline__ int32_t row_off(uint64_t r) { return (int32_t)(uint32_t)r; }
+static __device__ __forceinline__ uint32_t row_deg(uint64_t r) { return (uint32_t)(r >> 32); }
+
+// Bit b of the result is set when byte b of the 16 bytes is not InTree
+// (InTree bytes have top bits == epoch | InTree).  Per 4-byte word: SIMD byte
+// compare, then bit 7 of each byte gathered into 4 bits by one multiply.
+static __device__ __forceinline__ uint32_t gather4(uint32_t eq) { return ((((eq >> 7) & 0x01010101u) * 0x01020408u) >> 24) & 0xFu; }
+static __device__ __forceinline__ uint32_t not_tree_mask(ulonglong2 q, uint32_t ep)
+{
+    const uint32_t want = (ep | kBTree) * 0x01010101u;
+    const uint32_t w0 = (uint32_t)q.x, w1 = (uint32_t)(q.x >> 32), w2 = (uint32_t)q.y, w3 = (uint32_t)(q.y >> 32);
+    const uint32_t t = gather4(__vcmpeq4(w0 & 0xC0C0C0C0u, want)) | (gather4(__vcmpeq4(w1 & 0xC0C0C0C0u, want)) << 4) |
+                       (gather4(__vcmpeq4(w2 & 0xC0C0C0C0u, want)) << 8) | (gather4(__vcmpeq4(w3 & 0xC0C0C0C0u, want)) << 12);
+    return ~t & 0xFFFFu;
+}
+
+// The lane keeps the 16 state bytes at `chunk` in registers (pq) as an exact
+// copy: it is the only writer of its state, so every byte it writes inside
+// the chunk is also written into pq.  Starts found in pq need no re-read.
+static __device__ __forceinline__ void pq_set(ulonglong2 &pq, int32_t chunk, uint32_t u, uint32_t b)
+{
+    const uint32_t off = u - (uint32_t)chunk;
+    if (off < 16u) {
+        const uint32_t sh = 8u * (off & 7u);
+        const unsigned long long m = ~(0xFFull << sh), v = (unsigned long long)(b & 0xFFu) << sh;
+        if (off < 8u) pq.x = (pq.x & m) | v;
+        else pq.y = (pq.y & m) | v;
+    }
+}
+
+// Marks every node on the stack InTree, keeping its draw count.  The order
+// does not matter, so entries are read 16 at a time with independent vector
+// loads (the stack is 16-byte aligned) instead of one dependent pop each.
+static __device__ __forceinline__ void commit_one(uint8_t *st, uint32_t e, uint32_t ep, ulonglong2 &pq, int32_t chunk)
+{
+    const uint32_t b = ep | kBTree | (e >> kEntryShift);
+    st[e & kNodeMask] = (uint8_t)b;
+    pq_set(pq, chunk, e & kNodeMask, b);
+}
+static __device__ __forceinline__ void commit_path(uint8_t *st, const uint32_t *stk, uint32_t sp, uint32_t ep,
+                                            ulonglong2 &pq, int32_t chunk)
+{
+    uint32_t j = 0;
+    for (; j + 16u <= sp; j += 16u) {
+        uint4 e[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e[q] = *reinterpret_cast<const uint4 *>(stk + j + 4u * q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            commit_one(st, e[q].x, ep, pq, chunk);
+            commit_one(st, e[q].y, ep, pq, chunk);
+            commit_one(st, e[q].z, ep, pq, chunk);
+            commit_one(st, e[q].w, ep, pq, chunk);
+        }
+    }
+    for (; j < sp; ++j) commit_one(st, stk[j], ep, pq, chunk);
+}
+
+// Loop closed at head h (h is on the stack): erases the entries above h
+// (OnPath cleared, draw counts kept) and removes h's own entry; returns the
+// new depth.  Reads the stack top down, one aligned group of 4 per load.
+static __device__ __forceinline__ uint32_t erase_loop(uint8_t *st, const uint32_t *stk, uint32_t sp, uint32_t ep, uint32_t h,
+                                               ulonglong2 &pq, int32_t chunk)
+{
+    for (;;) {
+        const uint32_t top = sp - 1u;
+        const uint32_t g0 = top & ~3u;
+        const uint4 e4 = *reinterpret_cast<const uint4 *>(stk + g0);
+        const uint32_t e[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+        for (int q = 3; q >= 0; --q) {
+            if ((uint32_t)q > top - g0) continue;
+            const uint32_t node = e[q] & kNodeMask;
+            if (node == h) return g0 + (uint32_t)q;
+            st[node] = (uint8_t)(ep | (e[q] >> kEntryShift));
+            pq_set(pq, chunk, node, ep | (e[q] >> kEntryShift));
+        }
+        sp = g0;
+    }
+}
+
+// Withdraws a partly run sample: subtracts the k - 1 repeat visits every
+// node of the sample has contributed (and, with the control variate, the
+// potentials h1[w] of its k draws, recomputed from their Philox keys) and
+// marks all bytes "current epoch, untouched", so that the next sample (next
+// epoch) reads them as stale.
+static __device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsigned long long *rep1, const int2 *rowinfo,
+                                const int32_t *col, const long long *h1, unsigned long long *a1, uint32_t i,
+                                uint32_t key0, uint32_t key1)
+{
+    for (int32_t base = 0; base < n; base += 16) {
+        ulonglong2 q = *reinterpret_cast<ulonglong2 *>(st + base);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+            const uint32_t byte = (uint32_t)(((b < 8 ? q.x : q.y) >> (8 * (b & 7))) & 0xFFu);
+            const uint32_t k = b_k(byte, ep);
+            if (base + b >= n) continue;
+            if (k >= 2u) atomicAdd(&rep1[base + b], (unsigned long long)(-(long long)(k - 1u)));
+            if (h1 && k) {
+                const int2 r = rowinfo[base + b];
+                long long sub = 0;
+                for (uint32_t j = 0; j < k; ++j) {
+                    const uint64_t x = lap::philox_r64((uint32_t)(base + b), j, i, 0u, key0, key1);
+                    sub += h1[col[r.x + (int64_t)lap::below(x, (uint64_t)r.y)]];
+                }
+                atomicAdd(&a1[base + b], (unsigned long long)(-sub));
+            }
+        }
+        const unsigned long long fill = 0x0101010101010101ull * (unsigned long long)ep;
+        *reinterpret_cast<ulonglong2 *>(st + base) = make_ulonglong2(fill, fill);
+    }
+}
+
+}  // namespace lap_compact

@@ -89,6 +89,63 @@ __global__ void counts_kernel(int32_t n, int32_t root, unsigned long long omega,
         cnt1[u] = (u == root) ? 0ull : omega + rep1[u];
 }
 
+// Batched forms: blockIdx.y is the graph; per graph the same chunks, block
+// reductions and operation order as the single-graph kernels above, so each
+// graph's results are bit-identical to lap_launch_finalize on that graph.
+constexpr int kRedStride = kParts + 2;
+
+__global__ void partial_batch_kernel(const LapBatchGraph *__restrict__ gs, double omega, int which, double *red)
+{
+    const LapBatchGraph &g = gs[blockIdx.y];
+    const int32_t n = g.n;
+    const int64_t chunk = ((int64_t)n + kParts - 1) / kParts;
+    const int64_t a = (int64_t)blockIdx.x * chunk;
+    const int64_t b = a + chunk < n ? a + chunk : n;
+    double acc = 0.0;
+    for (int64_t u = a + threadIdx.x; u < b; u += kBlock) {
+        double x;
+        if (which == 0) x = y_of(g.cnt2[u], __dmul_rn(omega, (double)g.rowinfo[u].y));
+        else x = g.ldiag[u];
+        acc = __dadd_rn(acc, x);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) red[(int64_t)blockIdx.y * kRedStride + blockIdx.x] = acc;
+}
+
+__global__ void total_batch_kernel(int which, double *red)
+{
+    double *part = red + (int64_t)blockIdx.x * kRedStride;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < kParts; k += kBlock) acc = __dadd_rn(acc, part[k]);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[kParts + which] = acc;
+}
+
+__global__ void ldiag_batch_kernel(const LapBatchGraph *__restrict__ gs, double omega, unsigned long long omega_u,
+                                   const double *red)
+{
+    const LapBatchGraph &g = gs[blockIdx.y];
+    const int32_t n = g.n;
+    const double lvv = __ddiv_rn(red[(int64_t)blockIdx.y * kRedStride + kParts], (double)n);
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        if (u == g.root) { g.ldiag[u] = lvv; continue; }
+        const double wd = __dmul_rn(omega, (double)g.rowinfo[u].y);
+        const double y1 = y_of(omega_u + g.rep1[u], wd);
+        const double y2 = y_of(g.cnt2[u], wd);
+        g.ldiag[u] = __dadd_rn(__dsub_rn(y1, __dmul_rn(2.0, y2)), lvv);
+    }
+}
+
+__global__ void ecc_batch_kernel(const LapBatchGraph *__restrict__ gs, const double *red)
+{
+    const LapBatchGraph &g = gs[blockIdx.y];
+    const int32_t n = g.n;
+    const double t = red[(int64_t)blockIdx.y * kRedStride + kParts + 1];
+    const double num = (double)(n - 1);
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        g.ecc[u] = __ddiv_rn(num, __dadd_rn(__dmul_rn((double)n, g.ldiag[u]), t));
+}
+
 int grid_for(int64_t n)
 {
     int64_t g = (n + kBlock - 1) / kBlock;
@@ -118,5 +175,23 @@ cudaError_t lap_launch_counts(int32_t n, int32_t root, uint64_t omega, const uns
                               unsigned long long *cnt1, cudaStream_t st)
 {
     counts_kernel<<<grid_for(n), kBlock, 0, st>>>(n, root, (unsigned long long)omega, rep1, cnt1);
+    return cudaGetLastError();
+}
+
+cudaError_t lap_launch_finalize_batch(const LapBatchGraph *graphs, int32_t n_graphs, int32_t max_n, uint64_t omega,
+                                      double *red, cudaStream_t st)
+{
+    if (n_graphs <= 0) return cudaSuccess;
+    const double w = (double)omega;
+    int gx = (int)(((int64_t)max_n + kBlock - 1) / kBlock);
+    if (gx > 64) gx = 64;
+    if (gx < 1) gx = 1;
+    const dim3 parts(kParts, (unsigned)n_graphs), nodes((unsigned)gx, (unsigned)n_graphs);
+    partial_batch_kernel<<<parts, kBlock, 0, st>>>(graphs, w, 0, red);
+    total_batch_kernel<<<n_graphs, kBlock, 0, st>>>(0, red);
+    ldiag_batch_kernel<<<nodes, kBlock, 0, st>>>(graphs, w, (unsigned long long)omega, red);
+    partial_batch_kernel<<<parts, kBlock, 0, st>>>(graphs, w, 1, red);
+    total_batch_kernel<<<n_graphs, kBlock, 0, st>>>(1, red);
+    ecc_batch_kernel<<<nodes, kBlock, 0, st>>>(graphs, red);
     return cudaGetLastError();
 }

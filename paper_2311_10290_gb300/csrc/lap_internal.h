@@ -87,6 +87,65 @@ cudaError_t lap_launch_sample(const LapSampleLaunch &p, cudaStream_t st);
 // sampler_compact.cu
 cudaError_t lap_launch_sample_compact(const LapSampleLaunch &p, cudaStream_t st);
 
+// ------------------------------------------------------------ batches
+// One graph of a batch (device descriptor).  Pointers index the batch's
+// packed arenas; row records hold offsets local to the graph's columns.
+struct LapBatchGraph {
+    const int2 *rowinfo;          // [n]
+    const int32_t *col;           // [arcs]
+    unsigned long long *rep1;     // [n] repeat Wilson visits
+    unsigned long long *cnt2;     // [n] uniform-start walk passes
+    double *ldiag;                // [n] finalize output
+    double *ecc;                  // [n] finalize output
+    int64_t arcs;
+    uint64_t step_limit;
+    int32_t n;
+    int32_t root;
+    uint32_t count;               // samples of the graph in the current run
+    uint32_t pad;
+};
+
+// Control block of a batch launch (one cache line).
+struct LapBatchCtl {
+    unsigned long long t0;        // globaltimer at kernel start (minimum over blocks)
+    unsigned long long steps;     // probe launches: walk steps taken before the deadline
+    unsigned int claim;           // next work unit
+    unsigned int status;          // LAP_DEV_* bits
+    unsigned int ovf_count;       // samples withdrawn (re-run with the 8-byte kernel)
+    unsigned int pad[9];
+};
+
+struct LapBatchLaunch {
+    const LapBatchGraph *graphs;
+    const uint2 *units;           // work units {graph, first sample}, in claim order
+    uint32_t n_units;
+    uint32_t claim;               // samples per unit (the last unit of a graph may hold fewer)
+    uint64_t seed;
+    uint64_t lanes;
+    void *ws;                     // lanes * slot_bytes
+    uint64_t slot_bytes;
+    uint64_t n_pad;               // state bytes of a slot (largest n rounded up to 256)
+    uint32_t stack_cap;
+    unsigned int *slot_meta;      // per lane: bit 31 epoch, bits 0..30 extent of bytes carrying it
+    LapDevAcc *acc;               // [graphs] sum Y1, sum Y2
+    unsigned int *done;           // [graphs] samples finished
+    unsigned long long *t_done;   // [graphs] globaltimer when the graph's last sample finished
+    LapBatchCtl *ctl;
+    uint2 *ovf;                   // [ovf_cap] withdrawn samples {graph, sample id}
+    uint32_t ovf_cap;
+    unsigned long long window_ns; // probe launches: each lane stops after this long
+    int block;
+    int num_sms;
+};
+// sampler_batch.cu
+cudaError_t lap_launch_batch(const LapBatchLaunch &p, bool probe, cudaStream_t st);
+int lap_batch_block(const LapBatchLaunch &p);
+uint64_t lap_batch_resident_lanes(int block, int num_sms);
+// finalize.cu: finalize of every graph of a batch, bit-identical per graph to
+// lap_launch_finalize; red holds graphs * (1024 + 2) doubles.
+cudaError_t lap_launch_finalize_batch(const LapBatchGraph *graphs, int32_t n_graphs, int32_t max_n, uint64_t omega,
+                                      double *red, cudaStream_t st);
+
 // Threads per block for `lanes` persistent lanes: the smallest warp multiple
 // (up to 256) that keeps at most 16 blocks per SM, so that the blocks, and
 // the lanes with them, spread evenly over all SMs.

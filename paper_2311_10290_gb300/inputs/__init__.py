@@ -165,7 +165,7 @@ def rmat_22(seed=0) -> Graph:
 def batch_spec(count=512, n_lo=1_000, n_hi=1_000_000, seed0=0):
     """(family, n, avg_degree, seed) for the uneven batch: family by seed mod 3
     (ER, BA, R-MAT), n log-uniform in [n_lo, n_hi], average degree uniform in
-    [4, 32], all drawn from a SplitMix64-style hash of the seed."""
+    [4, 32], both drawn from numpy's PCG64 seeded with 1000003 + seed."""
     out = []
     for k in range(count):
         s = seed0 + k
@@ -186,3 +186,19 @@ def batch_graph(family, n, deg, seed) -> Graph:
         g = rmat(scale, n_edges=int(round(deg / 2 * n)), seed=seed, lcc=True)
     g.name = "%s(n=%d,deg=%.1f,seed=%d)" % (family, n, deg, seed)
     return g
+
+
+def batch_graphs(spec, threads=None):
+    """batch_graph for every entry of `spec`, generated on `threads` host
+    threads (the C generator releases the GIL and keeps no global state)."""
+    from concurrent.futures import ThreadPoolExecutor
+    threads = threads or max(1, min(len(spec), os.cpu_count() or 4))
+    order = sorted(range(len(spec)), key=lambda k: -spec[k][1])      # large graphs first
+    out = [None] * len(spec)
+
+    def run(k):
+        out[k] = batch_graph(*spec[k])
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(run, order))
+    return out

@@ -28,6 +28,8 @@ STATUS = {
 LAP_OPT_STEP_LIMIT, LAP_OPT_SLOTS, LAP_OPT_BLOCK, LAP_OPT_CURSOR, LAP_OPT_KERNEL, LAP_OPT_STACK = 1, 2, 3, 4, 5, 6
 LAP_STAT_SLOTS, LAP_STAT_KERNEL, LAP_STAT_FALLBACKS = 1, 2, 3
 LAP_MLP_PARAMS = 4866
+LAP_BOPT_LANES, LAP_BOPT_CLAIM, LAP_BOPT_ORDER, LAP_BOPT_BLOCK, LAP_BOPT_STACK = 1, 2, 3, 4, 5
+LAP_BSTAT_LANES, LAP_BSTAT_CLAIM, LAP_BSTAT_UNITS, LAP_BSTAT_RERUNS, LAP_BSTAT_GRAPH_CAPTURES = 1, 2, 3, 4, 5
 
 
 class LapError(RuntimeError):
@@ -83,6 +85,25 @@ def library():
                             ctypes.c_float, ctypes.c_float, vp]),
         "lap_static_scratch_bytes": (u64, []),
         "lap_static_last_error": (ctypes.c_char_p, []),
+        "lap_batch_create": (i32, [i32, vp, vp, vp, vp, ctypes.POINTER(vp)]),
+        "lap_batch_destroy": (i32, [vp]),
+        "lap_batch_set_stream": (i32, [vp, vp]),
+        "lap_batch_set_option": (i32, [vp, i32, i64]),
+        "lap_batch_workspace_query": (i32, [vp, u64, ctypes.POINTER(u64)]),
+        "lap_batch_set_workspace": (i32, [vp, vp, u64]),
+        "lap_batch_autotune": (i32, [vp, u64, u64, ctypes.c_double, i32, vp, vp, vp, ctypes.POINTER(i32)]),
+        "lap_batch_run": (i32, [vp, u64, u64]),
+        "lap_batch_sync": (i32, [vp]),
+        "lap_batch_ecc": (i32, [vp, vp, ctypes.c_int]),
+        "lap_batch_ldiag": (i32, [vp, vp, ctypes.c_int]),
+        "lap_batch_kemeny": (i32, [vp, vp]),
+        "lap_batch_completion": (i32, [vp, vp]),
+        "lap_batch_counts": (i32, [vp, i32, vp, vp, vp, ctypes.c_int]),
+        "lap_batch_graph_info": (i32, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                       ctypes.POINTER(i64)]),
+        "lap_batch_stat": (i32, [vp, i32, ctypes.POINTER(i64)]),
+        "lap_batch_schedule": (i32, [i32, vp, i32, u64, ctypes.c_uint32, vp, vp, u64, ctypes.POINTER(u64)]),
+        "lap_batch_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -300,6 +321,141 @@ def lap_adamw(params_dev, m_dev, v_dev, grad_dev, count, step, lr, beta1=0.9, be
                                ctypes.c_void_p(int(stream))))
 
 
+# ------------------------------------------------------------ batches (include/lap_batch.h)
+
+def _bcheck(status, handle=None):
+    if status != 0:
+        msg = library().lap_batch_last_error(handle)
+        raise LapError(status, msg.decode() if msg else "")
+
+
+def lap_batch_create(graphs, roots=None):
+    """graphs: sequence of (row_ptr, col) host int32 arrays; roots: int32 per
+    graph (< 0: highest degree) or None.  Returns the handle."""
+    rps = [np.ascontiguousarray(r, dtype=np.int32) for r, _ in graphs]
+    cols = [np.ascontiguousarray(c, dtype=np.int32) for _, c in graphs]
+    ns = np.array([r.size - 1 for r in rps], dtype=np.int32)
+    rp_ptrs = (ctypes.c_void_p * len(rps))(*[r.ctypes.data for r in rps])
+    col_ptrs = (ctypes.c_void_p * len(cols))(*[c.ctypes.data for c in cols])
+    rt = None if roots is None else np.ascontiguousarray(roots, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _bcheck(library().lap_batch_create(len(rps), _host_ptr(ns), rp_ptrs, col_ptrs,
+                                       None if rt is None else _host_ptr(rt), ctypes.byref(h)))
+    return h
+
+
+def lap_batch_destroy(h):
+    _bcheck(library().lap_batch_destroy(h), h)
+
+
+def lap_batch_set_stream(h, stream_ptr):
+    _bcheck(library().lap_batch_set_stream(h, ctypes.c_void_p(int(stream_ptr))), h)
+
+
+def lap_batch_set_option(h, option, value):
+    _bcheck(library().lap_batch_set_option(h, int(option), int(value)), h)
+
+
+def lap_batch_workspace_query(h, lanes):
+    out = ctypes.c_uint64()
+    _bcheck(library().lap_batch_workspace_query(h, int(lanes), ctypes.byref(out)), h)
+    return out.value
+
+
+def lap_batch_set_workspace(h, dev_ptr, nbytes):
+    _bcheck(library().lap_batch_set_workspace(h, ctypes.c_void_p(int(dev_ptr)), int(nbytes)), h)
+
+
+def lap_batch_autotune(h, samples_per_graph, seed, window_ms=300.0, max_trials=16):
+    """Returns the probe table [(lanes, claim, steps/s), ...]."""
+    lanes = np.zeros(max_trials, dtype=np.int64)
+    claim = np.zeros(max_trials, dtype=np.int32)
+    sps = np.zeros(max_trials, dtype=np.float64)
+    rows = ctypes.c_int32()
+    _bcheck(library().lap_batch_autotune(h, int(samples_per_graph), int(seed), float(window_ms), max_trials,
+                                         _host_ptr(lanes), _host_ptr(claim), _host_ptr(sps), ctypes.byref(rows)), h)
+    k = min(rows.value, max_trials)
+    return [(int(lanes[j]), int(claim[j]), float(sps[j])) for j in range(k)]
+
+
+def lap_batch_run(h, samples_per_graph, seed):
+    _bcheck(library().lap_batch_run(h, int(samples_per_graph), int(seed)), h)
+
+
+def lap_batch_sync(h):
+    _bcheck(library().lap_batch_sync(h), h)
+
+
+def lap_batch_ecc(h, total_n, out=None):
+    if out is not None:
+        _bcheck(library().lap_batch_ecc(h, _dp(out), 1), h)
+        return out
+    a = np.zeros(total_n)
+    _bcheck(library().lap_batch_ecc(h, _host_ptr(a), 0), h)
+    return a
+
+
+def lap_batch_ldiag(h, total_n, out=None):
+    if out is not None:
+        _bcheck(library().lap_batch_ldiag(h, _dp(out), 1), h)
+        return out
+    a = np.zeros(total_n)
+    _bcheck(library().lap_batch_ldiag(h, _host_ptr(a), 0), h)
+    return a
+
+
+def lap_batch_kemeny(h, n_graphs):
+    a = np.zeros(n_graphs)
+    _bcheck(library().lap_batch_kemeny(h, _host_ptr(a)), h)
+    return a
+
+
+def lap_batch_completion(h, n_graphs):
+    a = np.zeros(n_graphs)
+    _bcheck(library().lap_batch_completion(h, _host_ptr(a)), h)
+    return a
+
+
+def lap_batch_counts(h, graph, n):
+    """Host (cnt1, cnt2, sums {omega, sum Y1, sum Y2, seed}) of one graph."""
+    c1 = np.zeros(n, dtype=np.uint64)
+    c2 = np.zeros(n, dtype=np.uint64)
+    sums = np.zeros(4, dtype=np.uint64)
+    _bcheck(library().lap_batch_counts(h, int(graph), _host_ptr(c1), _host_ptr(c2), _host_ptr(sums), 0), h)
+    return c1, c2, sums
+
+
+def lap_batch_graph_info(h, graph):
+    n, arcs, root, off = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+    _bcheck(library().lap_batch_graph_info(h, int(graph), ctypes.byref(n), ctypes.byref(arcs), ctypes.byref(root),
+                                           ctypes.byref(off)), h)
+    return n.value, arcs.value, root.value, off.value
+
+
+def lap_batch_stat(h, which):
+    out = ctypes.c_int64()
+    _bcheck(library().lap_batch_stat(h, int(which), ctypes.byref(out)), h)
+    return out.value
+
+
+def lap_batch_schedule(n, order, samples, claim):
+    """Host-only: the work-unit queue as (graph, first sample) arrays."""
+    ns = np.ascontiguousarray(n, dtype=np.int32)
+    count = ctypes.c_uint64()
+    library().lap_batch_schedule(ns.size, _host_ptr(ns), int(order), int(samples), int(claim), None, None, 0,
+                                 ctypes.byref(count))
+    ug = np.zeros(max(1, count.value), dtype=np.uint32)
+    uf = np.zeros(max(1, count.value), dtype=np.uint32)
+    _bcheck(library().lap_batch_schedule(ns.size, _host_ptr(ns), int(order), int(samples), int(claim),
+                                         _host_ptr(ug), _host_ptr(uf), ug.size, ctypes.byref(count)))
+    return ug[:count.value], uf[:count.value]
+
+
+def lap_batch_last_error(h=None):
+    m = library().lap_batch_last_error(h)
+    return m.decode() if m else ""
+
+
 # ------------------------------------------------------------ convenience
 
 class LapGraph:
@@ -413,3 +569,82 @@ class LapGraph:
         m2 = t.zeros(n_samples, dtype=t.float64, device="cuda")
         lap_sample_trace_cv(self.h, n_samples, seed, y1, y2, m2)
         return y1, y2, m2
+
+
+class LapBatch:
+    """Many graphs sampled in one persistent CUDA-graph launch (include/lap_batch.h).
+
+    graphs: sequence of (row_ptr, col) host int32 arrays; roots: per-graph
+    roots or None (highest degree).  workspace_bytes: device memory lent to
+    the sampler (default: 60% of the free device memory, capped at what the
+    resident lanes can use).
+    """
+
+    def __init__(self, graphs, roots=None, workspace_bytes=None, stream=None):
+        import torch
+        self._torch = torch
+        self.h = lap_batch_create(graphs, roots)
+        self.n_graphs = len(graphs)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        lap_batch_set_stream(self.h, s.cuda_stream)
+        info = [lap_batch_graph_info(self.h, g) for g in range(self.n_graphs)]
+        self.n = np.array([x[0] for x in info], dtype=np.int64)
+        self.arcs = np.array([x[1] for x in info], dtype=np.int64)
+        self.roots = np.array([x[2] for x in info], dtype=np.int64)
+        self.offsets = np.array([x[3] for x in info] + [int(self.n.sum())], dtype=np.int64)
+        self.total_n = int(self.n.sum())
+        per_lane = lap_batch_workspace_query(self.h, 1)
+        if workspace_bytes is None:
+            free, _ = torch.cuda.mem_get_info()
+            sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            workspace_bytes = min(int(free * 0.6), per_lane * sms * 1024)
+        workspace_bytes = max(per_lane, (int(workspace_bytes) // per_lane) * per_lane)
+        self.workspace = torch.empty(workspace_bytes + 256, dtype=torch.uint8, device="cuda")
+        aligned = (self.workspace.data_ptr() + 255) // 256 * 256
+        lap_batch_set_workspace(self.h, aligned, workspace_bytes)
+
+    def close(self):
+        if self.h is not None:
+            lap_batch_destroy(self.h)
+            self.h = None
+            self.workspace = None
+            self._torch.cuda.empty_cache()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, option, value):
+        lap_batch_set_option(self.h, option, value)
+
+    def stat(self, which):
+        return lap_batch_stat(self.h, which)
+
+    def autotune(self, samples_per_graph, seed, window_ms=300.0):
+        return lap_batch_autotune(self.h, samples_per_graph, seed, window_ms)
+
+    def run(self, samples_per_graph, seed):
+        lap_batch_run(self.h, samples_per_graph, seed)
+
+    def sync(self):
+        lap_batch_sync(self.h)
+
+    def split(self, flat):
+        return [flat[self.offsets[g]:self.offsets[g + 1]] for g in range(self.n_graphs)]
+
+    def ecc(self, out=None):
+        return lap_batch_ecc(self.h, self.total_n, out)
+
+    def ldiag(self, out=None):
+        return lap_batch_ldiag(self.h, self.total_n, out)
+
+    def kemeny(self):
+        return lap_batch_kemeny(self.h, self.n_graphs)
+
+    def completion(self):
+        return lap_batch_completion(self.h, self.n_graphs)
+
+    def counts(self, graph):
+        return lap_batch_counts(self.h, graph, int(self.n[graph]))
