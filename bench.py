@@ -493,7 +493,9 @@ def run_ours(args, rank, world):
     kernel_name = {1: "lewalk_kernel (8-byte state)", 2: "lewalk_compact_kernel (1-byte state)"}[G.stat(LAP_STAT_KERNEL)]
     B = args.batch
     total_steps = args.warmup + args.steps
-    G.set_option(LAP_OPT_CURSOR, rank * total_steps * B)
+    from paper_2311_10290_gb300.shard import allreduce_counts, id_range
+    first_id, _ = id_range(rank, world, world * total_steps * B)
+    G.set_option(LAP_OPT_CURSOR, first_id)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # larger than the 126 MB L2
     out = torch.empty(g.n, dtype=torch.float64, device="cuda")
 
@@ -522,6 +524,19 @@ def run_ours(args, rank, world):
             ev[k][2].record()
             torch.cuda.synchronize()
     c1b, c2b, sb = lap_counts(G.h, g.n)
+    merged = None
+    if world > 1:
+        # The one exchange step: sum the integer counts of all ranks, then
+        # finalize the totals on rank 0 (outside the timed region).
+        t0 = time.perf_counter()
+        tot = allreduce_counts(torch.from_numpy(c1b.view(np.int64).copy()).cuda(),
+                               torch.from_numpy(c2b.view(np.int64).copy()).cuda(),
+                               torch.from_numpy(sb[:3].view(np.int64).copy()).cuda())
+        if rank == 0:
+            G.set_counts(*tot)
+            merged = {"samples": int(tot[2][0].item()), "kemeny": G.kemeny(),
+                      "ecc_mean": float(np.mean(G.ecc())), "exchange_seconds": time.perf_counter() - t0,
+                      "exchange_bytes": 16 * g.n + 24}
     step_ms = [a.elapsed_time(c) for a, _, c in ev]
     kern_ms = [a.elapsed_time(b) for a, b, _ in ev]
     t_total = sum(step_ms) / 1e3
@@ -568,6 +583,8 @@ def run_ours(args, rank, world):
                      "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind},
         "gpu_launches": args.steps * 7,
     }
+    if merged:
+        res["merged_estimate"] = merged
     res["clocks"] = clk.summary()
     G.close()
     del flush, out

@@ -199,6 +199,23 @@ lap_status lap_kemeny(lap_graph *g, double *out1);
  */
 lap_status lap_counts(lap_graph *g, uint64_t *cnt1, uint64_t *cnt2, uint64_t *sums, int on_device);
 
+/*
+ * Replaces the handle's counts with given totals, in lap_counts' layout:
+ * cnt1[n], cnt2[n] and sums[3] = { omega, sum Y1, sum Y2 }.  The use is the
+ * one exchange step of a run split over processes or GPUs: each draws a
+ * disjoint sample-id range (LAP_OPT_CURSOR), the integer counts are summed
+ * (an all-reduce of 16 n + 24 bytes), and one handle finalizes the totals
+ * with lap_ecc / lap_ldiag / lap_kemeny, exactly as if it had drawn every
+ * sample itself (Alg. 2 and Alg. 4 estimate from these sums only).  Also
+ * restores a checkpoint taken with lap_counts.  Requires lap_set_root (same
+ * root as the counts); cnt1[v] must be 0 and cnt1[u] >= omega >= 1 for
+ * u != v (else LAP_ERR_INVALID_ARG).  Control-variate sums are not part of
+ * the state and are cleared.  Later lap_sample calls add to these totals
+ * (ids continue from the handle's cursor).  Host or device buffers
+ * (on_device).  Synchronises.
+ */
+lap_status lap_set_counts(lap_graph *g, const uint64_t *cnt1, const uint64_t *cnt2, const uint64_t *sums, int on_device);
+
 /* ------------------------------------------------------------------------
  * Learned control variate.  The paper has no control variate; these entry
  * points add one that keeps every estimator unbiased.  For an integer

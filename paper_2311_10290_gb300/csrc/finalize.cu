@@ -146,6 +146,24 @@ __global__ void ecc_batch_kernel(const LapBatchGraph *__restrict__ gs, const dou
         g.ecc[u] = __ddiv_rn(num, __dadd_rn(__dmul_rn((double)n, g.ldiag[u]), t));
 }
 
+// rep1[u] = cnt1[u] - omega (u != v); flags counts that cannot come from
+// omega samples (cnt1[v] != 0 or cnt1[u] < omega).
+__global__ void rep_from_counts_kernel(int32_t n, int32_t root, unsigned long long omega,
+                                       const unsigned long long *__restrict__ cnt1, unsigned long long *rep1,
+                                       unsigned int *bad)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long c = cnt1[u];
+        if (u == root) {
+            rep1[u] = 0ull;
+            if (c != 0ull) atomicOr(bad, 1u);
+        } else {
+            rep1[u] = c >= omega ? c - omega : 0ull;
+            if (c < omega) atomicOr(bad, 1u);
+        }
+    }
+}
+
 int grid_for(int64_t n)
 {
     int64_t g = (n + kBlock - 1) / kBlock;
@@ -193,5 +211,12 @@ cudaError_t lap_launch_finalize_batch(const LapBatchGraph *graphs, int32_t n_gra
     partial_batch_kernel<<<parts, kBlock, 0, st>>>(graphs, w, 1, red);
     total_batch_kernel<<<n_graphs, kBlock, 0, st>>>(1, red);
     ecc_batch_kernel<<<nodes, kBlock, 0, st>>>(graphs, red);
+    return cudaGetLastError();
+}
+
+cudaError_t lap_launch_rep_from_counts(int32_t n, int32_t root, uint64_t omega, const unsigned long long *cnt1,
+                                       unsigned long long *rep1, unsigned int *bad, cudaStream_t st)
+{
+    rep_from_counts_kernel<<<grid_for(n), kBlock, 0, st>>>(n, root, (unsigned long long)omega, cnt1, rep1, bad);
     return cudaGetLastError();
 }

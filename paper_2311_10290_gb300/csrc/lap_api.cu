@@ -631,6 +631,56 @@ lap_status lap_counts(lap_graph *g, uint64_t *cnt1, uint64_t *cnt2, uint64_t *su
     return LAP_OK;
 }
 
+lap_status lap_set_counts(lap_graph *g, const uint64_t *cnt1, const uint64_t *cnt2, const uint64_t *sums, int on_device)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (!cnt1 || !cnt2 || !sums) return fail(g, LAP_ERR_INVALID_ARG, "cnt1, cnt2 and sums must be set");
+    if ((s = poll_status(g)) != LAP_OK) return s;
+    uint64_t h3[3];
+    const size_t bytes = sizeof(uint64_t) * (size_t)g->n;
+    if (on_device) {
+        LAP_CUDA(g, cudaMemcpyAsync(h3, sums, sizeof(h3), cudaMemcpyDeviceToHost, g->stream));
+        LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    } else {
+        memcpy(h3, sums, sizeof(h3));
+    }
+    if (h3[0] == 0) return fail(g, LAP_ERR_INVALID_ARG, "omega (sums[0]) must be >= 1");
+    // cnt1 is staged in the ldiag buffer (finalize overwrites it anyway).
+    unsigned long long *stage = reinterpret_cast<unsigned long long *>(g->d_ldiag);
+    unsigned int *bad = reinterpret_cast<unsigned int *>(g->d_red);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    LAP_CUDA(g, cudaMemcpyAsync(stage, cnt1, bytes, kind, g->stream));
+    LAP_CUDA(g, cudaMemsetAsync(bad, 0, sizeof(unsigned int), g->stream));
+    LAP_CUDA(g, lap_launch_rep_from_counts(g->n, g->root, h3[0], stage, g->d_rep1, bad, g->stream));
+    unsigned int hb = 0;
+    LAP_CUDA(g, cudaMemcpyAsync(&hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, g->stream));
+    LAP_CUDA(g, cudaMemcpyAsync(g->d_cnt2, cnt2, bytes, kind, g->stream));
+    LapDevAcc acc;
+    memset(&acc, 0, sizeof(acc));
+    acc.sum_y1 = h3[1];
+    acc.sum_y2 = h3[2];
+    LAP_CUDA(g, cudaMemcpyAsync(g->d_acc, &acc, sizeof(acc), cudaMemcpyHostToDevice, g->stream));
+    if (g->d_cv_a1) {
+        LAP_CUDA(g, cudaMemsetAsync(g->d_cv_a1, 0, bytes, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_cv_a2, 0, bytes, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_cv_p2, 0, bytes, g->stream));
+    }
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    g->omega = h3[0];
+    g->results_valid = false;
+    if (hb) {
+        LAP_CUDA(g, cudaMemsetAsync(g->d_rep1, 0, bytes, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_cnt2, 0, bytes, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_acc, 0, sizeof(LapDevAcc), g->stream));
+        LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+        g->omega = 0;
+        return fail(g, LAP_ERR_INVALID_ARG, "counts inconsistent with omega samples (cnt1[v] != 0 or cnt1[u] < omega)");
+    }
+    return LAP_OK;
+}
+
 lap_status lap_hops(lap_graph *g, int32_t *out, int on_device)
 {
     lap_status s = check_sticky(g);

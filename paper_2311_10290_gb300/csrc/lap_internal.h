@@ -184,6 +184,8 @@ cudaError_t lap_launch_finalize(const int2 *rowinfo, int32_t n, int32_t root, ui
                                 double *ldiag, double *ecc, double *red, cudaStream_t st);
 cudaError_t lap_launch_counts(int32_t n, int32_t root, uint64_t omega, const unsigned long long *rep1,
                               unsigned long long *cnt1, cudaStream_t st);
+cudaError_t lap_launch_rep_from_counts(int32_t n, int32_t root, uint64_t omega, const unsigned long long *cnt1,
+                                       unsigned long long *rep1, unsigned int *bad, cudaStream_t st);
 
 struct lap_graph {
     int device = 0;

@@ -69,6 +69,7 @@ def library():
         "lap_kemeny": (i32, [vp, vp]),
         "lap_counts": (i32, [vp, vp, vp, vp, ctypes.c_int]),
         "lap_hops": (i32, [vp, vp, ctypes.c_int]),
+        "lap_set_counts": (i32, [vp, vp, vp, vp, ctypes.c_int]),
         "lap_get_stat": (i32, [vp, i32, ctypes.POINTER(i64)]),
         "lap_graph_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]),
         "lap_last_error": (ctypes.c_char_p, [vp]),
@@ -230,6 +231,18 @@ def lap_counts(h, n, per_node=True):
     _check(library().lap_counts(h, None if c1 is None else _host_ptr(c1), None if c2 is None else _host_ptr(c2),
                                 _host_ptr(s), 0), h)
     return c1, c2, s
+
+
+def lap_set_counts(h, cnt1, cnt2, sums):
+    """Replaces the handle's counts: cnt1, cnt2 uint64/int64 [n] and sums
+    {omega, sum Y1, sum Y2}, all host numpy arrays or all CUDA tensors."""
+    if _is_torch(cnt1):
+        _check(library().lap_set_counts(h, _dp(cnt1), _dp(cnt2), _dp(sums), 1), h)
+        return
+    c1 = np.ascontiguousarray(cnt1, dtype=np.uint64)
+    c2 = np.ascontiguousarray(cnt2, dtype=np.uint64)
+    s3 = np.ascontiguousarray(np.asarray(sums)[:3], dtype=np.uint64)
+    _check(library().lap_set_counts(h, _host_ptr(c1), _host_ptr(c2), _host_ptr(s3), 0), h)
 
 
 def lap_get_stat(h, stat):
@@ -542,6 +555,9 @@ class LapGraph:
 
     def hops(self, out=None):
         return lap_hops(self.h, self.n, out)
+
+    def set_counts(self, cnt1, cnt2, sums):
+        lap_set_counts(self.h, cnt1, cnt2, sums)
 
     def features(self):
         f = self._torch.empty((self.n, 8), dtype=self._torch.float32, device="cuda")

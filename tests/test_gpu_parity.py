@@ -311,3 +311,46 @@ def test_small_workload_accuracy():
     kc = D.kemeny(g.n, g.row_ptr, g.col)
     assert np.max(np.abs(r["ecc"] - ec) / ec) < 0.06
     assert abs(r["kc"] - kc) / kc < 0.02
+
+
+def test_sharded_ranges_merge_with_set_counts():
+    """Two handles draw disjoint sample-id ranges (LAP_OPT_CURSOR), their
+    counts are summed on the host and loaded into a third handle with
+    lap_set_counts: ECC and Kemeny equal, bit for bit, those of one handle
+    that drew every id; the totals equal the oracle's."""
+    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, LapError, LapGraph
+    from paper_2311_10290_gb300.shard import id_range
+    g = I.ba(3000, 4, seed=12)
+    total, seed = 900, 41
+    parts = []
+    for r in range(2):
+        first, count = id_range(r, 2, total)
+        G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 26)
+        try:
+            G.set_root()
+            G.set_option(LAP_OPT_CURSOR, first)
+            G.sample(count, seed)
+            parts.append(G.counts())
+        finally:
+            G.close()
+    c1 = parts[0][0] + parts[1][0]
+    c2 = parts[0][1] + parts[1][1]
+    s3 = np.array([total, int(parts[0][2][1]) + int(parts[1][2][1]), int(parts[0][2][2]) + int(parts[1][2][2])],
+                  dtype=np.uint64)
+    G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 26)
+    H = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 26)
+    try:
+        v = G.set_root()
+        G.set_counts(c1, c2, s3)
+        H.set_root()
+        H.sample(total, seed)
+        assert np.array_equal(G.ecc(), H.ecc()) and G.kemeny() == H.kemeny()
+        o = oracle.sample(g.row_ptr, g.col, v, seed, 0, total, keep_per_sample=False)
+        assert np.array_equal(c1, o.cnt1) and np.array_equal(c2, o.cnt2)
+        bad = c1.copy()
+        bad[(v + 1) % g.n] = 0
+        with pytest.raises(LapError, match="LAP_ERR_INVALID_ARG"):
+            G.set_counts(bad, c2, s3)
+    finally:
+        G.close()
+        H.close()
