@@ -76,10 +76,11 @@ typedef enum {
                                   first sample after lap_set_root.  Lets several processes or GPUs
                                   draw disjoint sample-id ranges whose counts add up exactly. */
     LAP_OPT_KERNEL = 5,        /* 0 = automatic, 1 = 8-byte state per node, 2 = 1-byte state per node
-                                  (default when n < 2^27).  A sample that does not fit kernel 2 (a
-                                  node drawn more than 31 times, or a loop-erased path longer than
-                                  the stack) is withdrawn and re-run with kernel 1: results are
-                                  identical either way. */
+                                  (default when n < 2^27).  Kernel 2 keeps draw counts above 30 in a
+                                  256-entry table per sample.  A sample that does not fit kernel 2
+                                  (more such nodes than the table holds, or a loop-erased path
+                                  longer than the stack) is withdrawn and re-run with kernel 1:
+                                  results are identical either way. */
     LAP_OPT_STACK = 6          /* loop-erased path capacity per sample of kernel 2; 0 = default
                                   (16 sqrt(n) rounded up to a power of two, at least 1024) */
 } lap_option;
@@ -126,8 +127,9 @@ lap_status lap_set_option(lap_graph *g, int32_t option, int64_t value);
 
 /*
  * Device workspace for the per-sample Wilson state (8 bytes per node per
- * sample in flight with kernel 1; n rounded up to 256 plus 4 bytes per
- * stack entry with kernel 2).  lap_workspace_query returns the bytes the
+ * sample in flight with kernel 1; with kernel 2, n rounded up to 256, plus
+ * 4 bytes per stack entry, plus 2048 bytes of draw-count table, rounded up to
+ * 256).  lap_workspace_query returns the bytes the
  * current kernel needs to keep `slots` samples in flight.  lap_set_workspace lends the handle a caller-owned
  * device buffer (at least 8*n bytes, 256-byte aligned), which must stay alive
  * while the handle uses it; the handle zeroes it.  Without a workspace,

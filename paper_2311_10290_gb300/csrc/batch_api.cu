@@ -136,7 +136,10 @@ uint32_t stack_cap_of(const lap_batch *b)
 
 uint64_t n_pad_of(const lap_batch *b) { return ((uint64_t)b->max_n + 255ull) & ~255ull; }
 
-uint64_t slot_bytes_of(const lap_batch *b) { return (n_pad_of(b) + 4ull * stack_cap_of(b) + 255ull) & ~255ull; }
+uint64_t slot_bytes_of(const lap_batch *b)
+{
+    return (n_pad_of(b) + 4ull * stack_cap_of(b) + LAP_COMPACT_TABLE_BYTES + 255ull) & ~255ull;
+}
 
 // Work units in claim order (shared by lap_batch_run and lap_batch_schedule).
 void build_units(int32_t G, const int32_t *n, int order, uint64_t samples, uint32_t claim, std::vector<uint2> &out)
@@ -255,7 +258,7 @@ LapBatchLaunch make_launch(const lap_batch *b, uint64_t seed, uint64_t lanes, ui
     p.ws = b->ws;
     p.slot_bytes = slot_bytes_of(b);
     p.n_pad = n_pad_of(b);
-    p.stack_cap = (uint32_t)((p.slot_bytes - p.n_pad) / 4ull);
+    p.stack_cap = (uint32_t)((p.slot_bytes - p.n_pad - LAP_COMPACT_TABLE_BYTES) / 4ull);
     p.slot_meta = b->d_slot_meta;
     p.acc = b->d_acc;
     p.done = b->d_done;

@@ -3,7 +3,14 @@
 // sample in flight plus a per-lane stack holding the loop-erased path.
 //
 // Per node and sample one byte:   bit 7 epoch | bit 6 InTree | bit 5 OnPath | bits 0..4 draws k
-// Stack entries: node | k << 27.
+// Stack entries: node | k << 27 (k as in the byte).
+//
+// Draw counts k <= 30 live in the byte.  From the 31st draw at a node on, the
+// byte holds kKSat and the count lives in a per-lane open-addressing table
+// after the path stack (kTblEntries entries {node + 1 : 32 | k : 32}); the
+// table is cleared before a sample that follows one that used it.  A sample
+// that needs more table entries than fit (kTblProbes probes), more than
+// kKMax draws at a node, or a longer path than the stack holds is withdrawn.
 #pragma once
 
 #include "lap_internal.h"
@@ -14,7 +21,12 @@ namespace lap_compact {
 // Functions are static: every translation unit keeps its own copy.
 
 constexpr uint32_t kBEpoch = 0x80u, kBTree = 0x40u, kBPath = 0x20u, kBK = 0x1Fu;
-constexpr uint32_t kKMax = 31u;
+constexpr uint32_t kKSat = 31u;                 // byte value: "count in the table"
+constexpr uint32_t kKMax = 1u << 24;             // draws at one node in one sample
+constexpr uint64_t kTblBytes = LAP_COMPACT_TABLE_BYTES;
+constexpr uint32_t kTblEntries = (uint32_t)(kTblBytes / 8u);    // a power of two
+constexpr uint32_t kTblProbes = 32u;
+static_assert(kTblEntries == 256u, "tbl_home maps to 8 bits");
 constexpr int kEntryShift = 27;
 constexpr uint32_t kNodeMask = (1u << kEntryShift) - 1u;
 
@@ -156,6 +168,46 @@ static __device__ __forceinline__ uint32_t erase_loop(uint8_t *st, const uint32_
     }
 }
 
+// The table follows the `cap` stack entries of the slot.
+static __device__ __forceinline__ unsigned long long *tbl_of(uint32_t *stk, uint32_t cap)
+{
+    return reinterpret_cast<unsigned long long *>(stk + cap);
+}
+
+static __device__ __forceinline__ uint32_t tbl_home(uint32_t node) { return (node * 2654435761u) >> 24; }
+
+// True draw count of a node whose byte holds kKSat (0 if absent: an error).
+static __device__ __forceinline__ uint32_t tbl_get(const unsigned long long *tbl, uint32_t node)
+{
+    uint32_t s = tbl_home(node);
+    for (uint32_t q = 0; q < kTblProbes; ++q, s = (s + 1u) & (kTblEntries - 1u)) {
+        const unsigned long long e = tbl[s];
+        if ((uint32_t)(e >> 32) == node + 1u) return (uint32_t)e;
+        if (e == 0ull) break;
+    }
+    return 0u;
+}
+
+// Sets a node's count (inserting it); false when its probe run is full.
+static __device__ __forceinline__ bool tbl_put(unsigned long long *tbl, uint32_t node, uint32_t k)
+{
+    uint32_t s = tbl_home(node);
+    for (uint32_t q = 0; q < kTblProbes; ++q, s = (s + 1u) & (kTblEntries - 1u)) {
+        const unsigned long long e = tbl[s];
+        if (e == 0ull || (uint32_t)(e >> 32) == node + 1u) {
+            tbl[s] = ((unsigned long long)(node + 1u) << 32) | k;
+            return true;
+        }
+    }
+    return false;
+}
+
+static __device__ __forceinline__ void tbl_clear(unsigned long long *tbl)
+{
+    uint4 *t = reinterpret_cast<uint4 *>(tbl);
+    for (uint32_t j = 0; j < (uint32_t)(kTblBytes / 16u); ++j) t[j] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 // Withdraws a partly run sample: subtracts the k - 1 repeat visits every
 // node of the sample has contributed (and, with the control variate, the
 // potentials h1[w] of its k draws, recomputed from their Philox keys) and
@@ -163,14 +215,14 @@ static __device__ __forceinline__ uint32_t erase_loop(uint8_t *st, const uint32_
 // epoch) reads them as stale.
 static __device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsigned long long *rep1, const int2 *rowinfo,
                                 const int32_t *col, const long long *h1, unsigned long long *a1, uint32_t i,
-                                uint32_t key0, uint32_t key1)
+                                uint32_t key0, uint32_t key1, const unsigned long long *tbl)
 {
     for (int32_t base = 0; base < n; base += 16) {
         ulonglong2 q = *reinterpret_cast<ulonglong2 *>(st + base);
 #pragma unroll
         for (int b = 0; b < 16; ++b) {
             const uint32_t byte = (uint32_t)(((b < 8 ? q.x : q.y) >> (8 * (b & 7))) & 0xFFu);
-            const uint32_t k = b_k(byte, ep);
+            const uint32_t k = b_k(byte, ep);          // kKSat for a node in the table: its first 31 draws
             if (base + b >= n) continue;
             if (k >= 2u) atomicAdd(&rep1[base + b], (unsigned long long)(-(long long)(k - 1u)));
             if (h1 && k) {
@@ -185,6 +237,24 @@ static __device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsi
         }
         const unsigned long long fill = 0x0101010101010101ull * (unsigned long long)ep;
         *reinterpret_cast<ulonglong2 *>(st + base) = make_ulonglong2(fill, fill);
+    }
+    // Draws kKSat .. k-1 of the nodes in the count table (exactly the nodes
+    // whose byte held kKSat).
+    for (uint32_t j = 0; j < kTblEntries; ++j) {
+        const unsigned long long e = tbl[j];
+        if (e == 0ull) continue;
+        const uint32_t node = (uint32_t)(e >> 32) - 1u, k = (uint32_t)e;
+        if ((int32_t)node >= n || k <= kKSat) continue;
+        atomicAdd(&rep1[node], (unsigned long long)(-(long long)(k - kKSat)));
+        if (h1) {
+            const int2 r = rowinfo[node];
+            long long sub = 0;
+            for (uint32_t d = kKSat; d < k; ++d) {
+                const uint64_t x = lap::philox_r64(node, d, i, 0u, key0, key1);
+                sub += h1[col[r.x + (int64_t)lap::below(x, (uint64_t)r.y)]];
+            }
+            atomicAdd(&a1[node], (unsigned long long)(-sub));
+        }
     }
 }
 

@@ -159,6 +159,10 @@ inline int lap_pick_block(uint64_t lanes, int num_sms)
 
 enum LapKernel : int { LAP_KERNEL_WIDE = 1, LAP_KERNEL_COMPACT = 2 };
 
+// Compact kernels: bytes per slot for the table of draw counts above 30
+// (after the path stack; see compact_state.cuh).
+constexpr uint64_t LAP_COMPACT_TABLE_BYTES = 2048;
+
 // Control variate (cv.cu, mlp.cu).
 constexpr int LAP_CV_FIXED_POINT_BITS = 16;   // h = round(2^16 phi)
 constexpr int LAP_CV_ABSORB_ITERS = 8;        // feature f7: P(hit v within 8 steps)

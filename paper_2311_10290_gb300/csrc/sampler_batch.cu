@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(256) lewalk_batch_kernel(LapBatchLaunch p)
     unsigned long long probe_steps = 0;
     uint32_t iter = 0;
     unsigned int bad = 0;
+    bool tbl_dirty = true;    // the count table may hold entries (cleared before the next sample)
 
     for (;;) {
         if (PROBE && ((++iter & 255u) == 0u) && global_ns() > t_stop) break;
@@ -99,11 +100,22 @@ __global__ void __launch_bounds__(256) lewalk_batch_kernel(LapBatchLaunch p)
             const uint32_t b = pa;
             if (!b_tree(b, ep)) {
                 if (b_path(b, ep)) sp = erase_loop(st, stk, sp, ep, (uint32_t)h, pq, chunk);
-                const uint32_t kh = b_k(b, ep);
+                uint32_t kh = b_k(b, ep);
+                if (kh == kKSat) {
+                    kh = tbl_get(tbl_of(stk, cap), (uint32_t)h);
+                    if (kh < kKSat) { bad |= LAP_DEV_BAD_INDEX; phase = P_CLAIM; continue; }
+                }
                 if (kh) w = ld_col(col + off + (int64_t)lap::below(lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1), deg), keep);
                 const uint32_t kn = kh + 1u;
-                if (kn > kKMax || sp >= cap) {
-                    withdraw_sample(st, n, ep, rep1, rowinfo, col, nullptr, nullptr, i, key0, key1);
+                uint32_t kb = kn;
+                bool fits = kn <= kKMax && sp < cap;
+                if (fits && kn >= kKSat) {
+                    kb = kKSat;
+                    fits = tbl_put(tbl_of(stk, cap), (uint32_t)h, kn);
+                    tbl_dirty = true;
+                }
+                if (!fits) {
+                    withdraw_sample(st, n, ep, rep1, rowinfo, col, nullptr, nullptr, i, key0, key1, tbl_of(stk, cap));
                     const unsigned int ix = atomicAdd(&p.ctl->ovf_count, 1u);
                     if (ix < p.ovf_cap) p.ovf[ix] = make_uint2((uint32_t)gi, i);
                     else bad |= LAP_DEV_K_OVERFLOW;
@@ -111,12 +123,12 @@ __global__ void __launch_bounds__(256) lewalk_batch_kernel(LapBatchLaunch p)
                     phase = P_CLAIM;
                     continue;
                 }
-                const uint32_t e = (uint32_t)h | (kn << kEntryShift);
+                const uint32_t e = (uint32_t)h | (kb << kEntryShift);
                 if (sp == 0) e0 = e;
                 st_stack(stk + sp, e, keep);
                 ++sp;
-                st_state(st + h, ep | kBPath | kn);
-                pq_set(pq, chunk, (uint32_t)h, ep | kBPath | kn);
+                st_state(st + h, ep | kBPath | kb);
+                pq_set(pq, chunk, (uint32_t)h, ep | kBPath | kb);
                 if (kh) atomicAdd(&rep1[h], 1ull);
                 if (PROBE) ++probe_steps;
                 if (++y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
@@ -225,6 +237,10 @@ __global__ void __launch_bounds__(256) lewalk_batch_kernel(LapBatchLaunch p)
             // Bytes [0, n) must carry the current epoch before it flips.
             if (n > extent) stamp(st, extent, n, ep);
             extent = n;
+            if (tbl_dirty) {
+                tbl_clear(tbl_of(stk, cap));
+                tbl_dirty = false;
+            }
             ep ^= kBEpoch;
             st[v] = (uint8_t)(ep | kBTree);
             s = 0;

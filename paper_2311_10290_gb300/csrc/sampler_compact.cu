@@ -19,9 +19,10 @@
 // draw is still the next entry of the node's stack.
 //
 // Every node's byte keeps its draw count k for the whole sample (also once
-// InTree), and the repeat-visit counter has received exactly k - 1 for every
-// node touched so far.  A sample that cannot be represented (a node drawn
-// more than 31 times, or a loop-erased path longer than the stack) is
+// InTree; counts above 30 go to the lane's count table, see
+// compact_state.cuh), and the repeat-visit counter has received exactly
+// k - 1 for every node touched so far.  A sample that cannot be represented
+// (the count table full, or a loop-erased path longer than the stack) is
 // therefore withdrawn exactly: the lane subtracts k - 1 for every node of
 // the sample, re-stamps its state bytes with the current epoch (so the next
 // sample sees them all as stale), appends the sample id to an overflow list
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
     long long cv_val = 0;
     unsigned long long acc1 = 0, acc2 = 0;
     unsigned int bad = 0;
+    bool tbl_dirty = true;    // the count table may hold entries (cleared before the next sample)
 
     for (;;) {
         if (phase == P_WALK) {
@@ -88,22 +90,33 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
             const uint32_t b = pa;
             if (!b_tree(b, ep)) {
                 if (b_path(b, ep)) sp = erase_loop(st, stk, sp, ep, (uint32_t)h, pq, chunk);
-                const uint32_t kh = b_k(b, ep);
+                uint32_t kh = b_k(b, ep);
+                if (kh == kKSat) {
+                    kh = tbl_get(tbl_of(stk, cap), (uint32_t)h);
+                    if (kh < kKSat) { bad |= LAP_DEV_BAD_INDEX; phase = P_CLAIM; continue; }
+                }
                 if (kh) w = ld_col(col + off + (int64_t)lap::below(lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1), deg), keep);
                 const uint32_t kn = kh + 1u;
-                if (kn > kKMax || sp >= cap) {
-                    withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1);
+                uint32_t kb = kn;
+                bool fits = kn <= kKMax && sp < cap;
+                if (fits && kn >= kKSat) {
+                    kb = kKSat;
+                    fits = tbl_put(tbl_of(stk, cap), (uint32_t)h, kn);
+                    tbl_dirty = true;
+                }
+                if (!fits) {
+                    withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1, tbl_of(stk, cap));
                     const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
                     if (ix < p.count) p.ovf_ids[ix] = i;
                     phase = P_CLAIM;
                     continue;
                 }
-                const uint32_t e = (uint32_t)h | (kn << kEntryShift);
+                const uint32_t e = (uint32_t)h | (kb << kEntryShift);
                 if (sp == 0) e0 = e;
                 st_stack(stk + sp, e, keep);
                 ++sp;
-                st_state(st + h, ep | kBPath | kn);
-                pq_set(pq, chunk, (uint32_t)h, ep | kBPath | kn);
+                st_state(st + h, ep | kBPath | kb);
+                pq_set(pq, chunk, (uint32_t)h, ep | kBPath | kb);
                 if (kh) atomicAdd(&p.rep1[h], 1ull);
                 if (++y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
                 if (CV && p.cv_h1) {
@@ -215,6 +228,10 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
             const unsigned int q = atomicAdd(&p.acc->claim, 1u);
             if (q >= p.count) break;
             i = p.first + q;
+            if (tbl_dirty) {
+                tbl_clear(tbl_of(stk, cap));
+                tbl_dirty = false;
+            }
             ep ^= kBEpoch;
             st[v] = (uint8_t)(ep | kBTree);
             s = 0;

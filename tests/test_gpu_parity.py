@@ -104,17 +104,21 @@ def test_compact_kernel_is_the_default_and_does_not_fall_back_on_social_graphs()
     assert_parity(g, r, c, 2000)
 
 
-@pytest.mark.parametrize("name,maker,root,stack", [
-    ("path_end_kmax", lambda: I.path(60), 0, None),      # far nodes are drawn more than 31 times
-    ("cycle_long_paths", lambda: I.cycle(301), 0, 16),   # loop-erased paths longer than 16
+@pytest.mark.parametrize("name,maker,root,stack,falls_back", [
+    ("path_end_counts_table", lambda: I.path(60), 0, None, False),   # far nodes drawn > 30 times: count table
+    ("star_leaf_root_hub_table", lambda: I.star(200), 1, None, False),  # the hub is drawn ~199 times per sample
+    ("path_far_root_table_full", lambda: I.path(400), 399, None, True),  # ~380 nodes drawn > 30 times
+    ("cycle_long_paths", lambda: I.cycle(301), 0, 16, True),         # loop-erased paths longer than the stack
 ])
-def test_compact_overflow_rolls_back_to_wide_kernel(name, maker, root, stack):
-    """Samples that do not fit the 1-byte state are re-run with the 8-byte
-    kernel from the counts saved before the launch: results stay exact."""
+def test_compact_overflow_rolls_back_to_wide_kernel(name, maker, root, stack, falls_back):
+    """Draw counts above 30 live in the compact kernel's per-sample count
+    table; samples that still do not fit (table full, path longer than the
+    stack) are withdrawn and re-run with the 8-byte kernel: results stay
+    exact either way."""
     g = maker()
     st = {}
     r = gpu_run(g, 3, 300, root=root, kernel=2, stack=stack, splits=[100, 200], stats=st)
-    assert st["fallbacks"] >= 1
+    assert (st["fallbacks"] >= 1) == falls_back, st
     c = oracle_run(g, root, 3, 300, threads=4)
     assert_parity(g, r, c, 300)
 
