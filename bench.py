@@ -91,7 +91,19 @@ def parse():
     ap.add_argument("--cv-batch", type=int, default=16384, help="samples per batch in the CV-vs-plain measurement")
     ap.add_argument("--batched-graphs", type=int, default=512, help="graphs of the uneven batch (0: skip)")
     ap.add_argument("--batched-samples", type=int, default=4096, help="samples per graph of the uneven batch")
-    ap.add_argument("--batched-order", type=int, default=0, help="unit order: 0 largest first, 1 smallest first")
+    ap.add_argument("--batched-nmax", type=int, default=1_000_000, help="largest n of the uneven batch recipe")
+    ap.add_argument("--batched-ws-gb", type=float, default=0.0, help="cap on the batch workspace in GB (profiler runs)")
+    ap.add_argument("--batched-orders", default="0,1",
+                    help="unit orders to time on the uneven batch: 0 largest first, 1 smallest first")
+    ap.add_argument("--landmark-roots", type=int, default=32,
+                    help="roots of the landmark study on the BA 1e6 graph (0: skip)")
+    ap.add_argument("--kemeny-sweep", type=int, default=1, help="kappa/n of 1e6-node BA and ER graphs (0: skip)")
+    ap.add_argument("--study-samples", type=int, default=256, help="samples per root / graph of the two studies")
+    ap.add_argument("--spantree-trees", type=int, default=16384,
+                    help="SpanTree (Alg. 1/3) trees timed on the main workload (0: skip the SpanTree section)")
+    ap.add_argument("--extra-workloads", default="rmat_22",
+                    help="comma-separated extra single-graph workloads (plain throughput, CV vs plain)")
+    ap.add_argument("--extra-samples", type=int, default=16384, help="samples per step of the extra workloads")
     return ap.parse_args()
 
 
@@ -419,6 +431,208 @@ def cv_measurement(torch, LapGraph, g, v, params, samples_per_batch, batches):
                                                                                      samples_per_batch)}
 
 
+# ------------------------------------------------------------ SpanTree (Alg. 1, Alg. 3)
+
+def spantree_tta(torch, LapGraph, seeds=10, target=1e-2):
+    """Time-to-accuracy of the SpanTree estimators on Erdos-Renyi G(1000, 0.01)
+    against the dense truth (same protocol and omega grid as the plain form)."""
+    import hashlib
+    from paper_2311_10290_gb300 import inputs
+    g = inputs.er_1000()
+    ecc_t, kc_t, meta = read_truth()
+    h = hashlib.sha1()
+    h.update(g.row_ptr.astype("<i4").tobytes())
+    h.update(g.col.astype("<i4").tobytes())
+    if h.hexdigest() != meta.get("sha1"):
+        return {"error": "dense truth file does not match the generated graph"}
+    handles = [LapGraph(g.row_ptr, g.col, workspace_bytes=8 * g.n * 32768) for _ in range(seeds)]
+    for H in handles:
+        H.set_root()
+    done, curve, found = 0, [], None
+    for k in range(0, 49):
+        target_omega = int(round(256 * 2.0 ** (k / 4.0)))
+        e1, e2 = [], []
+        for sd, H in enumerate(handles):
+            H.spantree_sample(target_omega - done, 1000 + sd)
+        for H in handles:
+            _, ec, kc = H.spantree_estimates()
+            e1.append(float(np.max(np.abs(ec - ecc_t) / ecc_t)))
+            e2.append(abs(kc - kc_t) / kc_t)
+        done = target_omega
+        curve.append((target_omega, float(np.mean(e1)), float(np.mean(e2))))
+        if np.mean(e1) <= target and np.mean(e2) <= target:
+            found = target_omega
+            break
+    for H in handles:
+        H.close()
+    label = "er_1000 (Erdos-Renyi G(1000,0.01), dense FP64 truth)"
+    if found is None:
+        return {"workload": label, "reached": False,
+                "curve": [{"omega": o, "ecc_max_rel": round(x, 5), "kc_rel": round(y, 6)} for o, x, y in curve]}
+    H = LapGraph(g.row_ptr, g.col, workspace_bytes=8 * g.n * 32768)
+    H.set_root()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    H.spantree_sample(found, 7)
+    H.spantree_estimates()
+    b.record()
+    torch.cuda.synchronize()
+    H.close()
+    return {"workload": label, "seeds": seeds, "omega": found, "gpu_seconds": a.elapsed_time(b) / 1e3,
+            "ecc_max_rel_err_mean": curve[-1][1], "kc_rel_err_mean": curve[-1][2],
+            "curve": [{"omega": o, "ecc_max_rel": round(x, 5), "kc_rel": round(y, 6)} for o, x, y in curve]}
+
+
+def spantree_measurement(torch, LapGraph, g, v, args):
+    """SpanTree throughput on the main workload (trees/s and per-tree cost
+    against the LEWalk sampler's per-sample cost), then its time to accuracy
+    on the small workload."""
+    free, _ = torch.cuda.mem_get_info()
+    G = LapGraph(g.row_ptr, g.col, workspace_bytes=int(free * 0.5))
+    try:
+        G.set_root(v)
+        G.spantree_sample(256, args.seed)             # warm-up (allocations, BFS parents)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        G.spantree_sample(args.spantree_trees, args.seed)
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        _, _, kc = G.spantree_estimates()
+    finally:
+        G.close()
+    return {"workload": g.name, "trees": args.spantree_trees, "seconds": t, "trees_per_s": args.spantree_trees / t,
+            "kemeny_estimate": kc, "time_to_accuracy": spantree_tta(torch, LapGraph),
+            "note": "trees: 8-byte Wilson kernel, one tree per lane, then one CTA per tree for the flow sums "
+                    "(children, levels, subtree sizes, preorder intervals, BFS-path sums)"}
+
+
+# ------------------------------------------------------------ studies (batched runtime)
+
+def landmark_study(torch, g, args):
+    """Section 6 landmark study on one graph: Tr((I - P_v)^{-1}) (the expected
+    cost of a Wilson run, estimated by sum Y1 / omega) and Kemeny's constant
+    for the highest-degree roots and for random roots, all roots in one
+    batched launch sharing one copy of the CSR."""
+    from paper_2311_10290_gb300.lap import LapBatch
+    deg = np.diff(g.row_ptr.astype(np.int64))
+    top = [int(x) for x in np.argsort(-deg, kind="stable")[:8]]
+    rng = np.random.Generator(np.random.PCG64(7))
+    rand = [int(x) for x in rng.choice(g.n, size=max(0, args.landmark_roots - len(top)), replace=False)]
+    roots = top + rand
+    t0 = time.perf_counter()
+    B = LapBatch([(g.row_ptr, g.col)] * len(roots), roots=roots)
+    try:
+        B.autotune(args.study_samples, args.seed, window_ms=100.0)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        B.run(args.study_samples, args.seed)
+        B.sync()
+        b.record()
+        torch.cuda.synchronize()
+        tr = B.mean_wilson_steps() / g.n
+        kc = B.kemeny()
+    finally:
+        B.close()
+    rows = [{"root": v, "degree": int(deg[v]), "tr_over_n": round(float(t), 4), "kemeny": round(float(k), 1)}
+            for v, t, k in zip(roots, tr, kc)]
+    return {"graph": g.name, "roots": len(roots), "samples_per_root": args.study_samples,
+            "gpu_seconds": a.elapsed_time(b) / 1e3, "wall_seconds": round(time.perf_counter() - t0, 2),
+            "best_root": rows[int(np.argmin(tr))], "max_degree_root": rows[0],
+            "tr_over_n_random_roots": {"min": float(np.min(tr[len(top):])) if rand else None,
+                                       "median": float(np.median(tr[len(top):])) if rand else None,
+                                       "max": float(np.max(tr[len(top):])) if rand else None},
+            "rows": rows}
+
+
+def kemeny_sweep(torch, args):
+    """Kemeny's constant per node of 1e6-node Barabasi-Albert (m = 2, 3, 5, 8)
+    and Erdos-Renyi (average degree 4, 8, 16, 32) graphs, one batched launch
+    (the paper's synthetic-graph Kemeny experiment, Section 6)."""
+    from paper_2311_10290_gb300 import inputs
+    from paper_2311_10290_gb300.lap import LapBatch
+    spec = [("ba", 1_000_000, 2.0 * m, 900 + m) for m in (2, 3, 5, 8)] + \
+           [("er", 1_000_000, float(d), 950 + d) for d in (4, 8, 16, 32)]
+    t0 = time.perf_counter()
+    graphs = inputs.batch_graphs(spec)
+    t_gen = time.perf_counter() - t0
+    B = LapBatch([(x.row_ptr, x.col) for x in graphs])
+    try:
+        B.autotune(args.study_samples, args.seed, window_ms=100.0)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        B.run(args.study_samples, args.seed)
+        B.sync()
+        b.record()
+        torch.cuda.synchronize()
+        kc = B.kemeny()
+        tr = B.mean_wilson_steps()
+    finally:
+        B.close()
+    rows = [{"family": f, "avg_degree": d, "n": x.n, "arcs": x.arcs, "kemeny_over_n": round(float(k) / x.n, 4),
+             "tr_over_n": round(float(t) / x.n, 4)} for (f, _, d, _), x, k, t in zip(spec, graphs, kc, tr)]
+    return {"samples_per_graph": args.study_samples, "gpu_seconds": a.elapsed_time(b) / 1e3,
+            "generate_seconds": round(t_gen, 1), "rows": rows}
+
+
+# ------------------------------------------------------------ extra workloads
+
+def extra_workload(torch, LapGraph, name, args, params):
+    """Plain throughput (1 warm-up and 1 timed launch of `extra_samples`
+    samples) on another single-graph workload, then the control variate
+    against plain on it when a trained network is given."""
+    from paper_2311_10290_gb300.lap import LAP_STAT_FALLBACKS, LAP_STAT_KERNEL, lap_counts
+    t0 = time.perf_counter()
+    g = load_graph(name)
+    t_gen = time.perf_counter() - t0
+    free, _ = torch.cuda.mem_get_info()
+    G = LapGraph(g.row_ptr, g.col, workspace_bytes=int(free * args.ws_frac))
+    try:
+        v = G.set_root()
+        B = args.extra_samples
+        G.sample(B, args.seed)
+        G.kemeny()
+        _, c2a, sa = lap_counts(G.h, g.n)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        G.sample(B, args.seed)
+        ev[1].record()
+        G.ecc()
+        kc = G.kemeny()
+        ev[2].record()
+        torch.cuda.synchronize()
+        _, c2b, sb = lap_counts(G.h, g.n)
+        wilson = int(sb[1]) - int(sa[1])
+        uwalk = int(c2b.sum()) - int(c2a.sum())
+        piwalk = int(sb[2]) - int(sa[2])
+        t_kernel = ev[0].elapsed_time(ev[1]) / 1e3
+        t_step = ev[0].elapsed_time(ev[2]) / 1e3
+        alg = BYTES_WILSON_STEP * wilson + BYTES_TREE_INSERT * (g.n - 1) * B + BYTES_WALK_STEP * (uwalk + piwalk)
+        peak, _ = peaks()
+        res = {"workload": g.name, "n": g.n, "arcs": g.arcs, "root": v, "max_degree": int(np.diff(g.row_ptr).max()),
+               "samples_per_step": B, "ms_per_step": t_step * 1e3, "value": (wilson + uwalk + piwalk) / t_step,
+               "unit": "walk steps/s",
+               "walk_steps": {"wilson": wilson, "uniform_walk": uwalk, "pi_walk": piwalk,
+                              "wilson_steps_per_node_per_sample": wilson / B / g.n},
+               "roofline": {"bound": "hbm", "achieved": alg / t_kernel / 1e9, "peak": peak, "unit": "GB/s",
+                            "frac": alg / t_kernel / 1e9 / peak},
+               "kernel": G.stat(LAP_STAT_KERNEL), "fallbacks": G.stat(LAP_STAT_FALLBACKS),
+               "kemeny_estimate": kc, "slots": G.slots, "generate_seconds": round(t_gen, 1)}
+    finally:
+        G.close()
+    if params is not None:
+        note("control variate: CV vs plain on %s" % g.name)
+        res["cv_vs_plain"] = cv_measurement(torch, LapGraph, g, v, params, B, 4)
+    return res
+
+
 # ------------------------------------------------------------ uneven batch
 
 def batched_measurement(torch, args):
@@ -430,33 +644,43 @@ def batched_measurement(torch, args):
     from paper_2311_10290_gb300 import inputs
     from paper_2311_10290_gb300.lap import LAP_BOPT_ORDER, LAP_BSTAT_CLAIM, LAP_BSTAT_LANES, LAP_BSTAT_RERUNS, LapBatch
     t0 = time.perf_counter()
-    spec = inputs.batch_spec(count=args.batched_graphs)
+    spec = inputs.batch_spec(count=args.batched_graphs, n_hi=args.batched_nmax)
     graphs = inputs.batch_graphs(spec)
     t_gen = time.perf_counter() - t0
     k, seed = args.batched_samples, args.seed
     t0 = time.perf_counter()
-    B = LapBatch([(g.row_ptr, g.col) for g in graphs])
+    B = LapBatch([(g.row_ptr, g.col) for g in graphs],
+                 workspace_bytes=int(args.batched_ws_gb * 1e9) if args.batched_ws_gb > 0 else None)
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
+    orders = [int(x) for x in args.batched_orders.split(",") if x.strip()]
+    runs = []
     try:
-        B.set_option(LAP_BOPT_ORDER, args.batched_order)
         t0 = time.perf_counter()
+        B.set_option(LAP_BOPT_ORDER, orders[0])
         table = B.autotune(k, seed)
         t_tune = time.perf_counter() - t0
-        B.run(max(1, k // 16), seed + 1)
-        B.sync()
-        torch.cuda.synchronize()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        ev[0].record()
-        B.run(k, seed)
-        ev[1].record()
-        B.sync()
-        ev[2].record()
-        torch.cuda.synchronize()
-        t_launch = ev[0].elapsed_time(ev[1]) / 1e3
-        t_total = ev[0].elapsed_time(ev[2]) / 1e3
+        for order in orders:
+            B.set_option(LAP_BOPT_ORDER, order)
+            B.run(max(1, k // 16), seed + 1)            # warm-up (own CUDA graph)
+            B.sync()
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record()
+            B.run(k, seed)
+            ev[1].record()
+            B.sync()
+            ev[2].record()
+            torch.cuda.synchronize()
+            done = B.completion()
+            runs.append({"order": ["largest first", "smallest first", "given"][order],
+                         "seconds": ev[0].elapsed_time(ev[2]) / 1e3,
+                         "launch_seconds": ev[0].elapsed_time(ev[1]) / 1e3,
+                         "completion_seconds": {"p50": float(np.percentile(done, 50)),
+                                                "p99": float(np.percentile(done, 99)),
+                                                "max": float(done.max()), "min": float(done.min())},
+                         "reruns": B.stat(LAP_BSTAT_RERUNS)})
         kc = B.kemeny()
-        done = B.completion()
         wilson = uwalk = piwalk = inserts = 0
         for j, g in enumerate(graphs):
             _, c2, sums = B.counts(j)
@@ -467,20 +691,23 @@ def batched_measurement(torch, args):
         steps = wilson + uwalk + piwalk
         alg_bytes = BYTES_WILSON_STEP * wilson + BYTES_TREE_INSERT * inserts + BYTES_WALK_STEP * (uwalk + piwalk)
         peak, peak_kind = peaks()
+        for r in runs:
+            r["value"] = steps / r["seconds"]
+            r["roofline_frac"] = alg_bytes / r["launch_seconds"] / 1e9 / peak
+        best = max(runs, key=lambda r: r["value"])
+        t_total, t_launch = best["seconds"], best["launch_seconds"]
         achieved = alg_bytes / t_launch / 1e9
         res = {
-            "workload": "%d uneven graphs (ER/BA/R-MAT by seed mod 3, n log-uniform in [1e3, 1e6], average degree "
+            "workload": "%d uneven graphs (ER/BA/R-MAT by seed mod 3, n log-uniform in [1e3, %.0e], average degree "
                         "uniform in [4, 32], seeds 0..%d; root = each graph's max-degree node)"
-                        % (len(graphs), len(graphs) - 1),
+                        % (len(graphs), args.batched_nmax, len(graphs) - 1),
             "graphs": len(graphs), "total_nodes": int(sum(g.n for g in graphs)),
             "total_arcs": int(sum(g.arcs for g in graphs)), "largest_n": int(max(g.n for g in graphs)),
             "samples_per_graph": k, "seconds": t_total, "launch_seconds": t_launch,
             "walk_steps": {"wilson": wilson, "uniform_walk": uwalk, "pi_walk": piwalk},
             "value": steps / t_total, "unit": "walk steps/s",
-            "completion_seconds": {"p50": float(np.percentile(done, 50)), "p99": float(np.percentile(done, 99)),
-                                   "max": float(done.max()), "min": float(done.min())},
-            "order": ["largest first", "smallest first", "given"][args.batched_order],
-            "lanes": B.stat(LAP_BSTAT_LANES), "claim": B.stat(LAP_BSTAT_CLAIM), "reruns": B.stat(LAP_BSTAT_RERUNS),
+            "completion_seconds": best["completion_seconds"], "order": best["order"], "runs": runs,
+            "lanes": B.stat(LAP_BSTAT_LANES), "claim": B.stat(LAP_BSTAT_CLAIM), "reruns": best["reruns"],
             "autotune": [{"lanes": a, "claim": c, "walk_steps_per_s": round(r, 1)} for a, c, r in table],
             "autotune_seconds": round(t_tune, 2), "generate_seconds": round(t_gen, 2),
             "create_seconds": round(t_create, 2),
@@ -490,7 +717,8 @@ def batched_measurement(torch, args):
             "kemeny_first_graphs": [round(float(x), 3) for x in kc[:4]],
             "note": "seconds: CUDA graph launch (resets, persistent sampler, finalize of every graph) to results "
                     "ready, re-runs of withdrawn samples included; completion: from the sampler's start to each "
-                    "graph's last sample",
+                    "graph's last sample; top-level value/completion: the faster of `runs` (same samples, same "
+                    "counts: only the unit order differs)",
         }
     finally:
         B.close()
@@ -626,6 +854,7 @@ def run_ours(args, rank, world):
     if rank == 0 and not args.no_tta:
         note("time to accuracy (plain)")
         res["time_to_accuracy"] = time_to_accuracy(torch, LapGraph)
+    params = None
     if rank == 0 and args.cv_graphs > 0:
         note("control variate: training data and training")
         params, info = cv_train(torch, LapGraph, args.cv_graphs)
@@ -635,6 +864,22 @@ def run_ours(args, rank, world):
             note("time to accuracy (CV)")
             info["time_to_accuracy_cv"] = time_to_accuracy(torch, LapGraph, params=params)
         res["cv_vs_plain"] = info
+    if rank == 0 and args.spantree_trees > 0:
+        note("SpanTree estimators")
+        res["spantree"] = spantree_measurement(torch, LapGraph, g, v, args)
+        res["spantree"]["lewalk_samples_per_s"] = samples / max(t_total, 1e-9)
+    if rank == 0 and args.landmark_roots > 0:
+        note("landmark study: %d roots" % args.landmark_roots)
+        res["landmark_study"] = landmark_study(torch, g if args.workload == "ba_1m" else load_graph("ba_1m"), args)
+    if rank == 0 and args.kemeny_sweep > 0:
+        note("Kemeny sweep over 1e6-node BA and ER graphs")
+        res["kemeny_sweep"] = kemeny_sweep(torch, args)
+    for name in [x for x in args.extra_workloads.split(",") if x.strip()]:
+        if rank != 0:
+            break
+        note("extra workload %s" % name)
+        res.setdefault("extra_workloads", []).append(
+            extra_workload(torch, LapGraph, name, args, params if args.cv_graphs > 0 else None))
     if rank == 0 and args.batched_graphs > 0:
         note("uneven batch: %d graphs" % args.batched_graphs)
         res["batched"] = batched_measurement(torch, args)

@@ -193,6 +193,50 @@ lap_status lap_ldiag(lap_graph *g, double *out, int out_on_device);
 lap_status lap_kemeny(lap_graph *g, double *out1);
 
 /*
+ * Two more quantities of the same diagonal (Section 5, "Discussions"):
+ *   lap_kirchhoff       the Kirchhoff index as the paper defines it,
+ *                       Tr(L^+) = sum_u (L^+)_uu (the sum of resistances
+ *                       over node pairs is n times this); out1: one double;
+ *   lap_rw_betweenness  random-walk betweenness for every node,
+ *                       c_b(u) = 1/n + Tr(L^+) / ((n-1) (Tr(L^+) + n (L^+)_uu));
+ *                       out: n doubles, host or device (out_on_device).
+ * Computed from the same estimates as lap_ecc (same samples, same sums).
+ * Synchronise.  Errors as lap_ecc.
+ */
+lap_status lap_kirchhoff(lap_graph *g, double *out1);
+lap_status lap_rw_betweenness(lap_graph *g, double *out, int out_on_device);
+
+/*
+ * SpanTree estimators (Alg. 1 for ECC, Alg. 3 for Kemeny's constant;
+ * Section 4.1 and Section 5.1), on the same handle and root, with their own
+ * sample ids (0, 1, ... since lap_set_root) and sums:
+ *   lap_spantree_sample     draws n_samples uniform spanning trees rooted at v
+ *                           (Wilson's algorithm with the Philox keying of
+ *                           lap_sample, so tree i equals the tree of
+ *                           lap_sample's sample id i) and adds, for every node u,
+ *                           the integer flow sums along u's BFS path (the BFS
+ *                           parent of u is its smallest-id neighbour one hop
+ *                           closer to v):
+ *                             x1(u)   unit current u -> v on the tree,
+ *                             x2(u)   1/n injected at every node (times n),
+ *                             x2d(u)  d_w/2m injected at every w (times 2m).
+ *                           Synchronises.  Uses the handle's workspace (8 n bytes
+ *                           per tree in flight) and allocates per-CTA scratch.
+ *   lap_spantree_sums       the integer sums (int64[n] each, any may be NULL) and
+ *                           the number of trees; host or device (on_device).
+ *   lap_spantree_estimates  (L^+)_uu = x1/omega - 2 x2/(n omega) + (1/n) sum x2/(n omega),
+ *                           ECC as lap_ecc, and
+ *                           kappa = sum_u d_u x1(u)/omega - sum_u d_u x2d(u)/(2m omega);
+ *                           ldiag/ecc: n doubles (may be NULL), kemeny: one double.
+ * The estimators are unbiased with bounded per-sample range (Section 4.1,
+ * Hoeffding bound).  Errors: LAP_ERR_NO_ROOT, LAP_ERR_INVALID_ARG (seed change),
+ * LAP_ERR_NO_SAMPLES, LAP_ERR_STEP_LIMIT, LAP_ERR_OOM, sticky errors.
+ */
+lap_status lap_spantree_sample(lap_graph *g, uint64_t n_samples, uint64_t seed);
+lap_status lap_spantree_sums(lap_graph *g, int64_t *x1, int64_t *x2, int64_t *x2d, uint64_t *omega, int on_device);
+lap_status lap_spantree_estimates(lap_graph *g, double *ldiag, double *ecc, int on_device, double *kemeny);
+
+/*
  * Raw integer state (for parity checks and checkpointing):
  *   cnt1[n]  visits per node summed over samples (0 at v),
  *   cnt2[n]  passes of the uniform-start walks per node,

@@ -59,8 +59,11 @@ typedef enum {
  * landmark v, or < 0 for its highest-degree node (smallest id on ties);
  * roots may be NULL (all < 0).  The graphs are copied to the device (packed
  * arenas), validated and checked for connectivity from their roots; the
- * caller's buffers are not kept.  1 <= n_graphs <= 65535; the arcs of all
- * graphs together must be fewer than 2^40.
+ * caller's buffers are not kept.  Graphs passed with the same n and the same
+ * row_ptr and col_idx pointers share one device copy of the CSR (one graph
+ * sampled from several roots, e.g. a landmark study: Section 6).
+ * 1 <= n_graphs <= 65535; the arcs of all graphs together must be fewer than
+ * 2^40.
  * Errors: LAP_ERR_INVALID_ARG, LAP_ERR_BAD_CSR, LAP_ERR_NOT_SYMMETRIC,
  * LAP_ERR_SELF_LOOP, LAP_ERR_DISCONNECTED (naming the graph), LAP_ERR_OOM,
  * LAP_ERR_CUDA; explained by lap_batch_last_error(NULL).
@@ -78,7 +81,7 @@ lap_status lap_batch_set_option(lap_batch *b, int32_t option, int64_t value);
 
 /* Device bytes of the Wilson-state workspace for `lanes` samples in flight
  * (one slot per lane: a state byte per node of the largest graph, rounded up
- * to 256, plus the path stack). */
+ * to 256, plus the path stack and a 2 KB table of draw counts above 30). */
 lap_status lap_batch_workspace_query(const lap_batch *b, uint64_t lanes, uint64_t *bytes);
 
 /* Lends the handle device memory for the workspace (256-byte aligned; the
@@ -128,6 +131,8 @@ lap_status lap_batch_ecc(lap_batch *b, double *out, int on_device);
 lap_status lap_batch_ldiag(lap_batch *b, double *out, int on_device);
 lap_status lap_batch_kemeny(lap_batch *b, double *out);
 lap_status lap_batch_completion(lap_batch *b, double *seconds);
+/* Per graph: Tr(L^+) (the Kirchhoff index as Section 5 defines it), host double[n_graphs]. */
+lap_status lap_batch_kirchhoff(lap_batch *b, double *out);
 lap_status lap_batch_counts(lap_batch *b, int32_t graph, uint64_t *cnt1, uint64_t *cnt2, uint64_t *sums,
                             int on_device);
 

@@ -59,6 +59,28 @@ def ecc(n, row_ptr, col):
     return (n - 1) / (n * dg + dg.sum())
 
 
+def kirchhoff(n, row_ptr, col):
+    """Kirchhoff index as Section 5 ("Discussions") defines it: Tr(L^+)."""
+    return float(np.trace(pinv_laplacian(n, row_ptr, col)))
+
+
+def rw_betweenness(n, row_ptr, col):
+    """Random-walk betweenness as Section 5 ("Discussions") states it:
+    c_b(u) = 1/n + Tr(L^+) / ((n-1) (Tr(L^+) + n L^+_uu))."""
+    dg = np.diag(pinv_laplacian(n, row_ptr, col))
+    return from_ldiag(dg)[1]
+
+
+def from_ldiag(ldiag):
+    """(Kirchhoff index, random-walk betweenness) from a vector of L^+_uu
+    (Section 5, "Discussions"); the trace is a compensated FP64 sum."""
+    import math
+    ld = np.asarray(ldiag, dtype=np.float64)
+    n = ld.size
+    tr = math.fsum(ld.tolist())
+    return tr, 1.0 / n + tr / ((n - 1) * (tr + n * ld))
+
+
 def kemeny(n, row_ptr, col):
     """kappa(G) = Tr(calL^+) = sum over the nonzero eigenvalues sigma of
     calL = I - D^{-1/2} A D^{-1/2} of 1/sigma (Section 2, KC)."""

@@ -18,7 +18,10 @@ struct lap_batch {
     int num_sms = 0;
     int32_t G = 0;
     std::vector<int32_t> n, roots;
-    std::vector<int64_t> arcs, node_off, arc_off;
+    std::vector<int64_t> arcs, node_off, arc_off;   // per-graph offsets of counts and outputs
+    std::vector<int32_t> src;                        // graph whose CSR arena region graph g shares (itself if first)
+    std::vector<int64_t> csr_node_off, csr_arc_off;  // graph g's row records and columns in the CSR arenas
+    int64_t csr_nodes = 0, csr_arcs = 0;
     int64_t total_n = 0, total_arcs = 0;
     int32_t max_n = 0;
 
@@ -466,14 +469,35 @@ lap_status lap_batch_create(int32_t n_graphs, const int32_t *n, const int32_t *c
     }
     b->total_n = b->node_off[(size_t)n_graphs];
     b->total_arcs = b->arc_off[(size_t)n_graphs];
+    // Graphs passed with the same (n, row_ptr, col_idx) pointers share one copy
+    // of the CSR (e.g. one graph sampled from many roots).
+    b->src.resize((size_t)n_graphs);
+    b->csr_node_off.resize((size_t)n_graphs);
+    b->csr_arc_off.resize((size_t)n_graphs);
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        int32_t same = g;
+        for (int32_t h = 0; h < g && same == g; ++h)
+            if (b->src[(size_t)h] == h && n[h] == n[g] && row_ptr[h] == row_ptr[g] && col_idx[h] == col_idx[g]) same = h;
+        b->src[(size_t)g] = same;
+        if (same == g) {
+            b->csr_node_off[(size_t)g] = b->csr_nodes;
+            b->csr_arc_off[(size_t)g] = b->csr_arcs;
+            b->csr_nodes += n[g];
+            b->csr_arcs += b->arcs[(size_t)g];
+        } else {
+            b->csr_node_off[(size_t)g] = b->csr_node_off[(size_t)same];
+            b->csr_arc_off[(size_t)g] = b->csr_arc_off[(size_t)same];
+        }
+    }
     if (b->total_arcs >= (1ll << 40)) return bad(LAP_ERR_TOO_LARGE, "more than 2^40 arcs in the batch");
     cudaGetDevice(&b->device);
     cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
     if (b->num_sms <= 0) b->num_sms = 1;
     const size_t G = (size_t)n_graphs, tn = (size_t)b->total_n;
     int32_t *d_row_ptr = nullptr;
-    bool ok = balloc(&d_row_ptr, tn + G) == cudaSuccess && balloc(&b->d_col, (size_t)b->total_arcs) == cudaSuccess &&
-              balloc(&b->d_rowinfo, tn) == cudaSuccess && balloc(&b->d_rep1, tn) == cudaSuccess &&
+    bool ok = balloc(&d_row_ptr, (size_t)b->csr_nodes + G) == cudaSuccess &&
+              balloc(&b->d_col, (size_t)b->csr_arcs) == cudaSuccess &&
+              balloc(&b->d_rowinfo, (size_t)b->csr_nodes) == cudaSuccess && balloc(&b->d_rep1, tn) == cudaSuccess &&
               balloc(&b->d_cnt2, tn) == cudaSuccess && balloc(&b->d_ldiag, tn) == cudaSuccess &&
               balloc(&b->d_ecc, tn) == cudaSuccess && balloc(&b->d_scratch, (size_t)b->max_n) == cudaSuccess &&
               balloc(&b->d_red, G * 1026) == cudaSuccess && balloc(&b->d_graphs, G) == cudaSuccess &&
@@ -491,12 +515,14 @@ lap_status lap_batch_create(int32_t n_graphs, const int32_t *n, const int32_t *c
     cudaStream_t st = nullptr;
     cudaError_t e = cudaMemsetAsync(b->d_acc, 0, sizeof(LapDevAcc) * G, st);
     for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
-        int32_t *rp = d_row_ptr + b->node_off[g] + (int64_t)g;
+        if (b->src[g] != (int32_t)g) continue;
+        int32_t *rp = d_row_ptr + b->csr_node_off[g] + (int64_t)g;
         e = cudaMemcpyAsync(rp, row_ptr[g], sizeof(int32_t) * ((size_t)n[g] + 1), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b->d_col + b->arc_off[g], col_idx[g], sizeof(int32_t) * (size_t)b->arcs[g],
+            e = cudaMemcpyAsync(b->d_col + b->csr_arc_off[g], col_idx[g], sizeof(int32_t) * (size_t)b->arcs[g],
                                 cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = lap_launch_validate(rp, b->d_col + b->arc_off[g], n[g], b->arcs[g], &b->d_acc[g].status, st);
+        if (e == cudaSuccess)
+            e = lap_launch_validate(rp, b->d_col + b->csr_arc_off[g], n[g], b->arcs[g], &b->d_acc[g].status, st);
     }
     std::vector<LapDevAcc> acc(G);
     if (e == cudaSuccess) e = cudaMemcpyAsync(acc.data(), b->d_acc, sizeof(LapDevAcc) * G, cudaMemcpyDeviceToHost, st);
@@ -516,7 +542,8 @@ lap_status lap_batch_create(int32_t n_graphs, const int32_t *n, const int32_t *c
         }
     }
     for (size_t g = 0; g < G && e == cudaSuccess; ++g)
-        e = lap_launch_rowinfo(d_row_ptr + b->node_off[g] + (int64_t)g, n[g], b->d_rowinfo + b->node_off[g], st);
+        if (b->src[g] == (int32_t)g)
+            e = lap_launch_rowinfo(d_row_ptr + b->csr_node_off[g] + (int64_t)g, n[g], b->d_rowinfo + b->csr_node_off[g], st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d_row_ptr);
     d_row_ptr = nullptr;
@@ -524,7 +551,7 @@ lap_status lap_batch_create(int32_t n_graphs, const int32_t *n, const int32_t *c
     // Roots: the highest degree, smallest id on ties, where none was given.
     e = cudaMemsetAsync(b->d_tdone, 0, sizeof(unsigned long long) * G, st);
     for (size_t g = 0; g < G && e == cudaSuccess; ++g)
-        if (b->roots[g] < 0) e = lap_launch_argmax_degree(b->d_rowinfo + b->node_off[g], n[g], b->d_tdone + g, st);
+        if (b->roots[g] < 0) e = lap_launch_argmax_degree(b->d_rowinfo + b->csr_node_off[g], n[g], b->d_tdone + g, st);
     std::vector<unsigned long long> best(G);
     if (e == cudaSuccess) e = cudaMemcpyAsync(best.data(), b->d_tdone, sizeof(unsigned long long) * G, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -545,7 +572,7 @@ lap_status lap_batch_create(int32_t n_graphs, const int32_t *n, const int32_t *c
         for (size_t g = 0; g < G && e == cudaSuccess; ++g) {
             if (!active[g]) continue;
             any = true;
-            e = lap_launch_bfs_level(b->d_rowinfo + b->node_off[g], b->d_col + b->arc_off[g], hops + b->node_off[g], n[g],
+            e = lap_launch_bfs_level(b->d_rowinfo + b->csr_node_off[g], b->d_col + b->csr_arc_off[g], hops + b->node_off[g], n[g],
                                      level, b->d_done + g, st);
         }
         if (!any || e != cudaSuccess) break;
@@ -567,8 +594,8 @@ lap_status lap_batch_create(int32_t n_graphs, const int32_t *n, const int32_t *c
     for (size_t g = 0; g < G; ++g) {
         LapBatchGraph &d = b->h_graphs[g];
         memset(&d, 0, sizeof(d));
-        d.rowinfo = b->d_rowinfo + b->node_off[g];
-        d.col = b->d_col + b->arc_off[g];
+        d.rowinfo = b->d_rowinfo + b->csr_node_off[g];
+        d.col = b->d_col + b->csr_arc_off[g];
         d.rep1 = b->d_rep1 + b->node_off[g];
         d.cnt2 = b->d_cnt2 + b->node_off[g];
         d.ldiag = b->d_ldiag + b->node_off[g];
@@ -811,6 +838,18 @@ lap_status lap_batch_kemeny(lap_batch *b, double *out)
     // Alg. 4 per graph: kappa = (sum Y1 - sum Y2) / omega.
     for (int32_t g = 0; g < b->G; ++g)
         out[g] = ((double)acc[(size_t)g].sum_y1 - (double)acc[(size_t)g].sum_y2) / (double)b->omega;
+    return LAP_OK;
+}
+
+lap_status lap_batch_kirchhoff(lap_batch *b, double *out)
+{
+    lap_status s = finish(b);
+    if (s != LAP_OK) return s;
+    if (!out) return bfail(b, LAP_ERR_INVALID_ARG, "output pointer is NULL");
+    // The batched finalize leaves graph g's Tr(L^+) at red[g * 1026 + 1025].
+    B_CUDA(b, cudaMemcpy2DAsync(out, sizeof(double), b->d_red + 1025, sizeof(double) * 1026, sizeof(double),
+                                (size_t)b->G, cudaMemcpyDeviceToHost, b->stream));
+    B_CUDA(b, cudaStreamSynchronize(b->stream));
     return LAP_OK;
 }
 

@@ -82,6 +82,17 @@ __global__ void ecc_kernel(int32_t n, const double *__restrict__ ldiag, const do
         ecc[u] = __ddiv_rn(num, __dadd_rn(__dmul_rn((double)n, ldiag[u]), t));
 }
 
+// Random-walk betweenness (Section 5, "Discussions"):
+//   c_b(u) = 1/n + Tr(L^+) / ((n-1) (Tr(L^+) + n (L^+)_uu)).
+__global__ void rwb_kernel(int32_t n, const double *__restrict__ ldiag, const double *tr, double *out)
+{
+    const double t = *tr;
+    const double inv_n = __ddiv_rn(1.0, (double)n);
+    const double nm1 = (double)(n - 1);
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        out[u] = __dadd_rn(inv_n, __ddiv_rn(t, __dmul_rn(nm1, __dadd_rn(t, __dmul_rn((double)n, ldiag[u])))));
+}
+
 __global__ void counts_kernel(int32_t n, int32_t root, unsigned long long omega,
                               const unsigned long long *__restrict__ rep1, unsigned long long *cnt1)
 {
@@ -218,5 +229,12 @@ cudaError_t lap_launch_rep_from_counts(int32_t n, int32_t root, uint64_t omega, 
                                        unsigned long long *rep1, unsigned int *bad, cudaStream_t st)
 {
     rep_from_counts_kernel<<<grid_for(n), kBlock, 0, st>>>(n, root, (unsigned long long)omega, cnt1, rep1, bad);
+    return cudaGetLastError();
+}
+
+// red as filled by lap_launch_finalize (trace at red[1024 + 1]).
+cudaError_t lap_launch_rw_betweenness(int32_t n, const double *ldiag, const double *red, double *out, cudaStream_t st)
+{
+    rwb_kernel<<<grid_for(n), kBlock, 0, st>>>(n, ldiag, red + kParts + 1, out);
     return cudaGetLastError();
 }

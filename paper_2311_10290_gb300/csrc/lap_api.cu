@@ -50,6 +50,7 @@ void free_all(lap_graph *g)
     cudaFree(g->d_ldiag);
     cudaFree(g->d_ecc);
     cudaFree(g->d_red);
+    cudaFree(g->d_aux);
     cudaFree(g->d_slot_epoch);
     cudaFree(g->d_ovf_ids);
     cudaFree(g->d_cv_h1);
@@ -60,6 +61,16 @@ void free_all(lap_graph *g)
     cudaFree(g->d_cv_a2);
     cudaFree(g->d_cv_p2);
     cudaFree(g->d_feat_scratch);
+    cudaFree(g->d_bpar);
+    cudaFree(g->d_st_x1);
+    cudaFree(g->d_st_x2);
+    cudaFree(g->d_st_x2d);
+    cudaFree(g->d_st_rep1);
+    cudaFree(g->d_st_ldiag);
+    cudaFree(g->d_st_ecc);
+    cudaFree(g->d_st_red);
+    cudaFree(g->d_st_acc);
+    cudaFree(g->d_st_scratch);
     if (g->ws_owned) cudaFree(g->ws);
 }
 
@@ -429,6 +440,16 @@ lap_status lap_set_root(lap_graph *g, int32_t v, int32_t *root_out)
         LAP_CUDA(g, cudaMemsetAsync(g->d_cv_a2, 0, nb, g->stream));
         LAP_CUDA(g, cudaMemsetAsync(g->d_cv_p2, 0, nb, g->stream));
     }
+    if (g->d_st_x1) {
+        const size_t nb = sizeof(unsigned long long) * (size_t)g->n;
+        LAP_CUDA(g, cudaMemsetAsync(g->d_st_x1, 0, nb, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_st_x2, 0, nb, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_st_x2d, 0, nb, g->stream));
+    }
+    g->bpar_valid = false;
+    g->st_omega = 0;
+    g->st_cursor = 0;
+    g->st_seed_set = false;
     g->ws_zeroed = false;                 // a failed earlier run may have left partial state
     g->pending = false;
     g->compact_disabled = false;
@@ -587,6 +608,34 @@ lap_status lap_ldiag(lap_graph *g, double *out, int out_on_device)
     return copy_out(g, out, g->d_ldiag, sizeof(double) * (size_t)g->n, out_on_device);
 }
 
+lap_status lap_kirchhoff(lap_graph *g, double *out1)
+{
+    lap_status s = ensure_results(g);
+    if (s != LAP_OK) return s;
+    return copy_out(g, out1, g->d_red + 1024 + 1, sizeof(double), 0);
+}
+
+lap_status lap_rw_betweenness(lap_graph *g, double *out, int out_on_device)
+{
+    lap_status s = ensure_results(g);
+    if (s != LAP_OK) return s;
+    if (!out) return fail(g, LAP_ERR_INVALID_ARG, "output pointer is NULL");
+    double *dst = out;
+    if (!out_on_device) {
+        if (!g->d_aux && dalloc(&g->d_aux, (size_t)g->n) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(g, LAP_ERR_OOM, "device allocation failed");
+        }
+        dst = g->d_aux;
+    }
+    LAP_CUDA(g, lap_launch_rw_betweenness(g->n, g->d_ldiag, g->d_red, dst, g->stream));
+    if (out_on_device) {
+        LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+        return LAP_OK;
+    }
+    return copy_out(g, out, g->d_aux, sizeof(double) * (size_t)g->n, 0);
+}
+
 lap_status lap_kemeny(lap_graph *g, double *out1)
 {
     lap_status s = check_sticky(g);
@@ -678,6 +727,164 @@ lap_status lap_set_counts(lap_graph *g, const uint64_t *cnt1, const uint64_t *cn
         g->omega = 0;
         return fail(g, LAP_ERR_INVALID_ARG, "counts inconsistent with omega samples (cnt1[v] != 0 or cnt1[u] < omega)");
     }
+    return LAP_OK;
+}
+
+// ------------------------------------------------------------ SpanTree (Alg. 1, Alg. 3)
+
+static lap_status spantree_prepare(lap_graph *g)
+{
+    const size_t n = (size_t)g->n;
+    if (!g->d_st_x1) {
+        bool ok = dalloc(&g->d_st_x1, n) == cudaSuccess && dalloc(&g->d_st_x2, n) == cudaSuccess &&
+                  dalloc(&g->d_st_x2d, n) == cudaSuccess && dalloc(&g->d_st_rep1, n) == cudaSuccess &&
+                  dalloc(&g->d_st_ldiag, n) == cudaSuccess && dalloc(&g->d_st_ecc, n) == cudaSuccess &&
+                  dalloc(&g->d_st_red, 1024 + 8) == cudaSuccess && dalloc(&g->d_st_acc, 1) == cudaSuccess &&
+                  dalloc(&g->d_bpar, n) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return fail(g, LAP_ERR_OOM, "SpanTree allocation failed");
+        }
+        const size_t nb = sizeof(unsigned long long) * n;
+        LAP_CUDA(g, cudaMemsetAsync(g->d_st_x1, 0, nb, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_st_x2, 0, nb, g->stream));
+        LAP_CUDA(g, cudaMemsetAsync(g->d_st_x2d, 0, nb, g->stream));
+        g->bpar_valid = false;
+    }
+    if (!g->bpar_valid) {
+        LAP_CUDA(g, cudaMemsetAsync(g->d_st_acc, 0, sizeof(LapDevAcc), g->stream));
+        LAP_CUDA(g, lap_launch_bfs_parent(g->d_rowinfo, g->d_col, g->d_hops, g->n, g->root, g->d_bpar,
+                                          &g->d_st_acc->status, g->stream));
+        g->bpar_valid = true;
+    }
+    if (!g->d_st_scratch) {
+        // One scratch region per tree CTA: two CTAs per SM, fewer if memory is short.
+        const uint64_t per = lap_spantree_scratch_ints(g->n) * sizeof(int32_t);
+        for (int b = 2 * g->num_sms; b >= 1; b /= 2) {
+            if (cudaMalloc(&g->d_st_scratch, per * (uint64_t)b) == cudaSuccess) {
+                g->st_blocks = b;
+                break;
+            }
+            cudaGetLastError();
+            g->d_st_scratch = nullptr;
+        }
+        if (!g->d_st_scratch) return fail(g, LAP_ERR_OOM, "SpanTree scratch allocation failed");
+    }
+    return LAP_OK;
+}
+
+lap_status lap_spantree_sample(lap_graph *g, uint64_t n_samples, uint64_t seed)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (g->st_seed_set && seed != g->st_seed) return fail(g, LAP_ERR_INVALID_ARG, "seed differs from the SpanTree seed in use since lap_set_root");
+    if (g->st_cursor + n_samples > (1ull << 32)) return fail(g, LAP_ERR_TOO_LARGE, "sample ids are limited to 2^32");
+    if (n_samples == 0) return LAP_OK;
+    if ((s = resolve_pending(g)) != LAP_OK) return s;      // the workspace is about to be reused
+    if ((s = spantree_prepare(g)) != LAP_OK) return s;
+    if ((s = ensure_workspace(g, LAP_KERNEL_WIDE)) != LAP_OK) return s;
+    g->st_seed = seed;
+    g->st_seed_set = true;
+    const uint64_t per_tree = 8ull * (uint64_t)g->n;
+    uint64_t cap = g->ws_bytes / per_tree;
+    if (cap > g->slot_epoch_cap) cap = g->slot_epoch_cap;
+    if (cap > (1ull << 24)) cap = 1ull << 24;
+    if (cap == 0) return fail(g, LAP_ERR_OOM, "workspace smaller than one tree");
+    const uint64_t limit = g->step_limit ? g->step_limit : default_step_limit(g->n);
+    for (uint64_t done = 0; done < n_samples;) {
+        const uint64_t c = n_samples - done < cap ? n_samples - done : cap;
+        LapSampleLaunch p;
+        memset(&p, 0, sizeof(p));
+        p.g = LapDevGraph{g->d_rowinfo, g->d_col, g->n, g->arcs};
+        p.root = g->root;
+        p.seed = seed;
+        p.first = (uint32_t)(g->st_cursor + done);
+        p.count = (uint32_t)c;
+        p.slots = c;
+        p.ws = g->ws;
+        p.slot_epoch = g->d_slot_epoch;
+        p.rep1 = g->d_st_rep1;
+        p.cnt2 = g->d_st_rep1;
+        p.acc = g->d_st_acc;
+        p.step_limit = limit;
+        p.block = g->block_opt;
+        p.num_sms = g->num_sms;
+        p.flags = LAP_SAMPLE_ONE_PER_LANE | LAP_SAMPLE_WILSON_ONLY;
+        LAP_CUDA(g, lap_launch_sample(p, g->stream));
+        LapSpanTreeLaunch t;
+        memset(&t, 0, sizeof(t));
+        t.rowinfo = g->d_rowinfo;
+        t.bpar = g->d_bpar;
+        t.trees = reinterpret_cast<const unsigned long long *>(g->ws);
+        t.n = g->n;
+        t.root = g->root;
+        t.count = (uint32_t)c;
+        t.scratch = g->d_st_scratch;
+        t.scratch_ints = lap_spantree_scratch_ints(g->n);
+        t.x1 = g->d_st_x1;
+        t.x2 = g->d_st_x2;
+        t.x2d = g->d_st_x2d;
+        t.status = &g->d_st_acc->status;
+        LAP_CUDA(g, lap_launch_spantree(t, (int)(c < (uint64_t)g->st_blocks ? c : (uint64_t)g->st_blocks), g->stream));
+        done += c;
+    }
+    LapDevAcc h;
+    LAP_CUDA(g, cudaMemcpyAsync(&h, g->d_st_acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    if (h.status & LAP_DEV_STEP_LIMIT) {
+        g->sticky = LAP_ERR_STEP_LIMIT;
+        return fail(g, LAP_ERR_STEP_LIMIT, "a Wilson run exceeded the per-sample step budget (LAP_OPT_STEP_LIMIT)");
+    }
+    if (h.status) {
+        g->sticky = LAP_ERR_CUDA;
+        return fail(g, LAP_ERR_CUDA, "internal error in the SpanTree kernels (status " + std::to_string(h.status) + ")");
+    }
+    g->st_cursor += n_samples;
+    g->st_omega += n_samples;
+    return LAP_OK;
+}
+
+lap_status lap_spantree_sums(lap_graph *g, int64_t *x1, int64_t *x2, int64_t *x2d, uint64_t *omega, int on_device)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (omega) *omega = g->st_omega;
+    if (!g->d_st_x1) {
+        if (x1 || x2 || x2d) return fail(g, LAP_ERR_NO_SAMPLES, "no SpanTree samples drawn");
+        return LAP_OK;
+    }
+    const size_t nb = sizeof(int64_t) * (size_t)g->n;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (x1) LAP_CUDA(g, cudaMemcpyAsync(x1, g->d_st_x1, nb, kind, g->stream));
+    if (x2) LAP_CUDA(g, cudaMemcpyAsync(x2, g->d_st_x2, nb, kind, g->stream));
+    if (x2d) LAP_CUDA(g, cudaMemcpyAsync(x2d, g->d_st_x2d, nb, kind, g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    return LAP_OK;
+}
+
+lap_status lap_spantree_estimates(lap_graph *g, double *ldiag, double *ecc, int on_device, double *kemeny)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (g->st_omega == 0) return fail(g, LAP_ERR_NO_SAMPLES, "no SpanTree samples drawn");
+    LAP_CUDA(g, lap_launch_spantree_finalize(g->d_rowinfo, g->n, g->root, g->st_omega,
+                                             reinterpret_cast<const long long *>(g->d_st_x1),
+                                             reinterpret_cast<const long long *>(g->d_st_x2),
+                                             reinterpret_cast<const long long *>(g->d_st_x2d), g->d_st_ldiag,
+                                             g->d_st_ecc, g->d_st_red, g->stream));
+    const size_t nb = sizeof(double) * (size_t)g->n;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (ldiag) LAP_CUDA(g, cudaMemcpyAsync(ldiag, g->d_st_ldiag, nb, kind, g->stream));
+    if (ecc) LAP_CUDA(g, cudaMemcpyAsync(ecc, g->d_st_ecc, nb, kind, g->stream));
+    double sums[2] = {0.0, 0.0};
+    LAP_CUDA(g, cudaMemcpyAsync(sums, g->d_st_red + 1024 + 2, sizeof(sums), cudaMemcpyDeviceToHost, g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    // Alg. 3: kappa = (sum_u d_u X1[u]) / omega - (sum_u d_u X2d[u]) / (2m omega).
+    const double w = (double)g->st_omega;
+    if (kemeny) *kemeny = sums[0] / w - sums[1] / ((double)g->arcs * w);
     return LAP_OK;
 }
 

@@ -82,6 +82,12 @@ struct LapSampleLaunch {
     unsigned long long *cv_a2;
     unsigned long long *cv_p2;
     double *m2_out;              // optional [count]: per-sample M2 (with y1_out)
+    uint32_t flags;              // wide kernel: LAP_SAMPLE_* below
+};
+enum : uint32_t {
+    LAP_SAMPLE_ONE_PER_LANE = 1u,   // lane j runs exactly sample first + j (j < count), so its
+                                    // slot ends holding that sample's tree (Next of every node)
+    LAP_SAMPLE_WILSON_ONLY = 2u,    // skip the two absorbed walks (Y2 = 0, no cnt2 passes)
 };
 cudaError_t lap_launch_sample(const LapSampleLaunch &p, cudaStream_t st);
 // sampler_compact.cu
@@ -146,6 +152,28 @@ uint64_t lap_batch_resident_lanes(int block, int num_sms);
 cudaError_t lap_launch_finalize_batch(const LapBatchGraph *graphs, int32_t n_graphs, int32_t max_n, uint64_t omega,
                                       double *red, cudaStream_t st);
 
+// ------------------------------------------------------------ SpanTree (Alg. 1, Alg. 3)
+struct LapSpanTreeLaunch {
+    const int2 *rowinfo;
+    const int32_t *bpar;                 // [n] BFS parent (-1 at the root)
+    const unsigned long long *trees;     // count slots of n 8-byte Wilson states (low 32 bits: Next)
+    int32_t n;
+    int32_t root;
+    uint32_t count;                      // trees in this launch
+    int32_t *scratch;                    // blocks * scratch_ints
+    uint64_t scratch_ints;
+    unsigned long long *x1, *x2, *x2d;   // [n] integer sums over trees
+    unsigned int *status;
+};
+// spantree.cu
+cudaError_t lap_launch_bfs_parent(const int2 *rowinfo, const int32_t *col, const int32_t *hops, int32_t n, int32_t root,
+                                  int32_t *bpar, unsigned int *status, cudaStream_t st);
+uint64_t lap_spantree_scratch_ints(int32_t n);
+cudaError_t lap_launch_spantree(const LapSpanTreeLaunch &p, int blocks, cudaStream_t st);
+cudaError_t lap_launch_spantree_finalize(const int2 *rowinfo, int32_t n, int32_t root, uint64_t omega,
+                                         const long long *X1, const long long *X2, const long long *X2d,
+                                         double *ldiag, double *ecc, double *red, cudaStream_t st);
+
 // Threads per block for `lanes` persistent lanes: the smallest warp multiple
 // (up to 256) that keeps at most 16 blocks per SM, so that the blocks, and
 // the lanes with them, spread evenly over all SMs.
@@ -186,6 +214,7 @@ cudaError_t lap_launch_adamw(float *w, float *m, float *v, const float *g, int64
 cudaError_t lap_launch_finalize(const int2 *rowinfo, int32_t n, int32_t root, uint64_t omega,
                                 const unsigned long long *rep1, const unsigned long long *cnt2,
                                 double *ldiag, double *ecc, double *red, cudaStream_t st);
+cudaError_t lap_launch_rw_betweenness(int32_t n, const double *ldiag, const double *red, double *out, cudaStream_t st);
 cudaError_t lap_launch_counts(int32_t n, int32_t root, uint64_t omega, const unsigned long long *rep1,
                               unsigned long long *cnt1, cudaStream_t st);
 cudaError_t lap_launch_rep_from_counts(int32_t n, int32_t root, uint64_t omega, const unsigned long long *cnt1,
@@ -207,6 +236,7 @@ struct lap_graph {
     double *d_ldiag = nullptr;
     double *d_ecc = nullptr;
     double *d_red = nullptr;                // reduction scratch
+    double *d_aux = nullptr;                // [n] random-walk betweenness (allocated on first use)
     unsigned int *d_slot_epoch = nullptr;   // per-slot epoch parity of the Wilson state
     uint64_t slot_epoch_cap = 0;
 
@@ -237,6 +267,17 @@ struct lap_graph {
     unsigned long long *d_cv_a1 = nullptr, *d_cv_a2 = nullptr, *d_cv_p2 = nullptr;
     double *d_feat_scratch = nullptr;
     bool cv1 = false, cv2 = false;
+
+    // SpanTree estimators (allocated on first use).
+    int32_t *d_bpar = nullptr;
+    bool bpar_valid = false;
+    unsigned long long *d_st_x1 = nullptr, *d_st_x2 = nullptr, *d_st_x2d = nullptr, *d_st_rep1 = nullptr;
+    double *d_st_ldiag = nullptr, *d_st_ecc = nullptr, *d_st_red = nullptr;
+    LapDevAcc *d_st_acc = nullptr;
+    int32_t *d_st_scratch = nullptr;
+    int st_blocks = 0;
+    uint64_t st_omega = 0, st_cursor = 0, st_seed = 0;
+    bool st_seed_set = false;
 
     // Samples a compact launch withdrew; re-run with the wide kernel.
     unsigned int *d_ovf_ids = nullptr;

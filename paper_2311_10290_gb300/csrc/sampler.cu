@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
     double m2 = 0.0;          // control variate: the sample's pi-walk martingale
     unsigned long long acc1 = 0, acc2 = 0;
     unsigned int bad = 0;
+    bool one_done = false;
 
     while (phase != P_DONE) {
         if (phase == P_MOVE) {
@@ -167,6 +168,11 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
             }
             else { pb = ld_row(rowinfo, u); phase = P_PIDRAW; }
         } else if (phase == P_USTART) {
+            if (p.flags & LAP_SAMPLE_WILSON_ONLY) {
+                acc1 += y1;
+                phase = P_CLAIM;
+                continue;
+            }
             // Alg. 2: uniformly sample s in V; walk until v, counting passes.
             t = 0;
             const uint64_t r = lap::philox_r64(0u, 0u, i, 1u, key0, key1);
@@ -182,9 +188,15 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
             phase = P_PIMOVE;
         } else {  // P_CLAIM
             if (bad) { phase = P_DONE; break; }
-            const unsigned int q = atomicAdd(&p.acc->claim, 1u);
-            if (q >= p.count) { phase = P_DONE; break; }
-            i = p.ids ? p.ids[q] : p.first + q;
+            if (p.flags & LAP_SAMPLE_ONE_PER_LANE) {
+                if (one_done || slot >= p.count) { phase = P_DONE; break; }
+                one_done = true;
+                i = p.first + (uint32_t)slot;
+            } else {
+                const unsigned int q = atomicAdd(&p.acc->claim, 1u);
+                if (q >= p.count) { phase = P_DONE; break; }
+                i = p.ids ? p.ids[q] : p.first + q;
+            }
             epoch ^= kEpoch;
             st[v] = (unsigned long long)(epoch | kTree);
             s = 0;

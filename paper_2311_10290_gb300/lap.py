@@ -70,6 +70,12 @@ def library():
         "lap_counts": (i32, [vp, vp, vp, vp, ctypes.c_int]),
         "lap_hops": (i32, [vp, vp, ctypes.c_int]),
         "lap_set_counts": (i32, [vp, vp, vp, vp, ctypes.c_int]),
+        "lap_kirchhoff": (i32, [vp, vp]),
+        "lap_spantree_sample": (i32, [vp, u64, u64]),
+        "lap_spantree_sums": (i32, [vp, vp, vp, vp, ctypes.POINTER(u64), ctypes.c_int]),
+        "lap_spantree_estimates": (i32, [vp, vp, vp, ctypes.c_int, vp]),
+        "lap_rw_betweenness": (i32, [vp, vp, ctypes.c_int]),
+        "lap_batch_kirchhoff": (i32, [vp, vp]),
         "lap_get_stat": (i32, [vp, i32, ctypes.POINTER(i64)]),
         "lap_graph_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]),
         "lap_last_error": (ctypes.c_char_p, [vp]),
@@ -233,6 +239,37 @@ def lap_counts(h, n, per_node=True):
     return c1, c2, s
 
 
+def lap_spantree_sample(h, n_samples, seed):
+    _check(library().lap_spantree_sample(h, int(n_samples), int(seed)), h)
+
+
+def lap_spantree_sums(h, n):
+    """Host int64 (x1, x2, x2d) sums and the number of trees."""
+    x1, x2, x2d = (np.zeros(n, dtype=np.int64) for _ in range(3))
+    om = ctypes.c_uint64()
+    _check(library().lap_spantree_sums(h, _host_ptr(x1), _host_ptr(x2), _host_ptr(x2d), ctypes.byref(om), 0), h)
+    return x1, x2, x2d, om.value
+
+
+def lap_spantree_estimates(h, n):
+    """Host (ldiag, ecc) and Kemeny's constant of the SpanTree estimators."""
+    ld = np.zeros(n)
+    ec = np.zeros(n)
+    kc = np.zeros(1)
+    _check(library().lap_spantree_estimates(h, _host_ptr(ld), _host_ptr(ec), 0, _host_ptr(kc)), h)
+    return ld, ec, float(kc[0])
+
+
+def lap_kirchhoff(h):
+    out = np.zeros(1)
+    _check(library().lap_kirchhoff(h, _host_ptr(out)), h)
+    return float(out[0])
+
+
+def lap_rw_betweenness(h, n, out=None):
+    return _out(h, library().lap_rw_betweenness, n, np.float64, out)
+
+
 def lap_set_counts(h, cnt1, cnt2, sums):
     """Replaces the handle's counts: cnt1, cnt2 uint64/int64 [n] and sums
     {omega, sum Y1, sum Y2}, all host numpy arrays or all CUDA tensors."""
@@ -345,8 +382,18 @@ def _bcheck(status, handle=None):
 def lap_batch_create(graphs, roots=None):
     """graphs: sequence of (row_ptr, col) host int32 arrays; roots: int32 per
     graph (< 0: highest degree) or None.  Returns the handle."""
-    rps = [np.ascontiguousarray(r, dtype=np.int32) for r, _ in graphs]
-    cols = [np.ascontiguousarray(c, dtype=np.int32) for _, c in graphs]
+    # The same array objects map to the same host pointers, which the library
+    # turns into one shared device copy (one graph sampled from many roots).
+    conv = {}
+
+    def c32(a):
+        key = id(a)
+        if key not in conv:
+            conv[key] = (a, np.ascontiguousarray(a, dtype=np.int32))
+        return conv[key][1]
+
+    rps = [c32(r) for r, _ in graphs]
+    cols = [c32(c) for _, c in graphs]
     ns = np.array([r.size - 1 for r in rps], dtype=np.int32)
     rp_ptrs = (ctypes.c_void_p * len(rps))(*[r.ctypes.data for r in rps])
     col_ptrs = (ctypes.c_void_p * len(cols))(*[c.ctypes.data for c in cols])
@@ -423,18 +470,26 @@ def lap_batch_kemeny(h, n_graphs):
     return a
 
 
+def lap_batch_kirchhoff(h, n_graphs):
+    a = np.zeros(n_graphs)
+    _bcheck(library().lap_batch_kirchhoff(h, _host_ptr(a)), h)
+    return a
+
+
 def lap_batch_completion(h, n_graphs):
     a = np.zeros(n_graphs)
     _bcheck(library().lap_batch_completion(h, _host_ptr(a)), h)
     return a
 
 
-def lap_batch_counts(h, graph, n):
-    """Host (cnt1, cnt2, sums {omega, sum Y1, sum Y2, seed}) of one graph."""
-    c1 = np.zeros(n, dtype=np.uint64)
-    c2 = np.zeros(n, dtype=np.uint64)
+def lap_batch_counts(h, graph, n, per_node=True):
+    """Host (cnt1, cnt2, sums {omega, sum Y1, sum Y2, seed}) of one graph;
+    per_node=False reads only the sums."""
+    c1 = np.zeros(n, dtype=np.uint64) if per_node else None
+    c2 = np.zeros(n, dtype=np.uint64) if per_node else None
     sums = np.zeros(4, dtype=np.uint64)
-    _bcheck(library().lap_batch_counts(h, int(graph), _host_ptr(c1), _host_ptr(c2), _host_ptr(sums), 0), h)
+    _bcheck(library().lap_batch_counts(h, int(graph), None if c1 is None else _host_ptr(c1),
+                                       None if c2 is None else _host_ptr(c2), _host_ptr(sums), 0), h)
     return c1, c2, sums
 
 
@@ -556,6 +611,21 @@ class LapGraph:
     def hops(self, out=None):
         return lap_hops(self.h, self.n, out)
 
+    def kirchhoff(self):
+        return lap_kirchhoff(self.h)
+
+    def spantree_sample(self, n_samples, seed):
+        lap_spantree_sample(self.h, n_samples, seed)
+
+    def spantree_sums(self):
+        return lap_spantree_sums(self.h, self.n)
+
+    def spantree_estimates(self):
+        return lap_spantree_estimates(self.h, self.n)
+
+    def rw_betweenness(self, out=None):
+        return lap_rw_betweenness(self.h, self.n, out)
+
     def set_counts(self, cnt1, cnt2, sums):
         lap_set_counts(self.h, cnt1, cnt2, sums)
 
@@ -662,5 +732,17 @@ class LapBatch:
     def completion(self):
         return lap_batch_completion(self.h, self.n_graphs)
 
-    def counts(self, graph):
-        return lap_batch_counts(self.h, graph, int(self.n[graph]))
+    def kirchhoff(self):
+        return lap_batch_kirchhoff(self.h, self.n_graphs)
+
+    def counts(self, graph, per_node=True):
+        return lap_batch_counts(self.h, graph, int(self.n[graph]), per_node)
+
+    def mean_wilson_steps(self):
+        """Per graph: sum Y1 / omega, the estimate of Tr((I - P_v)^{-1}), the
+        expected cost of one Wilson run rooted at the graph's root (Section 3.4)."""
+        out = np.zeros(self.n_graphs)
+        for g in range(self.n_graphs):
+            _, _, s = self.counts(g, per_node=False)
+            out[g] = float(s[1]) / float(s[0])
+        return out

@@ -226,3 +226,58 @@ def test_uneven_batch_full_recipe_sampled_parity():
             assert int(np.delete(c1, v).min()) >= k
     finally:
         B.close()
+
+
+def test_many_roots_of_one_graph_share_the_csr():
+    """A landmark study (Section 6): one graph, many roots, passed as the same
+    arrays, so the batch keeps one copy of the CSR.  Every root's counts equal
+    the oracle's; sum Y1 / omega estimates Tr((I - P_v)^{-1}) (dense check
+    within 6 standard errors)."""
+    import oracle.dense as D
+    g = I.ba(1500, 3, seed=21)
+    deg = np.diff(g.row_ptr)
+    roots = [int(np.argmax(deg)), 0, 17, int(np.argmin(deg)), 700, 1499]
+    k, seed = 300, 13
+    B = LapBatch([(g.row_ptr, g.col)] * len(roots), roots=roots, workspace_bytes=1 << 26)
+    try:
+        B.run(k, seed)
+        tr = B.mean_wilson_steps()
+        for j, v in enumerate(roots):
+            c = oracle.sample(g.row_ptr, g.col, v, seed, 0, k)
+            c1, c2, sums = B.counts(j)
+            assert np.array_equal(c1, c.cnt1) and np.array_equal(c2, c.cnt2) and int(sums[1]) == c.sum_y1
+            lv = D.lv_inverse(g.n, g.row_ptr, g.col, v)
+            exact = float(np.sum(np.diag(lv) * deg))         # Tr((I - P_v)^{-1}) = sum_u d_u (L_v^{-1})_uu
+            se = np.std(c.y1.astype(np.float64)) / np.sqrt(k)
+            assert abs(tr[j] - exact) < 6 * se + 1e-9, (v, tr[j], exact, se)
+        assert np.argmin(tr) == 0                     # the hub is the cheapest root
+    finally:
+        B.close()
+
+
+def test_kirchhoff_and_rw_betweenness_match_oracle():
+    import oracle.dense as D
+    graphs = [I.er(300, 0.03, seed=2), I.ba(900, 4, seed=3)]
+    k, seed = 500, 9
+    B = LapBatch([(g.row_ptr, g.col) for g in graphs], workspace_bytes=1 << 26)
+    try:
+        B.run(k, seed)
+        kf_b = B.kirchhoff()
+    finally:
+        B.close()
+    for j, g in enumerate(graphs):
+        G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 24)
+        try:
+            v = G.set_root()
+            G.sample(k, seed)
+            kf = G.kirchhoff()
+            cb = G.rw_betweenness()
+            cb_dev = G.rw_betweenness(torch.empty(g.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+        finally:
+            G.close()
+        c = oracle.sample(g.row_ptr, g.col, v, seed, 0, k, keep_per_sample=False)
+        ld, _, _ = oracle.finalize(g.row_ptr, v, k, c.cnt1, c.cnt2, c.sum_y1, c.sum_y2)
+        tr, cbo = D.from_ldiag(ld)
+        assert kf == pytest.approx(tr, rel=1e-12) and kf == kf_b[j]
+        np.testing.assert_allclose(cb, cbo, rtol=1e-12)
+        assert np.array_equal(cb, cb_dev)

@@ -348,3 +348,33 @@ def test_thread_split_is_exact():
     b = oracle.sample_threads(g.row_ptr, g.col, v, 5, 0, 64, threads=4)
     assert np.array_equal(a.cnt1, b.cnt1) and np.array_equal(a.cnt2, b.cnt2)
     assert a.sum_y1 == b.sum_y1 and a.sum_y2 == b.sum_y2
+
+
+# ------------------------------------------------ Kirchhoff index, random-walk betweenness (Section 5)
+
+def test_kirchhoff_index_closed_forms():
+    """Tr(L^+) of K_n is (n-1)/n (L^+ = (I - J/n)/n); of the path P_n it is
+    (n^2 - 1)/6 (the sum of resistances over node pairs, (n^3 - n)/6, is
+    n Tr(L^+)); of the cycle C_n it is (n^2 - 1)/12."""
+    import oracle.dense as D
+    for n in (3, 5, 9):
+        g = I.complete(n)
+        assert D.kirchhoff(n, g.row_ptr, g.col) == pytest.approx((n - 1) / n, rel=1e-12)
+        g = I.path(n)
+        assert D.kirchhoff(n, g.row_ptr, g.col) == pytest.approx((n * n - 1) / 6.0, rel=1e-12)
+        g = I.cycle(n)
+        assert D.kirchhoff(n, g.row_ptr, g.col) == pytest.approx((n * n - 1) / 12.0, rel=1e-12)
+
+
+def test_rw_betweenness_closed_form_and_ldiag_route():
+    """On K_n every node has c_b = 1/n + 1/(2(n-1)); from_ldiag on the dense
+    diagonal reproduces the dense definition on an irregular graph."""
+    import oracle.dense as D
+    n = 7
+    g = I.complete(n)
+    np.testing.assert_allclose(D.rw_betweenness(n, g.row_ptr, g.col), 1.0 / n + 1.0 / (2 * (n - 1)), rtol=1e-12)
+    g = I.ba(60, 2, seed=3)
+    lp = np.diag(D.pinv_laplacian(g.n, g.row_ptr, g.col))
+    tr, cb = D.from_ldiag(lp)
+    assert tr == pytest.approx(float(lp.sum()), rel=1e-13)
+    assert np.all(cb > 1.0 / g.n) and np.argmax(cb) == np.argmin(lp)
