@@ -42,7 +42,7 @@ def _load():
             lib.oracle_sample.restype = ctypes.c_int
             lib.oracle_sample.argtypes = [ctypes.c_int32, p, p, ctypes.c_int32, ctypes.c_uint64,
                                           ctypes.c_uint64, ctypes.c_uint64, p, ctypes.c_int32,
-                                          p, p, p, p, p, ctypes.c_uint64]
+                                          p, p, p, p, p, ctypes.c_uint64, ctypes.c_int]
             lib.oracle_cyclepop.restype = ctypes.c_int
             lib.oracle_cyclepop.argtypes = [ctypes.c_int32, p, p, ctypes.c_int32, ctypes.c_uint64,
                                             ctypes.c_uint64, ctypes.c_uint64, p, p, p]
@@ -51,7 +51,8 @@ def _load():
                                             p, p, ctypes.c_uint64, ctypes.c_uint64, p, p, p]
             lib.oracle_sample_cv.restype = ctypes.c_int
             lib.oracle_sample_cv.argtypes = [ctypes.c_int32, p, p, ctypes.c_int32, ctypes.c_uint64,
-                                             ctypes.c_uint64, ctypes.c_uint64, p, p, p, p, p, p, p, p, p, p]
+                                             ctypes.c_uint64, ctypes.c_uint64, p, p, p, p, p, p, p, p, p, p,
+                                             ctypes.c_int]
             lib.oracle_hitting_walks.restype = ctypes.c_int
             lib.oracle_hitting_walks.argtypes = [ctypes.c_int32, p, p, ctypes.c_int32, ctypes.c_uint64,
                                                  ctypes.c_uint32, p, ctypes.c_uint64]
@@ -89,8 +90,10 @@ class Counts:
 
 
 def sample(row_ptr, col, v, seed, first, count, order=None, keep_per_sample=True,
-           keep_tree=False, max_steps=0):
-    """Run sample ids [first, first+count) on one thread; returns Counts."""
+           keep_tree=False, max_steps=0, paths=False):
+    """Run sample ids [first, first+count) on one thread; returns Counts.
+    paths=True: the two absorbed walks are the sample's loop-included paths
+    (see oracle_one_sample in lewalk_oracle.c)."""
     rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
     cl = np.ascontiguousarray(col, dtype=np.int32)
     n = rp.size - 1
@@ -102,7 +105,7 @@ def sample(row_ptr, col, v, seed, first, count, order=None, keep_per_sample=True
     rc = _load().oracle_sample(n, _ptr(rp), _ptr(cl), int(v), int(seed), int(first), int(count),
                                _ptr(od), 0 if od is None else od.size,
                                _ptr(out.cnt1), _ptr(out.cnt2), _ptr(y1), _ptr(y2), _ptr(tree),
-                               int(max_steps))
+                               int(max_steps), int(bool(paths)))
     if rc != 0:
         raise RuntimeError("oracle_sample failed with code %d" % rc)
     out.sum_y1 = int(y1.sum(dtype=np.uint64))
@@ -115,7 +118,7 @@ def sample(row_ptr, col, v, seed, first, count, order=None, keep_per_sample=True
     return out
 
 
-def sample_cv(row_ptr, col, v, seed, first, count, h1=None, h2=None):
+def sample_cv(row_ptr, col, v, seed, first, count, h1=None, h2=None, paths=False):
     """oracle.sample plus the control-variate sums: returns (Counts, a1, a2, p2,
     m2 per sample).  h1, h2: int64 potentials (or None)."""
     rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
@@ -132,7 +135,7 @@ def sample_cv(row_ptr, col, v, seed, first, count, h1=None, h2=None):
     H2 = None if h2 is None else np.ascontiguousarray(h2, dtype=np.int64)
     rc = _load().oracle_sample_cv(n, _ptr(rp), _ptr(cl), int(v), int(seed), int(first), int(count),
                                   _ptr(out.cnt1), _ptr(out.cnt2), _ptr(y1), _ptr(y2), _ptr(H1), _ptr(H2),
-                                  _ptr(a1), _ptr(a2), _ptr(p2), _ptr(m2))
+                                  _ptr(a1), _ptr(a2), _ptr(p2), _ptr(m2), int(bool(paths)))
     if rc != 0:
         raise RuntimeError("oracle_sample_cv failed with code %d" % rc)
     out.y1, out.y2 = y1, y2
@@ -154,14 +157,15 @@ def hitting_walks(row_ptr, col, v, seed, reps, max_steps=0):
     return sums
 
 
-def sample_threads(row_ptr, col, v, seed, first, count, threads):
+def sample_threads(row_ptr, col, v, seed, first, count, threads, paths=False):
     """Same counts as sample(), with the sample ids split into `threads`
     contiguous ranges run concurrently (ctypes releases the GIL)."""
     threads = max(1, min(int(threads), int(count))) if count else 1
     bounds = [first + (count * t) // threads for t in range(threads + 1)]
 
     def run(t):
-        return sample(row_ptr, col, v, seed, bounds[t], bounds[t + 1] - bounds[t], keep_per_sample=False)
+        return sample(row_ptr, col, v, seed, bounds[t], bounds[t + 1] - bounds[t], keep_per_sample=False,
+                      paths=paths)
 
     with ThreadPoolExecutor(max_workers=threads) as ex:
         parts = list(ex.map(run, range(threads)))

@@ -112,12 +112,18 @@ typedef struct {
     int64_t *a1, *a2, *p2;
 } oracle_cv;
 
+/* paths = 0: the two v-absorbed walks take their own draws (stream 1 for the
+ * uniform start, stream 2 for the pi start), as Alg. 2 and Alg. 4 print them.
+ * paths = 1: they are the loop-included paths of the sample's own stacks
+ * (Section 4.2, "loop-erased walk" interpretation and "Sample from the
+ * paths"; Section 5.2): same start draws, and the j-th departure of a path
+ * from u takes stack entry j of u, i.e. draw (u, j, i, 0) of the Wilson run. */
 static int oracle_one_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t v,
                              uint64_t seed, uint32_t i, const int32_t *order, int32_t n_order,
                              uint32_t *draws, int32_t *next, uint8_t *intree,
                              uint64_t *cnt1, uint64_t *cnt2,
                              uint64_t *y1_out, uint64_t *y2_out, int32_t *tree_out,
-                             uint64_t max_steps, const oracle_cv *cv, double *m2_out)
+                             uint64_t max_steps, const oracle_cv *cv, double *m2_out, int paths)
 {
     /* Alg. 2: InTree[u] = false, Next[u] = -1 for all u; InTree[v] = true. */
     for (int32_t u = 0; u < n; ++u) { intree[u] = 0; next[u] = -1; draws[u] = 0; }
@@ -150,15 +156,24 @@ static int oracle_one_sample(int32_t n, const int32_t *row_ptr, const int32_t *c
     if (tree_out)
         for (int32_t u = 0; u < n; ++u) tree_out[u] = (u == v) ? -1 : next[u];
 
-    /* v-absorbed walk from a uniformly drawn s (Alg. 2). */
+    /* v-absorbed walk from a uniformly drawn s (Alg. 2), or the sample's
+     * loop-included path from s.  draws[] now counts a path's departures. */
     {
         uint64_t t = 0;
         int32_t u = (int32_t)oracle_below(oracle_r64(seed, 0u, 0u, i, 1u), (uint64_t)n);
+        if (paths)
+            for (int32_t w = 0; w < n; ++w) draws[w] = 0;
         while (u != v) {
             cnt2[u] += 1;
             t += 1;
             if (max_steps && t > max_steps) return -1;
-            u = oracle_neighbor(row_ptr, col, u, oracle_r64(seed, (uint32_t)t, 0u, i, 1u));
+            if (paths) {
+                uint64_t x = oracle_r64(seed, (uint32_t)u, draws[u], i, 0u);
+                draws[u] += 1;
+                u = oracle_neighbor(row_ptr, col, u, x);
+            } else {
+                u = oracle_neighbor(row_ptr, col, u, oracle_r64(seed, (uint32_t)t, 0u, i, 1u));
+            }
         }
     }
     /* v-absorbed walk from s ~ pi (Alg. 4): the head of a uniformly drawn arc
@@ -168,10 +183,19 @@ static int oracle_one_sample(int32_t n, const int32_t *row_ptr, const int32_t *c
     {
         int64_t arcs = row_ptr[n];
         int32_t u = col[oracle_below(oracle_r64(seed, 0u, 0u, i, 2u), (uint64_t)arcs)];
+        if (paths)
+            for (int32_t w = 0; w < n; ++w) draws[w] = 0;
         while (u != v) {
             y2 += 1;
             if (max_steps && y2 > max_steps) return -1;
-            int32_t w = oracle_neighbor(row_ptr, col, u, oracle_r64(seed, (uint32_t)y2, 0u, i, 2u));
+            int32_t w;
+            if (paths) {
+                uint64_t x = oracle_r64(seed, (uint32_t)u, draws[u], i, 0u);
+                draws[u] += 1;
+                w = oracle_neighbor(row_ptr, col, u, x);
+            } else {
+                w = oracle_neighbor(row_ptr, col, u, oracle_r64(seed, (uint32_t)y2, 0u, i, 2u));
+            }
             if (cv && cv->h2) {
                 int64_t d = (int64_t)row_ptr[u + 1] - row_ptr[u];
                 cv->a2[u] += cv->h2[w];
@@ -197,7 +221,7 @@ int oracle_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t
                   uint64_t seed, uint64_t first, uint64_t count,
                   const int32_t *order, int32_t n_order,
                   uint64_t *cnt1, uint64_t *cnt2,
-                  uint64_t *y1, uint64_t *y2, int32_t *tree, uint64_t max_steps)
+                  uint64_t *y1, uint64_t *y2, int32_t *tree, uint64_t max_steps, int paths)
 {
     if (n <= 0 || v < 0 || v >= n || first + count > 0x100000000ull) return -2;
     uint32_t *draws = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
@@ -209,7 +233,7 @@ int oracle_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t
         uint64_t a = 0, b = 0;
         rc = oracle_one_sample(n, row_ptr, col, v, seed, (uint32_t)(first + q), order, n_order,
                                draws, next, intree, cnt1, cnt2, &a, &b,
-                               tree ? tree + (size_t)q * (size_t)n : NULL, max_steps, NULL, NULL);
+                               tree ? tree + (size_t)q * (size_t)n : NULL, max_steps, NULL, NULL, paths);
         if (rc) break;
         if (y1) y1[q] = a;
         if (y2) y2[q] = b;
@@ -226,7 +250,8 @@ int oracle_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t
 int oracle_sample_cv(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t v,
                      uint64_t seed, uint64_t first, uint64_t count,
                      uint64_t *cnt1, uint64_t *cnt2, uint64_t *y1, uint64_t *y2,
-                     const int64_t *h1, const int64_t *h2, int64_t *a1, int64_t *a2, int64_t *p2, double *m2)
+                     const int64_t *h1, const int64_t *h2, int64_t *a1, int64_t *a2, int64_t *p2, double *m2,
+                     int paths)
 {
     if (n <= 0 || v < 0 || v >= n || first + count > 0x100000000ull) return -2;
     int64_t *S1 = (int64_t *)calloc((size_t)n, sizeof(int64_t));
@@ -245,7 +270,7 @@ int oracle_sample_cv(int32_t n, const int32_t *row_ptr, const int32_t *col, int3
         uint64_t a = 0, b = 0;
         double mm = 0.0;
         rc = oracle_one_sample(n, row_ptr, col, v, seed, (uint32_t)(first + q), NULL, 0,
-                               draws, next, intree, cnt1, cnt2, &a, &b, NULL, 0, &cv, &mm);
+                               draws, next, intree, cnt1, cnt2, &a, &b, NULL, 0, &cv, &mm, paths);
         if (rc) break;
         if (y1) y1[q] = a;
         if (y2) y2[q] = b;

@@ -51,6 +51,8 @@ struct lap_batch {
 
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t rerun_streams[8] = {};
+    cudaEvent_t rerun_done[8] = {};
     cudaGraphExec_t exec = nullptr;
     bool key_valid = false;
     uint64_t key_samples = 0, key_seed = 0, key_lanes = 0;
@@ -77,6 +79,7 @@ struct lap_batch {
 namespace {
 
 thread_local std::string g_batch_error = "no error";
+constexpr int kRerunStreams = 8;
 
 lap_status bfail(lap_batch *b, lap_status s, const std::string &msg)
 {
@@ -107,6 +110,10 @@ void free_batch(lap_batch *b)
 {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (int k = 0; k < 8; ++k) {
+        if (b->rerun_streams[k]) cudaStreamDestroy(b->rerun_streams[k]);
+        if (b->rerun_done[k]) cudaEventDestroy(b->rerun_done[k]);
+    }
     cudaFree(b->d_col);
     cudaFree(b->d_rowinfo);
     cudaFree(b->d_rep1);
@@ -141,7 +148,7 @@ uint64_t n_pad_of(const lap_batch *b) { return ((uint64_t)b->max_n + 255ull) & ~
 
 uint64_t slot_bytes_of(const lap_batch *b)
 {
-    return (n_pad_of(b) + 4ull * stack_cap_of(b) + LAP_COMPACT_TABLE_BYTES + 255ull) & ~255ull;
+    return (n_pad_of(b) + 4ull * stack_cap_of(b) + (8ull << lap_table_log2(b->max_n)) + 255ull) & ~255ull;
 }
 
 // Work units in claim order (shared by lap_batch_run and lap_batch_schedule).
@@ -261,7 +268,8 @@ LapBatchLaunch make_launch(const lap_batch *b, uint64_t seed, uint64_t lanes, ui
     p.ws = b->ws;
     p.slot_bytes = slot_bytes_of(b);
     p.n_pad = n_pad_of(b);
-    p.stack_cap = (uint32_t)((p.slot_bytes - p.n_pad - LAP_COMPACT_TABLE_BYTES) / 4ull);
+    p.tbl_log2 = lap_table_log2(b->max_n);
+    p.stack_cap = (uint32_t)((p.slot_bytes - p.n_pad - (8ull << p.tbl_log2)) / 4ull);
     p.slot_meta = b->d_slot_meta;
     p.acc = b->d_acc;
     p.done = b->d_done;
@@ -331,39 +339,80 @@ lap_status rerun_withdrawn(lap_batch *b, uint32_t count)
     std::vector<unsigned int> ids(count);
     for (uint32_t k = 0; k < count; ++k) ids[k] = ovf[k].y;
     B_CUDA(b, cudaMemcpyAsync(b->d_rerun_ids, ids.data(), sizeof(unsigned int) * count, cudaMemcpyHostToDevice, b->stream));
-    for (uint32_t a = 0; a < count;) {
+    // Graphs with withdrawn samples are packed into the workspace side by
+    // side (one lane per sample where it fits) and re-run concurrently on a
+    // few streams; groups that do not fit together run one after another.
+    struct Job { uint32_t g, a, c; uint64_t slots, ws_off, meta_off; };
+    std::vector<Job> group;
+    uint64_t ws_used = 0, meta_used = 0;
+    cudaEvent_t ready = nullptr;
+    B_CUDA(b, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    auto flush = [&]() -> lap_status {
+        if (group.empty()) return LAP_OK;
+        B_CUDA(b, cudaEventRecord(ready, b->stream));
+        for (size_t j = 0; j < group.size(); ++j) {
+            const Job &jb = group[j];
+            cudaStream_t st = b->rerun_streams[j % kRerunStreams];
+            B_CUDA(b, cudaStreamWaitEvent(st, ready, 0));
+            const LapBatchGraph &d = b->h_graphs[jb.g];
+            char *ws = reinterpret_cast<char *>(b->ws) + jb.ws_off;
+            B_CUDA(b, cudaMemsetAsync(ws, 0, jb.slots * 8ull * (uint64_t)d.n, st));
+            B_CUDA(b, cudaMemsetAsync(b->d_slot_meta + jb.meta_off, 0, sizeof(unsigned int) * jb.slots, st));
+            B_CUDA(b, cudaMemsetAsync(&b->d_acc[jb.g].claim, 0, sizeof(unsigned int), st));
+            LapSampleLaunch p;
+            memset(&p, 0, sizeof(p));
+            p.g = LapDevGraph{d.rowinfo, d.col, d.n, d.arcs};
+            p.root = d.root;
+            p.seed = b->seed;
+            p.first = 0;
+            p.count = jb.c;
+            p.slots = jb.slots;
+            p.ws = ws;
+            p.slot_epoch = b->d_slot_meta + jb.meta_off;
+            p.rep1 = d.rep1;
+            p.cnt2 = d.cnt2;
+            p.acc = b->d_acc + jb.g;
+            p.step_limit = d.step_limit;
+            p.num_sms = b->num_sms;
+            p.ids = b->d_rerun_ids + jb.a;
+            B_CUDA(b, lap_launch_sample(p, st));
+        }
+        for (int k = 0; k < kRerunStreams && k < (int)group.size(); ++k) {
+            B_CUDA(b, cudaEventRecord(b->rerun_done[k], b->rerun_streams[k]));
+            B_CUDA(b, cudaStreamWaitEvent(b->stream, b->rerun_done[k], 0));
+        }
+        group.clear();
+        ws_used = meta_used = 0;
+        return LAP_OK;
+    };
+    if (!b->rerun_streams[0]) {
+        for (int k = 0; k < kRerunStreams; ++k) {
+            B_CUDA(b, cudaStreamCreateWithFlags(&b->rerun_streams[k], cudaStreamNonBlocking));
+            B_CUDA(b, cudaEventCreateWithFlags(&b->rerun_done[k], cudaEventDisableTiming));
+        }
+    }
+    lap_status fs = LAP_OK;
+    for (uint32_t a = 0; a < count && fs == LAP_OK;) {
         uint32_t c = a;
         const uint32_t g = ovf[a].x;
         while (c < count && ovf[c].x == g) ++c;
-        if (g >= (uint32_t)b->G) return bfail(b, LAP_ERR_CUDA, "internal error: overflow entry names no graph");
+        if (g >= (uint32_t)b->G) { fs = bfail(b, LAP_ERR_CUDA, "internal error: overflow entry names no graph"); break; }
         const uint64_t per = 8ull * (uint64_t)b->n[g];
-        uint64_t slots = b->ws_bytes / per;
+        uint64_t slots = c - a;
+        if (slots * per > b->ws_bytes) slots = b->ws_bytes / per;
         if (slots > b->meta_cap) slots = b->meta_cap;
-        if (slots > c - a) slots = c - a;
-        if (slots == 0) return bfail(b, LAP_ERR_OOM, "workspace too small to re-run a withdrawn sample");
-        B_CUDA(b, cudaMemsetAsync(b->ws, 0, slots * per, b->stream));
-        B_CUDA(b, cudaMemsetAsync(b->d_slot_meta, 0, sizeof(unsigned int) * slots, b->stream));
-        B_CUDA(b, cudaMemsetAsync(&b->d_acc[g].claim, 0, sizeof(unsigned int), b->stream));
-        LapSampleLaunch p;
-        memset(&p, 0, sizeof(p));
-        const LapBatchGraph &d = b->h_graphs[g];
-        p.g = LapDevGraph{d.rowinfo, d.col, d.n, d.arcs};
-        p.root = d.root;
-        p.seed = b->seed;
-        p.first = 0;
-        p.count = c - a;
-        p.slots = slots;
-        p.ws = b->ws;
-        p.slot_epoch = b->d_slot_meta;
-        p.rep1 = d.rep1;
-        p.cnt2 = d.cnt2;
-        p.acc = b->d_acc + g;
-        p.step_limit = d.step_limit;
-        p.num_sms = b->num_sms;
-        p.ids = b->d_rerun_ids + a;
-        B_CUDA(b, lap_launch_sample(p, b->stream));
+        if (slots == 0) { fs = bfail(b, LAP_ERR_OOM, "workspace too small to re-run a withdrawn sample"); break; }
+        const uint64_t bytes = (slots * per + 255ull) & ~255ull;
+        if (ws_used + bytes > b->ws_bytes || meta_used + slots > b->meta_cap) fs = flush();
+        if (fs != LAP_OK) break;
+        group.push_back(Job{g, a, c - a, slots, ws_used, meta_used});
+        ws_used += bytes;
+        meta_used += slots;
         a = c;
     }
+    if (fs == LAP_OK) fs = flush();
+    cudaEventDestroy(ready);
+    if (fs != LAP_OK) return fs;
     b->meta_dirty = true;                    // the slots now hold 8-byte states
     B_CUDA(b, cudaMemsetAsync(b->d_slot_meta, 0, sizeof(unsigned int) * b->meta_cap, b->stream));
     b->meta_dirty = false;

@@ -7,10 +7,12 @@
 //
 // Draw counts k <= 30 live in the byte.  From the 31st draw at a node on, the
 // byte holds kKSat and the count lives in a per-lane open-addressing table
-// after the path stack (kTblEntries entries {node + 1 : 32 | k : 32}); the
-// table is cleared before a sample that follows one that used it.  A sample
-// that needs more table entries than fit (kTblProbes probes), more than
-// kKMax draws at a node, or a longer path than the stack holds is withdrawn.
+// after the path stack: 2^tbl_log2 entries {node + 1 : 32 | tag : 8 | k : 24}.
+// Each sample of a lane has its own tag (1..255), so entries of earlier
+// samples read as empty and the table is cleared only when the tag wraps (and
+// at the lane's first sample).  A sample that needs more entries than a probe
+// run of kTblProbes finds, more than kKMax draws at a node, or a longer path
+// than the stack holds is withdrawn.
 #pragma once
 
 #include "lap_internal.h"
@@ -22,11 +24,8 @@ namespace lap_compact {
 
 constexpr uint32_t kBEpoch = 0x80u, kBTree = 0x40u, kBPath = 0x20u, kBK = 0x1Fu;
 constexpr uint32_t kKSat = 31u;                 // byte value: "count in the table"
-constexpr uint32_t kKMax = 1u << 24;             // draws at one node in one sample
-constexpr uint64_t kTblBytes = LAP_COMPACT_TABLE_BYTES;
-constexpr uint32_t kTblEntries = (uint32_t)(kTblBytes / 8u);    // a power of two
+constexpr uint32_t kKMax = (1u << 24) - 1u;       // draws at one node in one sample
 constexpr uint32_t kTblProbes = 32u;
-static_assert(kTblEntries == 256u, "tbl_home maps to 8 bits");
 constexpr int kEntryShift = 27;
 constexpr uint32_t kNodeMask = (1u << kEntryShift) - 1u;
 
@@ -174,38 +173,55 @@ static __device__ __forceinline__ unsigned long long *tbl_of(uint32_t *stk, uint
     return reinterpret_cast<unsigned long long *>(stk + cap);
 }
 
-static __device__ __forceinline__ uint32_t tbl_home(uint32_t node) { return (node * 2654435761u) >> 24; }
+static __device__ __forceinline__ uint32_t tbl_home(uint32_t node, uint32_t log2)
+{
+    return (node * 2654435761u) >> (32u - log2);
+}
 
 // True draw count of a node whose byte holds kKSat (0 if absent: an error).
-static __device__ __forceinline__ uint32_t tbl_get(const unsigned long long *tbl, uint32_t node)
+static __device__ __forceinline__ uint32_t tbl_get(const unsigned long long *tbl, uint32_t log2, uint32_t node,
+                                                   uint32_t tag)
 {
-    uint32_t s = tbl_home(node);
-    for (uint32_t q = 0; q < kTblProbes; ++q, s = (s + 1u) & (kTblEntries - 1u)) {
+    const uint32_t mask = (1u << log2) - 1u;
+    uint32_t s = tbl_home(node, log2);
+    for (uint32_t q = 0; q < kTblProbes; ++q, s = (s + 1u) & mask) {
         const unsigned long long e = tbl[s];
-        if ((uint32_t)(e >> 32) == node + 1u) return (uint32_t)e;
-        if (e == 0ull) break;
+        if (((uint32_t)e >> 24) != tag) break;                 // empty for this sample
+        if ((uint32_t)(e >> 32) == node + 1u) return (uint32_t)e & 0xFFFFFFu;
     }
     return 0u;
 }
 
 // Sets a node's count (inserting it); false when its probe run is full.
-static __device__ __forceinline__ bool tbl_put(unsigned long long *tbl, uint32_t node, uint32_t k)
+static __device__ __forceinline__ bool tbl_put(unsigned long long *tbl, uint32_t log2, uint32_t node, uint32_t k,
+                                               uint32_t tag)
 {
-    uint32_t s = tbl_home(node);
-    for (uint32_t q = 0; q < kTblProbes; ++q, s = (s + 1u) & (kTblEntries - 1u)) {
+    const uint32_t mask = (1u << log2) - 1u;
+    uint32_t s = tbl_home(node, log2);
+    for (uint32_t q = 0; q < kTblProbes; ++q, s = (s + 1u) & mask) {
         const unsigned long long e = tbl[s];
-        if (e == 0ull || (uint32_t)(e >> 32) == node + 1u) {
-            tbl[s] = ((unsigned long long)(node + 1u) << 32) | k;
+        if (((uint32_t)e >> 24) != tag || (uint32_t)(e >> 32) == node + 1u) {
+            tbl[s] = ((unsigned long long)(node + 1u) << 32) | ((unsigned long long)tag << 24) | k;
             return true;
         }
     }
     return false;
 }
 
-static __device__ __forceinline__ void tbl_clear(unsigned long long *tbl)
+static __device__ __forceinline__ void tbl_clear(unsigned long long *tbl, uint32_t log2)
 {
     uint4 *t = reinterpret_cast<uint4 *>(tbl);
-    for (uint32_t j = 0; j < (uint32_t)(kTblBytes / 16u); ++j) t[j] = make_uint4(0u, 0u, 0u, 0u);
+    for (uint32_t j = 0; j < (1u << log2) / 2u; ++j) t[j] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Next sample's tag; clears the table when the tags wrap around.
+static __device__ __forceinline__ uint32_t tbl_next_tag(unsigned long long *tbl, uint32_t log2, uint32_t tag)
+{
+    if (tag >= 255u) {
+        tbl_clear(tbl, log2);
+        return 1u;
+    }
+    return tag + 1u;
 }
 
 // Withdraws a partly run sample: subtracts the k - 1 repeat visits every
@@ -215,7 +231,8 @@ static __device__ __forceinline__ void tbl_clear(unsigned long long *tbl)
 // epoch) reads them as stale.
 static __device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsigned long long *rep1, const int2 *rowinfo,
                                 const int32_t *col, const long long *h1, unsigned long long *a1, uint32_t i,
-                                uint32_t key0, uint32_t key1, const unsigned long long *tbl)
+                                uint32_t key0, uint32_t key1, const unsigned long long *tbl, uint32_t log2,
+                                uint32_t tag)
 {
     for (int32_t base = 0; base < n; base += 16) {
         ulonglong2 q = *reinterpret_cast<ulonglong2 *>(st + base);
@@ -240,10 +257,10 @@ static __device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsi
     }
     // Draws kKSat .. k-1 of the nodes in the count table (exactly the nodes
     // whose byte held kKSat).
-    for (uint32_t j = 0; j < kTblEntries; ++j) {
+    for (uint32_t j = 0; j < (1u << log2); ++j) {
         const unsigned long long e = tbl[j];
-        if (e == 0ull) continue;
-        const uint32_t node = (uint32_t)(e >> 32) - 1u, k = (uint32_t)e;
+        if (((uint32_t)e >> 24) != tag) continue;
+        const uint32_t node = (uint32_t)(e >> 32) - 1u, k = (uint32_t)e & 0xFFFFFFu;
         if ((int32_t)node >= n || k <= kKSat) continue;
         atomicAdd(&rep1[node], (unsigned long long)(-(long long)(k - kKSat)));
         if (h1) {

@@ -99,7 +99,7 @@ uint32_t stack_cap_of(const lap_graph *g)
 uint64_t slot_bytes_of(const lap_graph *g, int kernel)
 {
     if (kernel == LAP_KERNEL_WIDE) return 8ull * (uint64_t)g->n;
-    return (n_pad_of(g) + 4ull * stack_cap_of(g) + LAP_COMPACT_TABLE_BYTES + 255ull) & ~255ull;
+    return (n_pad_of(g) + 4ull * stack_cap_of(g) + (8ull << lap_table_log2(g->n)) + 255ull) & ~255ull;
 }
 
 int choose_kernel(const lap_graph *g)
@@ -162,7 +162,8 @@ lap_status launch(lap_graph *g, LapSampleLaunch &p, int kernel)
     p.slots = slots_for(g, kernel, p.count);
     p.slot_bytes = slot_bytes_of(g, kernel);
     p.n_pad = n_pad_of(g);
-    p.stack_cap = kernel == LAP_KERNEL_COMPACT ? (uint32_t)((p.slot_bytes - p.n_pad - LAP_COMPACT_TABLE_BYTES) / 4ull) : 0u;
+    p.tbl_log2 = lap_table_log2(g->n);
+    p.stack_cap = kernel == LAP_KERNEL_COMPACT ? (uint32_t)((p.slot_bytes - p.n_pad - (8ull << p.tbl_log2)) / 4ull) : 0u;
     LAP_CUDA(g, cudaMemsetAsync(&g->d_acc->claim, 0, sizeof(unsigned int), g->stream));
     const cudaError_t e = kernel == LAP_KERNEL_WIDE ? lap_launch_sample(p, g->stream) : lap_launch_sample_compact(p, g->stream);
     if (e != cudaSuccess) {

@@ -69,6 +69,7 @@ struct LapSampleLaunch {
     uint64_t slot_bytes;         // compact kernel: bytes of one slot (state + stack)
     uint64_t n_pad;              // compact kernel: state bytes of one slot (n rounded up to 256)
     uint32_t stack_cap;          // compact kernel: stack entries of one slot
+    uint32_t tbl_log2;           // compact kernel: log2 of the count-table entries
     unsigned int *ovf_ids;       // compact kernel: withdrawn sample ids [count]
     const unsigned int *ids;     // wide kernel: explicit sample ids [count] (NULL: first + q)
     uint32_t trace_base;         // wide kernel with ids: y1_out/y2_out index = id - trace_base
@@ -132,6 +133,7 @@ struct LapBatchLaunch {
     uint64_t slot_bytes;
     uint64_t n_pad;               // state bytes of a slot (largest n rounded up to 256)
     uint32_t stack_cap;
+    uint32_t tbl_log2;            // log2 of the count-table entries of a slot
     unsigned int *slot_meta;      // per lane: bit 31 epoch, bits 0..30 extent of bytes carrying it
     LapDevAcc *acc;               // [graphs] sum Y1, sum Y2
     unsigned int *done;           // [graphs] samples finished
@@ -187,9 +189,15 @@ inline int lap_pick_block(uint64_t lanes, int num_sms)
 
 enum LapKernel : int { LAP_KERNEL_WIDE = 1, LAP_KERNEL_COMPACT = 2 };
 
-// Compact kernels: bytes per slot for the table of draw counts above 30
-// (after the path stack; see compact_state.cuh).
-constexpr uint64_t LAP_COMPACT_TABLE_BYTES = 2048;
+// Compact kernels: log2 of the entries of the per-lane table of draw counts
+// above 30 (after the path stack; see compact_state.cuh): the next power of
+// two >= n, from 2^8 to 2^13 entries (8 bytes each).
+inline uint32_t lap_table_log2(int64_t n)
+{
+    uint32_t l = 8;
+    while (l < 13 && (1ll << l) < n) ++l;
+    return l;
+}
 
 // Control variate (cv.cu, mlp.cu).
 constexpr int LAP_CV_FIXED_POINT_BITS = 16;   // h = round(2^16 phi)

@@ -89,62 +89,11 @@ __global__ void __launch_bounds__(256) lewalk_batch_kernel(LapBatchLaunch p)
     unsigned long long probe_steps = 0;
     uint32_t iter = 0;
     unsigned int bad = 0;
-    bool tbl_dirty = true;    // the count table may hold entries (cleared before the next sample)
-
-    // Lookahead of the next walk start (as in sampler_compact.cu).
-    int32_t la_s = 0;
-    uint32_t la_k = 0;
-    uint32_t la_stage = 0;    // 0 none, 1 row record in flight, 2 column entry in flight
-    uint64_t la_row = 0;
-    int32_t la_w = 0;
-
-    // One Wilson step from head h (draw count kh) to w; false when the sample
-    // was withdrawn or failed (phase set to P_CLAIM).
-    auto step_to = [&](uint32_t kh, int32_t w) -> bool {
-        const uint32_t kn = kh + 1u;
-        uint32_t kb = kn;
-        bool fits = kn <= kKMax && sp < cap;
-        if (fits && kn >= kKSat) {
-            kb = kKSat;
-            fits = tbl_put(tbl_of(stk, cap), (uint32_t)h, kn);
-            tbl_dirty = true;
-        }
-        if (!fits) {
-            withdraw_sample(st, n, ep, rep1, rowinfo, col, nullptr, nullptr, i, key0, key1, tbl_of(stk, cap));
-            const unsigned int ix = atomicAdd(&p.ctl->ovf_count, 1u);
-            if (ix < p.ovf_cap) p.ovf[ix] = make_uint2((uint32_t)gi, i);
-            else bad |= LAP_DEV_K_OVERFLOW;
-            if (atomicAdd(&p.done[gi], 1u) + 1u == count_g) p.t_done[gi] = global_ns();
-            phase = P_CLAIM;
-            return false;
-        }
-        const uint32_t e = (uint32_t)h | (kb << kEntryShift);
-        if (sp == 0) e0 = e;
-        st_stack(stk + sp, e, keep);
-        ++sp;
-        st_state(st + h, ep | kBPath | kb);
-        pq_set(pq, chunk, (uint32_t)h, ep | kBPath | kb);
-        if (kh) atomicAdd(&rep1[h], 1ull);
-        if (PROBE) ++probe_steps;
-        if (++y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; return false; }
-        h = w;
-        pa = ld_state(st + w);
-        pb = ld_row(rowinfo, w, keep);
-        phase = P_WALK;
-        return true;
-    };
+    const uint32_t tlog = p.tbl_log2;
+    uint32_t tag = 255u;      // count-table tag of the current sample (the first claim clears the table)
 
     for (;;) {
-        bool do_step = false;     // a Wilson step from h to step_w (draw count step_k) is due
-        uint32_t step_k = 0;
-        int32_t step_w = 0;
         if (PROBE && ((++iter & 255u) == 0u) && global_ns() > t_stop) break;
-        if (la_stage == 1) {
-            la_w = ld_col(col + row_off(la_row) +
-                              (int64_t)lap::below(lap::philox_r64((uint32_t)la_s, la_k, i, 0u, key0, key1), row_deg(la_row)),
-                          keep);
-            la_stage = 2;
-        }
         if (phase == P_WALK) {
             const int32_t off = row_off(pb);
             const uint32_t deg = row_deg(pb);
@@ -154,24 +103,49 @@ __global__ void __launch_bounds__(256) lewalk_batch_kernel(LapBatchLaunch p)
                 if (b_path(b, ep)) sp = erase_loop(st, stk, sp, ep, (uint32_t)h, pq, chunk);
                 uint32_t kh = b_k(b, ep);
                 if (kh == kKSat) {
-                    kh = tbl_get(tbl_of(stk, cap), (uint32_t)h);
+                    kh = tbl_get(tbl_of(stk, cap), tlog, (uint32_t)h, tag);
                     if (kh < kKSat) { bad |= LAP_DEV_BAD_INDEX; phase = P_CLAIM; continue; }
                 }
                 if (kh) w = ld_col(col + off + (int64_t)lap::below(lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1), deg), keep);
-                do_step = true;
-                step_k = kh;
-                step_w = w;
-            } else {
-                if (sp == 1) {
-                    st_state(st + (e0 & kNodeMask), ep | kBTree | (e0 >> kEntryShift));
-                    pq_set(pq, chunk, e0 & kNodeMask, ep | kBTree | (e0 >> kEntryShift));
-                } else if (sp > 1) {
-                    commit_path(st, stk, sp, ep, pq, chunk);
+                const uint32_t kn = kh + 1u;
+                uint32_t kb = kn;
+                bool fits = kn <= kKMax && sp < cap;
+                if (fits && kn >= kKSat) {
+                    kb = kKSat;
+                    fits = tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, kn, tag);
                 }
-                sp = 0;
-                ++s;
-                phase = P_SCAN;
+                if (!fits) {
+                    withdraw_sample(st, n, ep, rep1, rowinfo, col, nullptr, nullptr, i, key0, key1, tbl_of(stk, cap), tlog, tag);
+                    const unsigned int ix = atomicAdd(&p.ctl->ovf_count, 1u);
+                    if (ix < p.ovf_cap) p.ovf[ix] = make_uint2((uint32_t)gi, i);
+                    else bad |= LAP_DEV_K_OVERFLOW;
+                    if (atomicAdd(&p.done[gi], 1u) + 1u == count_g) p.t_done[gi] = global_ns();
+                    phase = P_CLAIM;
+                    continue;
+                }
+                const uint32_t e = (uint32_t)h | (kb << kEntryShift);
+                if (sp == 0) e0 = e;
+                st_stack(stk + sp, e, keep);
+                ++sp;
+                st_state(st + h, ep | kBPath | kb);
+                pq_set(pq, chunk, (uint32_t)h, ep | kBPath | kb);
+                if (kh) atomicAdd(&rep1[h], 1ull);
+                if (PROBE) ++probe_steps;
+                if (++y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
+                h = w;
+                pa = ld_state(st + w);
+                pb = ld_row(rowinfo, w, keep);
+                continue;
             }
+            if (sp == 1) {
+                st_state(st + (e0 & kNodeMask), ep | kBTree | (e0 >> kEntryShift));
+                pq_set(pq, chunk, e0 & kNodeMask, ep | kBTree | (e0 >> kEntryShift));
+            } else if (sp > 1) {
+                commit_path(st, stk, sp, ep, pq, chunk);
+            }
+            sp = 0;
+            ++s;
+            phase = P_SCAN;
         }
         if (phase == P_SCAN) {
             if (s < n) {
@@ -179,7 +153,6 @@ __global__ void __launch_bounds__(256) lewalk_batch_kernel(LapBatchLaunch p)
                 if (base != chunk) {
                     pq = *reinterpret_cast<const ulonglong2 *>(st + base);
                     chunk = base;
-                    la_stage = 0;
                     continue;
                 }
                 uint32_t m = not_tree_mask(pq, ep) & (0xFFFFu << (s - base));
@@ -187,54 +160,19 @@ __global__ void __launch_bounds__(256) lewalk_batch_kernel(LapBatchLaunch p)
                 if (m) {
                     s = base + __ffs(m) - 1;
                     h = s;
-                    const uint32_t bs = (uint32_t)((((s - base) < 8 ? pq.x : pq.y) >> (8 * ((s - base) & 7))) & 0xFFu);
-                    const bool same = la_stage != 0 && la_s == s && b_k(bs, ep) == la_k;
-                    const uint32_t stage = same ? la_stage : 0u;
-                    const int32_t w_ready = la_w;
-                    const uint64_t row_ready = la_row;
-                    const uint32_t rest = m & ~((2u << (s - base)) - 1u);
-                    la_stage = 0;
-                    if (rest) {
-                        const int32_t c = base + __ffs(rest) - 1;
-                        const uint32_t kc = b_k((uint32_t)((((c - base) < 8 ? pq.x : pq.y) >> (8 * ((c - base) & 7))) & 0xFFu), ep);
-                        if (kc < kKSat) {
-                            la_s = c;
-                            la_k = kc;
-                            la_row = ld_row(rowinfo, c, keep);
-                            la_stage = 1;
-                        }
-                    }
-                    if (stage == 2) {
-                        // First step of the walk from s with the prefetched
-                        // target, in the common step below.
-                        do_step = true;
-                        step_k = b_k(bs, ep);
-                        step_w = w_ready;
-                    } else {
-                        pa = bs;
-                        pb = stage == 1 ? row_ready : ld_row(rowinfo, h, keep);
-                        phase = P_WALK;
-                        continue;
-                    }
+                    pa = (uint32_t)((((s - base) < 8 ? pq.x : pq.y) >> (8 * ((s - base) & 7))) & 0xFFu);
+                    pb = ld_row(rowinfo, h, keep);
+                    phase = P_WALK;
+                    continue;
                 }
-                if (!do_step) {
-                    s = base + 16;
-                    if (s < n) {
-                        pq = *reinterpret_cast<const ulonglong2 *>(st + s);
-                        chunk = s;
-                        la_stage = 0;
-                        continue;
-                    }
+                s = base + 16;
+                if (s < n) {
+                    pq = *reinterpret_cast<const ulonglong2 *>(st + s);
+                    chunk = s;
+                    continue;
                 }
             }
-            if (!do_step) {
-                la_stage = 0;
-                phase = P_USTART_IMMEDIATE;
-            }
-        }
-        if (do_step) {
-            step_to(step_k, step_w);
-            continue;
+            phase = P_USTART_IMMEDIATE;
         }
         if (phase == P_USTART_IMMEDIATE) {
             t = 0;
@@ -296,14 +234,10 @@ __global__ void __launch_bounds__(256) lewalk_batch_kernel(LapBatchLaunch p)
                 i = u.y;
                 unit_end = u.y + p.claim < count_g ? u.y + p.claim : count_g;
             }
-            la_stage = 0;
             // Bytes [0, n) must carry the current epoch before it flips.
             if (n > extent) stamp(st, extent, n, ep);
             extent = n;
-            if (tbl_dirty) {
-                tbl_clear(tbl_of(stk, cap));
-                tbl_dirty = false;
-            }
+            tag = tbl_next_tag(tbl_of(stk, cap), tlog, tag);
             ep ^= kBEpoch;
             st[v] = (uint8_t)(ep | kBTree);
             s = 0;

@@ -107,7 +107,7 @@ def test_compact_kernel_is_the_default_and_does_not_fall_back_on_social_graphs()
 @pytest.mark.parametrize("name,maker,root,stack,falls_back", [
     ("path_end_counts_table", lambda: I.path(60), 0, None, False),   # far nodes drawn > 30 times: count table
     ("star_leaf_root_hub_table", lambda: I.star(200), 1, None, False),  # the hub is drawn ~199 times per sample
-    ("path_far_root_table_full", lambda: I.path(400), 399, None, True),  # ~380 nodes drawn > 30 times
+    ("path_far_root_table_heavy", lambda: I.path(256), 255, None, False),  # ~230 of 256 nodes drawn > 30 times
     ("cycle_long_paths", lambda: I.cycle(301), 0, 16, True),         # loop-erased paths longer than the stack
 ])
 def test_compact_overflow_rolls_back_to_wide_kernel(name, maker, root, stack, falls_back):

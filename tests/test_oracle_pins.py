@@ -283,10 +283,10 @@ def test_finalize_on_exact_k4e_expectations():
 
 # ------------------------------------------------ means match the estimand
 
-def _batch_means(g, v, batches, per):
+def _batch_means(g, v, batches, per, paths=False):
     c1, c2, y1, y2 = [], [], [], []
     for b in range(batches):
-        c = oracle.sample(g.row_ptr, g.col, v, 4242, b * per, per)
+        c = oracle.sample(g.row_ptr, g.col, v, 4242, b * per, per, paths=paths)
         c1.append(c.cnt1 / per)
         c2.append(c.cnt2 / per)
         y1.append(c.sum_y1 / per)
@@ -317,6 +317,68 @@ def test_sample_means_match_dense_expectations(g, root):
     _check(c2, e["passes"])
     _check(y1[:, None], np.array([e["y1"]]))
     _check(y2[:, None], np.array([e["y2"]]))
+
+
+@pytest.mark.parametrize("g,root", [(_k4e(), 0), (I.er(30, 0.2, seed=1), None), (I.ba(40, 2, seed=3), None),
+                                    (I.path(6), 0), (I.cycle(7), 3)],
+                         ids=["k4e", "er", "ba", "path", "cycle"])
+def test_loop_included_paths_have_the_walk_expectations(g, root):
+    """Section 4.2 ("loop-erased walk" lemma, "sample the paths") and
+    Section 5.2: the loop-included path of the sample's stacks from a uniform
+    (or pi-distributed) start has the law of a v-absorbed walk from it, so
+    the counts keep the expectations of the online walks."""
+    v = oracle.root_max_degree(g.row_ptr) if root is None else root
+    e = D.expectations(g.n, g.row_ptr, g.col, v)
+    c1, c2, y1, y2 = _batch_means(g, v, 24, 1500, paths=True)
+    _check(c1, e["visits"])
+    _check(c2, e["passes"])
+    _check(y1[:, None], np.array([e["y1"]]))
+    _check(y2[:, None], np.array([e["y2"]]))
+
+
+def _uniform_start(n, seed, i):
+    """Start node of sample i's uniform walk: counter (0, 0, i, 1), high 64
+    bits of R64 * n (the same reading as the sampler's)."""
+    blk = oracle.philox_block([0, 0, i, 1], [seed & 0xFFFFFFFF, seed >> 32])
+    r = int(blk[0]) | (int(blk[1]) << 32)
+    return (r * n) >> 64
+
+
+def test_loop_included_path_is_the_first_walk_from_its_start():
+    """By the stack representation (Fig. 1), the loop-included path from s
+    is exactly the walk Wilson's algorithm takes from s when s is the first
+    start: the same draws (u, j) in the same order.  So its length equals Y1
+    of a run whose only start is s, and no node is left more often than the
+    full run draws from it."""
+    g = I.ba(60, 2, seed=4)
+    v = oracle.root_max_degree(g.row_ptr)
+    seed = 77
+    checked = 0
+    for i in range(40):
+        s = _uniform_start(g.n, seed, i)
+        if s == v:
+            continue
+        full = oracle.sample(g.row_ptr, g.col, v, seed, i, 1, paths=True)
+        first = oracle.sample(g.row_ptr, g.col, v, seed, i, 1, order=np.array([s], dtype=np.int32), paths=True)
+        assert int(full.cnt2.sum()) == int(first.y1[0])             # path length = first walk's steps
+        assert np.array_equal(first.cnt1, full.cnt2)                 # passes per node = that walk's visits
+        assert np.all(full.cnt2 <= full.cnt1)                        # a prefix of every node's stack
+        assert full.y2[0] <= full.y1[0]
+        checked += 1
+    assert checked > 30
+
+
+def test_loop_included_paths_reduce_the_kemeny_variance():
+    """Sharing the stacks with the Wilson run correlates Y2 with Y1: on
+    G(200, 0.05) the per-sample variance of Y1 - Y2 drops by more than half."""
+    g = I.er(200, 0.05, seed=0)
+    v = oracle.root_max_degree(g.row_ptr)
+    a = oracle.sample(g.row_ptr, g.col, v, 3, 0, 6000)
+    b = oracle.sample(g.row_ptr, g.col, v, 3, 0, 6000, paths=True)
+    assert np.array_equal(a.cnt1, b.cnt1) and np.array_equal(a.y1, b.y1)    # the Wilson part is shared
+    va = np.var(a.y1.astype(np.float64) - a.y2)
+    vb = np.var(b.y1.astype(np.float64) - b.y2)
+    assert vb < 0.5 * va, (vb, va)
 
 
 def test_estimates_converge_on_small_er():
