@@ -99,6 +99,8 @@ def parse():
                     help="roots of the landmark study on the BA 1e6 graph (0: skip)")
     ap.add_argument("--kemeny-sweep", type=int, default=1, help="kappa/n of 1e6-node BA and ER graphs (0: skip)")
     ap.add_argument("--study-samples", type=int, default=256, help="samples per root / graph of the two studies")
+    ap.add_argument("--paths", type=int, default=1,
+                    help="measure the loop-included-path form (LAP_OPT_PATHS) against own draws (0: skip)")
     ap.add_argument("--spantree-trees", type=int, default=16384,
                     help="SpanTree (Alg. 1/3) trees timed on the main workload (0: skip the SpanTree section)")
     ap.add_argument("--extra-workloads", default="rmat_22",
@@ -220,7 +222,7 @@ def read_truth():
     return np.array(ecc), kc, meta
 
 
-def time_to_accuracy(torch, LapGraph, seeds=10, target=1e-2, params=None):
+def time_to_accuracy(torch, LapGraph, seeds=10, target=1e-2, params=None, paths=0):
     """Smallest omega on the grid round(256 * 2^(k/4)) at which the mean over
     seeds of the ECC max relative error and of the Kemeny relative error are
     both <= 1e-2, on Erdos-Renyi G(1000, 0.01) against its dense FP64 truth;
@@ -237,9 +239,11 @@ def time_to_accuracy(torch, LapGraph, seeds=10, target=1e-2, params=None):
     if h.hexdigest() != meta.get("sha1"):
         return {"error": "dense truth file does not match the generated graph"}
     pilot = 4096
+    from paper_2311_10290_gb300.lap import LAP_OPT_PATHS
     handles = [LapGraph(g.row_ptr, g.col, workspace_bytes=8 * g.n * 65536) for _ in range(seeds)]
     betas = []
     for s, H in enumerate(handles):
+        H.set_option(LAP_OPT_PATHS, paths)
         H.set_root()
         if params is not None:
             betas.append(cv_prepare(H, params, 500 + s, pilot=pilot, batches=4)[2:])
@@ -271,6 +275,7 @@ def time_to_accuracy(torch, LapGraph, seeds=10, target=1e-2, params=None):
     if found is None:
         return {"workload": label, "reached": False, "curve": curve}
     H = LapGraph(g.row_ptr, g.col, workspace_bytes=8 * g.n * 65536)
+    H.set_option(LAP_OPT_PATHS, paths)
     H.set_root()
     prep = 0.0
     if params is not None:
@@ -429,6 +434,55 @@ def cv_measurement(torch, LapGraph, g, v, params, samples_per_batch, batches):
             "protocol": "%d fresh samples for Kemeny (per-sample variance); %d batches of %d for per-node "
                         "visit-count variance; ratios CV/plain on the same samples" % (samples_per_batch, batches,
                                                                                      samples_per_batch)}
+
+
+# ------------------------------------------------------------ loop-included paths
+
+def paths_measurement(torch, LapGraph, g, v, args, samples=16384, batches=4):
+    """LAP_OPT_PATHS = 1 against own draws on one graph: per-sample variance
+    of Y1 - Y2 (Kemeny), per-node variance of the L^+_uu numerator
+    (cnt1 - 2 cnt2) / d between batches (ECC), and sampler time."""
+    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, LAP_OPT_PATHS, lap_counts
+    free, _ = torch.cuda.mem_get_info()
+    out = {"workload": g.name, "samples": samples, "batches": batches}
+    d = np.diff(g.row_ptr.astype(np.int64)).astype(np.float64)
+    keep = np.ones(g.n, bool)
+    keep[v] = False
+    res = {}
+    for mode in (0, 1):
+        G = LapGraph(g.row_ptr, g.col, workspace_bytes=int(free * 0.5))
+        try:
+            G.set_option(LAP_OPT_PATHS, mode)
+            G.set_root(v)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            y1, y2 = G.sample_trace(samples, args.seed)
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3
+            kvar = float(np.var((y1 - y2).double().cpu().numpy()))
+            G.set_root(v)
+            G.set_option(LAP_OPT_CURSOR, samples)
+            prev1, prev2, rows = np.zeros(g.n), np.zeros(g.n), []
+            for _ in range(batches):
+                G.sample(samples, args.seed)
+                c1, c2, _ = lap_counts(G.h, g.n)
+                c1, c2 = c1.astype(np.float64), c2.astype(np.float64)
+                rows.append(((c1 - prev1) - 2.0 * (c2 - prev2)) / d)
+                prev1, prev2 = c1, c2
+            ev = np.array(rows).var(axis=0, ddof=1)[keep]
+        finally:
+            G.close()
+        res[mode] = (t, kvar, ev)
+    t0, k0, e0 = res[0]
+    t1, k1, e1 = res[1]
+    ok = e0 > 0
+    out.update({"kemeny_samples_ratio": k1 / k0, "ecc_numerator_samples_ratio_total": float(e1[ok].sum() / e0[ok].sum()),
+                "ecc_numerator_samples_ratio_median_node": float(np.median(e1[ok] / e0[ok])),
+                "sampler_time_ratio": t1 / t0, "sampler_seconds_own_draws": t0, "sampler_seconds_paths": t1,
+                "kemeny_time_ratio_same_error": k1 / k0 * t1 / t0})
+    return out
 
 
 # ------------------------------------------------------------ SpanTree (Alg. 1, Alg. 3)
@@ -864,6 +918,11 @@ def run_ours(args, rank, world):
             note("time to accuracy (CV)")
             info["time_to_accuracy_cv"] = time_to_accuracy(torch, LapGraph, params=params)
         res["cv_vs_plain"] = info
+    if rank == 0 and args.paths > 0:
+        note("loop-included paths against own draws")
+        res["paths_vs_own_draws"] = paths_measurement(torch, LapGraph, g, v, args)
+        if not args.no_tta:
+            res["paths_vs_own_draws"]["time_to_accuracy_paths"] = time_to_accuracy(torch, LapGraph, paths=1)
     if rank == 0 and args.spantree_trees > 0:
         note("SpanTree estimators")
         res["spantree"] = spantree_measurement(torch, LapGraph, g, v, args)

@@ -81,8 +81,17 @@ typedef enum {
                                   (more such nodes than the table holds, or a loop-erased path
                                   longer than the stack) is withdrawn and re-run with kernel 1:
                                   results are identical either way. */
-    LAP_OPT_STACK = 6          /* loop-erased path capacity per sample of kernel 2; 0 = default
+    LAP_OPT_STACK = 6,         /* loop-erased path capacity per sample of kernel 2; 0 = default
                                   (16 sqrt(n) rounded up to a power of two, at least 1024) */
+    LAP_OPT_PATHS = 7          /* 0 (default): the uniform-start and pi-start v-absorbed walks take
+                                  their own draws, as Alg. 2 and Alg. 4 print them.  1: they are the
+                                  loop-included paths of the sample's own Wilson stacks (Section 4.2,
+                                  "loop-erased walk" lemma and "Sample from the paths"; Section 5.2):
+                                  same starts, and the j-th departure of a path from u takes u's
+                                  stack entry j, the draw (u, j, i, 0) of the Wilson run.  Same
+                                  expectations (so the same estimands), correlated with the Wilson
+                                  counts, which lowers the variance of y1 - 2 y2 and of Y1 - Y2.
+                                  Only before the first sample after lap_set_root. */
 } lap_option;
 
 /* Statistics for lap_get_stat. */

@@ -40,7 +40,8 @@ typedef enum {
     LAP_BOPT_ORDER = 3,  /* unit order: 0 = largest graphs first (default), 1 = smallest first,
                             2 = the caller's graph order */
     LAP_BOPT_BLOCK = 4,  /* threads per block; 0 = automatic */
-    LAP_BOPT_STACK = 5   /* loop-erased path capacity per lane; 0 = 16 sqrt(largest n), at least 1024 */
+    LAP_BOPT_STACK = 5,  /* loop-erased path capacity per lane; 0 = 16 sqrt(largest n), at least 1024 */
+    LAP_BOPT_PATHS = 6   /* LAP_OPT_PATHS for every graph of the batch (0 default, 1 loop-included paths) */
 } lap_batch_option;
 
 /* Statistics for lap_batch_stat. */

@@ -56,7 +56,7 @@ struct lap_batch {
     cudaGraphExec_t exec = nullptr;
     bool key_valid = false;
     uint64_t key_samples = 0, key_seed = 0, key_lanes = 0;
-    uint32_t key_claim = 0, key_stack = 0;
+    uint32_t key_claim = 0, key_stack = 0, key_paths = 0;
     int key_order = -1, key_block = -1;
     int64_t captures = 0;
 
@@ -65,6 +65,7 @@ struct lap_batch {
     int order_opt = 0;
     int block_opt = 0;
     uint32_t stack_opt = 0;
+    uint32_t paths_opt = 0;
 
     uint64_t omega = 0;
     uint64_t seed = 0;
@@ -279,6 +280,7 @@ LapBatchLaunch make_launch(const lap_batch *b, uint64_t seed, uint64_t lanes, ui
     p.ovf_cap = b->ovf_cap;
     p.block = block;
     p.num_sms = b->num_sms;
+    p.paths = b->paths_opt;
     return p;
 }
 
@@ -323,6 +325,7 @@ lap_status capture(lap_batch *b, uint64_t samples, uint64_t seed, uint64_t lanes
     b->key_order = b->order_opt;
     b->key_block = block;
     b->key_stack = stack_cap_of(b);
+    b->key_paths = b->paths_opt;
     ++b->captures;
     return LAP_OK;
 }
@@ -375,6 +378,7 @@ lap_status rerun_withdrawn(lap_batch *b, uint32_t count)
             p.step_limit = d.step_limit;
             p.num_sms = b->num_sms;
             p.ids = b->d_rerun_ids + jb.a;
+            p.paths = b->paths_opt;
             B_CUDA(b, lap_launch_sample(p, st));
         }
         for (int k = 0; k < kRerunStreams && k < (int)group.size(); ++k) {
@@ -696,6 +700,10 @@ lap_status lap_batch_set_option(lap_batch *b, int32_t option, int64_t value)
         if (value != 0 && (value % 32 != 0 || value > 256)) return bfail(b, LAP_ERR_INVALID_ARG, "block must be 0 or a multiple of 32 up to 256");
         b->block_opt = (int)value;
         return LAP_OK;
+    case LAP_BOPT_PATHS:
+        if (value > 1) return bfail(b, LAP_ERR_INVALID_ARG, "paths must be 0 or 1");
+        b->paths_opt = (uint32_t)value;
+        return LAP_OK;
     case LAP_BOPT_STACK:
         if (value != 0 && (value < 16 || value > (1 << 26) || (value & 3))) return bfail(b, LAP_ERR_INVALID_ARG, "stack capacity must be 0 or a multiple of 4 in [16, 2^26]");
         if ((uint32_t)value != b->stack_opt) b->meta_dirty = true;
@@ -755,7 +763,8 @@ lap_status lap_batch_run(lap_batch *b, uint64_t samples_per_graph, uint64_t seed
     if (lanes == 0) return bfail(b, LAP_ERR_OOM, "no lane fits the workspace");
     const uint32_t claim = b->claim_opt;
     if (!b->key_valid || !b->exec || b->key_samples != samples_per_graph || b->key_seed != seed || b->key_lanes != lanes ||
-        b->key_claim != claim || b->key_order != b->order_opt || b->key_block != block || b->key_stack != stack_cap_of(b)) {
+        b->key_claim != claim || b->key_order != b->order_opt || b->key_block != block || b->key_stack != stack_cap_of(b) ||
+        b->key_paths != b->paths_opt) {
         s = capture(b, samples_per_graph, seed, lanes, claim, block);
         if (s != LAP_OK) return s;
     }

@@ -8,11 +8,14 @@
 // Draw counts k <= 30 live in the byte.  From the 31st draw at a node on, the
 // byte holds kKSat and the count lives in a per-lane open-addressing table
 // after the path stack: 2^tbl_log2 entries {node + 1 : 32 | tag : 8 | k : 24}.
-// Each sample of a lane has its own tag (1..255), so entries of earlier
-// samples read as empty and the table is cleared only when the tag wraps (and
-// at the lane's first sample).  A sample that needs more entries than a probe
-// run of kTblProbes finds, more than kKMax draws at a node, or a longer path
-// than the stack holds is withdrawn.
+// Each sample of a lane owns three consecutive tags (base, base+1, base+2):
+// base keys the Wilson draw counts; base+1 and base+2 key the departure
+// counts of the loop-included paths (uniform and pi start) when the absorbed
+// walks are taken on the sample's own stacks.  Entries with other tags read
+// as empty, so the table is cleared only when the tags wrap (and at the
+// lane's first sample).  A sample that needs more entries than a probe run of
+// kTblProbes finds, more than kKMax draws at a node, or a longer path than the
+// stack holds is withdrawn.
 #pragma once
 
 #include "lap_internal.h"
@@ -178,29 +181,35 @@ static __device__ __forceinline__ uint32_t tbl_home(uint32_t node, uint32_t log2
     return (node * 2654435761u) >> (32u - log2);
 }
 
-// True draw count of a node whose byte holds kKSat (0 if absent: an error).
+// An entry belongs to the current sample when its tag is base .. base + 2.
+static __device__ __forceinline__ bool tbl_live(unsigned long long e, uint32_t base)
+{
+    return (((uint32_t)e >> 24) - base) <= 2u;
+}
+
+// Count of (node, tag); 0 if absent.
 static __device__ __forceinline__ uint32_t tbl_get(const unsigned long long *tbl, uint32_t log2, uint32_t node,
-                                                   uint32_t tag)
+                                                   uint32_t tag, uint32_t base)
 {
     const uint32_t mask = (1u << log2) - 1u;
     uint32_t s = tbl_home(node, log2);
     for (uint32_t q = 0; q < kTblProbes; ++q, s = (s + 1u) & mask) {
         const unsigned long long e = tbl[s];
-        if (((uint32_t)e >> 24) != tag) break;                 // empty for this sample
-        if ((uint32_t)(e >> 32) == node + 1u) return (uint32_t)e & 0xFFFFFFu;
+        if (!tbl_live(e, base)) break;
+        if ((uint32_t)(e >> 32) == node + 1u && ((uint32_t)e >> 24) == tag) return (uint32_t)e & 0xFFFFFFu;
     }
     return 0u;
 }
 
-// Sets a node's count (inserting it); false when its probe run is full.
+// Sets the count of (node, tag), inserting it; false when its probe run is full.
 static __device__ __forceinline__ bool tbl_put(unsigned long long *tbl, uint32_t log2, uint32_t node, uint32_t k,
-                                               uint32_t tag)
+                                               uint32_t tag, uint32_t base)
 {
     const uint32_t mask = (1u << log2) - 1u;
     uint32_t s = tbl_home(node, log2);
     for (uint32_t q = 0; q < kTblProbes; ++q, s = (s + 1u) & mask) {
         const unsigned long long e = tbl[s];
-        if (((uint32_t)e >> 24) != tag || (uint32_t)(e >> 32) == node + 1u) {
+        if (!tbl_live(e, base) || ((uint32_t)(e >> 32) == node + 1u && ((uint32_t)e >> 24) == tag)) {
             tbl[s] = ((unsigned long long)(node + 1u) << 32) | ((unsigned long long)tag << 24) | k;
             return true;
         }
@@ -214,14 +223,14 @@ static __device__ __forceinline__ void tbl_clear(unsigned long long *tbl, uint32
     for (uint32_t j = 0; j < (1u << log2) / 2u; ++j) t[j] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Next sample's tag; clears the table when the tags wrap around.
-static __device__ __forceinline__ uint32_t tbl_next_tag(unsigned long long *tbl, uint32_t log2, uint32_t tag)
+// Next sample's base tag; clears the table when the tags wrap around.
+static __device__ __forceinline__ uint32_t tbl_next_tag(unsigned long long *tbl, uint32_t log2, uint32_t base)
 {
-    if (tag >= 255u) {
+    if (base >= 250u) {
         tbl_clear(tbl, log2);
         return 1u;
     }
-    return tag + 1u;
+    return base + 3u;
 }
 
 // Withdraws a partly run sample: subtracts the k - 1 repeat visits every
@@ -234,6 +243,7 @@ static __device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsi
                                 uint32_t key0, uint32_t key1, const unsigned long long *tbl, uint32_t log2,
                                 uint32_t tag)
 {
+    // (tag is the sample's base tag: the Wilson draw counts.)
     for (int32_t base = 0; base < n; base += 16) {
         ulonglong2 q = *reinterpret_cast<ulonglong2 *>(st + base);
 #pragma unroll
@@ -271,6 +281,37 @@ static __device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsi
                 sub += h1[col[r.x + (int64_t)lap::below(x, (uint64_t)r.y)]];
             }
             atomicAdd(&a1[node], (unsigned long long)(-sub));
+        }
+    }
+}
+
+// Withdraws what the loop-included paths of a sample added before it was
+// withdrawn (paths taken on the sample's stacks; departures counted in the
+// table under base + 1 and base + 2): every departure of the uniform-start
+// path added one pass to cnt2; every departure of the pi-start path added
+// h2[w] to a2 and one to p2 (control variate).
+static __device__ void withdraw_paths(const unsigned long long *tbl, uint32_t log2, uint32_t base, int32_t n,
+                                      unsigned long long *cnt2, const int2 *rowinfo, const int32_t *col,
+                                      const long long *h2, unsigned long long *a2, unsigned long long *p2,
+                                      uint32_t i, uint32_t key0, uint32_t key1)
+{
+    for (uint32_t j = 0; j < (1u << log2); ++j) {
+        const unsigned long long e = tbl[j];
+        const uint32_t t = (uint32_t)e >> 24;
+        if (t != base + 1u && t != base + 2u) continue;
+        const uint32_t node = (uint32_t)(e >> 32) - 1u, k = (uint32_t)e & 0xFFFFFFu;
+        if ((int32_t)node >= n || k == 0u) continue;
+        if (t == base + 1u) {
+            atomicAdd(&cnt2[node], (unsigned long long)(-(long long)k));
+        } else if (h2) {
+            const int2 r = rowinfo[node];
+            long long sub = 0;
+            for (uint32_t d = 0; d < k; ++d) {
+                const uint64_t x = lap::philox_r64(node, d, i, 0u, key0, key1);
+                sub += h2[col[r.x + (int64_t)lap::below(x, (uint64_t)r.y)]];
+            }
+            atomicAdd(&a2[node], (unsigned long long)(-sub));
+            atomicAdd(&p2[node], (unsigned long long)(-(long long)k));
         }
     }
 }

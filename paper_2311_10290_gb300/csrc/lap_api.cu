@@ -356,6 +356,11 @@ lap_status lap_set_option(lap_graph *g, int32_t option, int64_t value)
         if (value != 0 && (value % 32 != 0 || value > 256)) return fail(g, LAP_ERR_INVALID_ARG, "block must be 0 or a multiple of 32 up to 256");
         g->block_opt = (int)value;
         return LAP_OK;
+    case LAP_OPT_PATHS:
+        if (value > 1) return fail(g, LAP_ERR_INVALID_ARG, "paths must be 0 or 1");
+        if (g->omega != 0) return fail(g, LAP_ERR_INVALID_ARG, "the walk mode can only be set before the first sample after lap_set_root");
+        g->paths_opt = (uint32_t)value;
+        return LAP_OK;
     default:
         return fail(g, LAP_ERR_INVALID_ARG, "unknown option");
     }
@@ -528,6 +533,7 @@ static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, 
     p.step_limit = g->step_limit ? g->step_limit : default_step_limit(g->n);
     p.block = g->block_opt;
     p.num_sms = g->num_sms;
+    p.paths = g->paths_opt;
     p.y1_out = reinterpret_cast<unsigned long long *>(y1_dev);
     p.y2_out = reinterpret_cast<unsigned long long *>(y2_dev);
     p.m2_out = m2_dev;

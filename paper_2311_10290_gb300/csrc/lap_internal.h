@@ -70,6 +70,8 @@ struct LapSampleLaunch {
     uint64_t n_pad;              // compact kernel: state bytes of one slot (n rounded up to 256)
     uint32_t stack_cap;          // compact kernel: stack entries of one slot
     uint32_t tbl_log2;           // compact kernel: log2 of the count-table entries
+    uint32_t paths;              // 1: the absorbed walks are the loop-included paths of the sample's
+                                 // own stacks (departure j from u takes draw (u, j, i, 0)); 0: own draws
     unsigned int *ovf_ids;       // compact kernel: withdrawn sample ids [count]
     const unsigned int *ids;     // wide kernel: explicit sample ids [count] (NULL: first + q)
     uint32_t trace_base;         // wide kernel with ids: y1_out/y2_out index = id - trace_base
@@ -134,6 +136,7 @@ struct LapBatchLaunch {
     uint64_t n_pad;               // state bytes of a slot (largest n rounded up to 256)
     uint32_t stack_cap;
     uint32_t tbl_log2;            // log2 of the count-table entries of a slot
+    uint32_t paths;               // as LapSampleLaunch::paths
     unsigned int *slot_meta;      // per lane: bit 31 epoch, bits 0..30 extent of bytes carrying it
     LapDevAcc *acc;               // [graphs] sum Y1, sum Y2
     unsigned int *done;           // [graphs] samples finished
@@ -265,6 +268,7 @@ struct lap_graph {
     uint64_t slots_opt = 0;
     int block_opt = 0;
     int kernel_opt = 0;                     // 0 auto, LAP_KERNEL_WIDE, LAP_KERNEL_COMPACT
+    uint32_t paths_opt = 0;                 // LAP_OPT_PATHS
     uint32_t stack_cap = 0;                 // 0: default, about 16 sqrt(n)
     int last_kernel = 0;                    // layout the workspace currently holds
     bool compact_disabled = false;          // set after a compact launch overflowed

@@ -34,6 +34,11 @@ namespace {
 constexpr uint64_t kEpoch = 1ull << 63;
 constexpr uint64_t kTree = 1ull << 62;
 constexpr uint32_t kKMax = 0x3FFFFFFFu;
+// Loop-included paths (LapSampleLaunch::paths): after the Wilson run every
+// word is InTree; the uniform-start path clears InTree at the nodes it
+// leaves and keeps its departure count in the k field, the pi-start path
+// marks them with bit 31 (node ids are < 2^31) and keeps its own count there.
+constexpr uint64_t kPiMark = 1ull << 31;
 
 enum Phase : uint32_t {
     P_CLAIM = 0,
@@ -132,17 +137,39 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
             }
         } else if (phase == P_UDRAW) {
             ++t;
-            const uint64_t r = lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1);
+            uint64_t r;
+            if (p.paths) {
+                // Departure j from u takes u's stack entry j (draw (u, j, i, 0)).
+                const uint32_t j = (pa & kTree) ? 0u : (uint32_t)(pa >> 32) & kKMax;
+                r = lap::philox_r64((uint32_t)u, j, i, 0u, key0, key1);
+                st[u] = (unsigned long long)(epoch | ((uint64_t)(j + 1u) << 32) | (pa & 0xFFFFFFFFull));
+                atomicAdd(&p.cnt2[u], 1ull);
+            } else {
+                r = lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1);
+            }
             pb = (uint64_t)(uint32_t)__ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
             phase = P_UMOVE;
             if (t > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; }
         } else if (phase == P_UMOVE) {
             u = (int32_t)(uint32_t)pb;
             if (u == v) phase = P_PISTART;
-            else { atomicAdd(&p.cnt2[u], 1ull); pb = ld_row(rowinfo, u); phase = P_UDRAW; }
+            else {
+                if (p.paths) pa = st[u];
+                else atomicAdd(&p.cnt2[u], 1ull);
+                pb = ld_row(rowinfo, u);
+                phase = P_UDRAW;
+            }
         } else if (phase == P_PIDRAW) {
             ++y2;
-            const uint64_t r = lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1);
+            uint64_t r;
+            if (p.paths) {
+                const uint32_t j = (pa & kPiMark) ? (uint32_t)(pa >> 32) & kKMax : 0u;
+                r = lap::philox_r64((uint32_t)u, j, i, 0u, key0, key1);
+                st[u] = (unsigned long long)(epoch | (pa & kTree) | ((uint64_t)(j + 1u) << 32) | kPiMark |
+                                             (pa & 0x7FFFFFFFull));
+            } else {
+                r = lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1);
+            }
             const int32_t w = __ldg(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)));
             if (p.cv_h2) {
                 const long long d = (long long)row_deg(pb), hw = p.cv_h2[w], s2 = p.cv_S2[u];
@@ -166,7 +193,11 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
                 }
                 phase = P_CLAIM;
             }
-            else { pb = ld_row(rowinfo, u); phase = P_PIDRAW; }
+            else {
+                if (p.paths) pa = st[u];
+                pb = ld_row(rowinfo, u);
+                phase = P_PIDRAW;
+            }
         } else if (phase == P_USTART) {
             if (p.flags & LAP_SAMPLE_WILSON_ONLY) {
                 acc1 += y1;
@@ -178,7 +209,12 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
             const uint64_t r = lap::philox_r64(0u, 0u, i, 1u, key0, key1);
             u = (int32_t)lap::below(r, (uint64_t)n);
             if (u == v) phase = P_PISTART;
-            else { atomicAdd(&p.cnt2[u], 1ull); pb = ld_row(rowinfo, u); phase = P_UDRAW; }
+            else {
+                if (p.paths) pa = st[u];
+                else atomicAdd(&p.cnt2[u], 1ull);
+                pb = ld_row(rowinfo, u);
+                phase = P_UDRAW;
+            }
         } else if (phase == P_PISTART) {
             // Alg. 4: s ~ pi is the head of a uniformly drawn arc.
             y2 = 0;

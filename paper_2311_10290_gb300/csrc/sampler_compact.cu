@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
                 if (b_path(b, ep)) sp = erase_loop(st, stk, sp, ep, (uint32_t)h, pq, chunk);
                 uint32_t kh = b_k(b, ep);
                 if (kh == kKSat) {
-                    kh = tbl_get(tbl_of(stk, cap), tlog, (uint32_t)h, tag);
+                    kh = tbl_get(tbl_of(stk, cap), tlog, (uint32_t)h, tag, tag);
                     if (kh < kKSat) { bad |= LAP_DEV_BAD_INDEX; phase = P_CLAIM; continue; }
                 }
                 if (kh) w = ld_col(col + off + (int64_t)lap::below(lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1), deg), keep);
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
                 bool fits = kn <= kKMax && sp < cap;
                 if (fits && kn >= kKSat) {
                     kb = kKSat;
-                    fits = tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, kn, tag);
+                    fits = tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, kn, tag, tag);
                 }
                 if (!fits) {
                     withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1, tbl_of(stk, cap), tlog, tag);
@@ -173,15 +173,41 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
             // Alg. 2: uniformly sample s in V; walk until v, counting passes.
             t = 0;
             h = (int32_t)lap::below(lap::philox_r64(0u, 0u, i, 1u, key0, key1), (uint64_t)n);
-            if (h != v) { atomicAdd(&p.cnt2[h], 1ull); pb = ld_row(rowinfo, h, keep); phase = P_UWALK; continue; }
+            if (h != v) {
+                if (!p.paths) atomicAdd(&p.cnt2[h], 1ull);
+                pb = ld_row(rowinfo, h, keep);
+                phase = P_UWALK;
+                continue;
+            }
             phase = P_PISTART_IMMEDIATE;
         }
         if (phase == P_UWALK) {
             ++t;
-            const uint64_t r = lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1);
-            h = ld_col(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)), keep);
+            int32_t w;
+            if (p.paths) {
+                // Loop-included path: departure j from h takes h's stack entry j.
+                const uint32_t j = tbl_get(tbl_of(stk, cap), tlog, (uint32_t)h, tag + 1u, tag);
+                w = ld_col(col + row_off(pb) + (int64_t)lap::below(lap::philox_r64((uint32_t)h, j, i, 0u, key0, key1), row_deg(pb)), keep);
+                if (!tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, j + 1u, tag + 1u, tag)) {
+                    withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1, tbl_of(stk, cap), tlog, tag);
+                    withdraw_paths(tbl_of(stk, cap), tlog, tag, n, p.cnt2, rowinfo, col, CV ? p.cv_h2 : nullptr, p.cv_a2, p.cv_p2, i, key0, key1);
+                    const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
+                    if (ix < p.count) p.ovf_ids[ix] = i;
+                    phase = P_CLAIM;
+                    continue;
+                }
+                atomicAdd(&p.cnt2[h], 1ull);
+            } else {
+                const uint64_t r = lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1);
+                w = ld_col(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)), keep);
+            }
+            h = w;
             if (t > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
-            if (h != v) { atomicAdd(&p.cnt2[h], 1ull); pb = ld_row(rowinfo, h, keep); continue; }
+            if (h != v) {
+                if (!p.paths) atomicAdd(&p.cnt2[h], 1ull);
+                pb = ld_row(rowinfo, h, keep);
+                continue;
+            }
             phase = P_PISTART_IMMEDIATE;
         }
         if (phase == P_PISTART_IMMEDIATE) {
@@ -194,8 +220,22 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
         }
         if (phase == P_PIWALK) {
             ++y2;
-            const uint64_t r = lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1);
-            const int32_t w = ld_col(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)), keep);
+            int32_t w;
+            if (p.paths) {
+                const uint32_t j = tbl_get(tbl_of(stk, cap), tlog, (uint32_t)h, tag + 2u, tag);
+                w = ld_col(col + row_off(pb) + (int64_t)lap::below(lap::philox_r64((uint32_t)h, j, i, 0u, key0, key1), row_deg(pb)), keep);
+                if (!tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, j + 1u, tag + 2u, tag)) {
+                    withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1, tbl_of(stk, cap), tlog, tag);
+                    withdraw_paths(tbl_of(stk, cap), tlog, tag, n, p.cnt2, rowinfo, col, CV ? p.cv_h2 : nullptr, p.cv_a2, p.cv_p2, i, key0, key1);
+                    const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
+                    if (ix < p.count) p.ovf_ids[ix] = i;
+                    phase = P_CLAIM;
+                    continue;
+                }
+            } else {
+                const uint64_t r = lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1);
+                w = ld_col(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)), keep);
+            }
             if (CV && p.cv_h2) {
                 if ((uint32_t)h >= (uint32_t)n || (uint32_t)w >= (uint32_t)n) {
                     bad |= LAP_DEV_BAD_INDEX;

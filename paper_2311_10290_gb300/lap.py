@@ -26,9 +26,10 @@ STATUS = {
     8: "LAP_ERR_NO_SAMPLES", 9: "LAP_ERR_STEP_LIMIT", 10: "LAP_ERR_CUDA", 11: "LAP_ERR_NO_ROOT",
 }
 LAP_OPT_STEP_LIMIT, LAP_OPT_SLOTS, LAP_OPT_BLOCK, LAP_OPT_CURSOR, LAP_OPT_KERNEL, LAP_OPT_STACK = 1, 2, 3, 4, 5, 6
+LAP_OPT_PATHS = 7
 LAP_STAT_SLOTS, LAP_STAT_KERNEL, LAP_STAT_FALLBACKS = 1, 2, 3
 LAP_MLP_PARAMS = 4866
-LAP_BOPT_LANES, LAP_BOPT_CLAIM, LAP_BOPT_ORDER, LAP_BOPT_BLOCK, LAP_BOPT_STACK = 1, 2, 3, 4, 5
+LAP_BOPT_LANES, LAP_BOPT_CLAIM, LAP_BOPT_ORDER, LAP_BOPT_BLOCK, LAP_BOPT_STACK, LAP_BOPT_PATHS = 1, 2, 3, 4, 5, 6
 LAP_BSTAT_LANES, LAP_BSTAT_CLAIM, LAP_BSTAT_UNITS, LAP_BSTAT_RERUNS, LAP_BSTAT_GRAPH_CAPTURES = 1, 2, 3, 4, 5
 
 

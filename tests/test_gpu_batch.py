@@ -13,7 +13,8 @@ from paper_2311_10290_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-from paper_2311_10290_gb300.lap import (LAP_BOPT_CLAIM, LAP_BOPT_LANES, LAP_BOPT_ORDER, LAP_BOPT_STACK,  # noqa: E402
+from paper_2311_10290_gb300.lap import (LAP_BOPT_CLAIM, LAP_BOPT_LANES, LAP_BOPT_ORDER, LAP_BOPT_PATHS,  # noqa: E402
+                                        LAP_BOPT_STACK,
                                         LAP_BSTAT_GRAPH_CAPTURES, LAP_BSTAT_RERUNS, LapBatch, LapError, LapGraph)
 
 
@@ -281,3 +282,22 @@ def test_kirchhoff_and_rw_betweenness_match_oracle():
         assert kf == pytest.approx(tr, rel=1e-12) and kf == kf_b[j]
         np.testing.assert_allclose(cb, cbo, rtol=1e-12)
         assert np.array_equal(cb, cb_dev)
+
+
+def test_batch_loop_included_paths_match_oracle():
+    graphs = mixed_graphs() + [I.path(256)]
+    roots = [-1] * (len(graphs) - 1) + [255]
+    k, seed = 30, 4
+    B = LapBatch([(g.row_ptr, g.col) for g in graphs], roots=roots, workspace_bytes=1 << 26)
+    try:
+        B.set_option(LAP_BOPT_PATHS, 1)
+        B.set_option(LAP_BOPT_LANES, 96)
+        B.run(k, seed)
+        for j, g in enumerate(graphs):
+            v = int(B.roots[j])
+            c = oracle.sample(g.row_ptr, g.col, v, seed, 0, k, keep_per_sample=False, paths=True)
+            c1, c2, sums = B.counts(j)
+            assert np.array_equal(c1, c.cnt1) and np.array_equal(c2, c.cnt2), j
+            assert int(sums[1]) == c.sum_y1 and int(sums[2]) == c.sum_y2, j
+    finally:
+        B.close()

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 from paper_2311_10290_gb300 import cv as CVG  # noqa: E402
-from paper_2311_10290_gb300.lap import (LAP_MLP_PARAMS, LAP_OPT_KERNEL, LapGraph, lap_adamw,  # noqa: E402
+from paper_2311_10290_gb300.lap import (LAP_MLP_PARAMS, LAP_OPT_KERNEL, LAP_OPT_PATHS, LapGraph, lap_adamw,  # noqa: E402
                                         lap_mlp_forward, lap_mlp_loss_grad)
 
 
@@ -60,11 +60,13 @@ def test_hitting_walks_bit_exact():
     assert np.array_equal(s, oracle.hitting_walks(g.row_ptr, g.col, v, 99, 7))
 
 
-def _cv_run(g, root, seed, omega, phi1, phi2, kernel=None, splits=None):
+def _cv_run(g, root, seed, omega, phi1, phi2, kernel=None, splits=None, paths=False):
     G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 28)
     try:
         if kernel:
             G.set_option(LAP_OPT_KERNEL, kernel)
+        if paths:
+            G.set_option(LAP_OPT_PATHS, 1)
         v = G.set_root(root)
         G.cv_set_potentials(None if phi1 is None else torch.from_numpy(phi1).cuda(),
                             None if phi2 is None else torch.from_numpy(phi2).cuda())
@@ -78,21 +80,22 @@ def _cv_run(g, root, seed, omega, phi1, phi2, kernel=None, splits=None):
         G.close()
 
 
+@pytest.mark.parametrize("paths", [False, True], ids=["own_draws", "stack_paths"])
 @pytest.mark.parametrize("kernel", [1, 2], ids=["wide", "compact"])
 @pytest.mark.parametrize("name,maker,root", [("ba", lambda: I.ba(3000, 3, seed=5), -1),
                                              ("rmat", lambda: I.rmat(9, 8, seed=6), -1),
                                              ("path_counts_table", lambda: I.path(50), 0),
                                              ("path_table_heavy", lambda: I.path(256), 255)],
                          ids=["ba", "rmat", "path_counts_table", "path_table_heavy"])
-def test_cv_sums_and_estimates_match_oracle(name, maker, root, kernel):
+def test_cv_sums_and_estimates_match_oracle(name, maker, root, kernel, paths):
     g = maker()
     rng = np.random.default_rng(3)
     phi1 = rng.uniform(0.0, 3.0, g.n)
     phi2 = rng.uniform(0.0, 50.0, g.n)
-    r = _cv_run(g, root, 17, 300, phi1, phi2, kernel=kernel, splits=[100, 200])
+    r = _cv_run(g, root, 17, 300, phi1, phi2, kernel=kernel, splits=[100, 200], paths=paths)
     v = r["v"]
     h1, h2 = CV.quantize_potential(phi1), CV.quantize_potential(phi2)
-    cnt, a1, a2, p2, m2 = oracle.sample_cv(g.row_ptr, g.col, v, 17, 0, 300, h1=h1, h2=h2)
+    cnt, a1, a2, p2, m2 = oracle.sample_cv(g.row_ptr, g.col, v, 17, 0, 300, h1=h1, h2=h2, paths=paths)
     assert np.array_equal(r["c1"], cnt.cnt1) and np.array_equal(r["c2"], cnt.cnt2)
     assert np.array_equal(r["a1"], a1) and np.array_equal(r["a2"], a2) and np.array_equal(r["p2"], p2)
     z1 = CV.martingale_z1(g.row_ptr, g.col, h1, cnt.cnt1, a1)
