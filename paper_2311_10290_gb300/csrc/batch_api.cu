@@ -149,7 +149,8 @@ uint64_t n_pad_of(const lap_batch *b) { return ((uint64_t)b->max_n + 255ull) & ~
 
 uint64_t slot_bytes_of(const lap_batch *b)
 {
-    return (n_pad_of(b) + 4ull * stack_cap_of(b) + (8ull << lap_table_log2(b->max_n)) + 255ull) & ~255ull;
+    return ((b->paths_opt ? 2ull : 1ull) * n_pad_of(b) + 4ull * stack_cap_of(b) + (8ull << lap_table_log2(b->max_n)) +
+            255ull) & ~255ull;
 }
 
 // Work units in claim order (shared by lap_batch_run and lap_batch_schedule).
@@ -270,7 +271,7 @@ LapBatchLaunch make_launch(const lap_batch *b, uint64_t seed, uint64_t lanes, ui
     p.slot_bytes = slot_bytes_of(b);
     p.n_pad = n_pad_of(b);
     p.tbl_log2 = lap_table_log2(b->max_n);
-    p.stack_cap = (uint32_t)((p.slot_bytes - p.n_pad - (8ull << p.tbl_log2)) / 4ull);
+    p.stack_cap = (uint32_t)((p.slot_bytes - (b->paths_opt ? 2ull : 1ull) * p.n_pad - (8ull << p.tbl_log2)) / 4ull);
     p.slot_meta = b->d_slot_meta;
     p.acc = b->d_acc;
     p.done = b->d_done;
@@ -702,6 +703,7 @@ lap_status lap_batch_set_option(lap_batch *b, int32_t option, int64_t value)
         return LAP_OK;
     case LAP_BOPT_PATHS:
         if (value > 1) return bfail(b, LAP_ERR_INVALID_ARG, "paths must be 0 or 1");
+        if (b->paths_opt != (uint32_t)value) b->meta_dirty = true;   // the slot layout changes
         b->paths_opt = (uint32_t)value;
         return LAP_OK;
     case LAP_BOPT_STACK:

@@ -285,33 +285,51 @@ static __device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsi
     }
 }
 
-// Withdraws what the loop-included paths of a sample added before it was
-// withdrawn (paths taken on the sample's stacks; departures counted in the
-// table under base + 1 and base + 2): every departure of the uniform-start
-// path added one pass to cnt2; every departure of the pi-start path added
-// h2[w] to a2 and one to p2 (control variate).
-static __device__ void withdraw_paths(const unsigned long long *tbl, uint32_t log2, uint32_t base, int32_t n,
-                                      unsigned long long *cnt2, const int2 *rowinfo, const int32_t *col,
-                                      const long long *h2, unsigned long long *a2, unsigned long long *p2,
-                                      uint32_t i, uint32_t key0, uint32_t key1)
+// Loop-included paths (paths taken on the sample's own stacks): each node has
+// one more byte in a second region of the slot, reset chunk by chunk while
+// the Wilson scan passes over it: bits 0..3 count the departures of the
+// uniform-start path from the node, bits 4..7 those of the pi-start path; 15
+// means "15 or more, see the table" (tags base + 1 and base + 2).
+constexpr uint32_t kPathSat = 15u;
+
+// Departure count of `nib` (0: uniform path, 1: pi path) of a node.
+static __device__ __forceinline__ uint32_t path_count(uint32_t byte, uint32_t nib, const unsigned long long *tbl,
+                                                      uint32_t log2, uint32_t node, uint32_t base)
 {
-    for (uint32_t j = 0; j < (1u << log2); ++j) {
-        const unsigned long long e = tbl[j];
-        const uint32_t t = (uint32_t)e >> 24;
-        if (t != base + 1u && t != base + 2u) continue;
-        const uint32_t node = (uint32_t)(e >> 32) - 1u, k = (uint32_t)e & 0xFFFFFFu;
-        if ((int32_t)node >= n || k == 0u) continue;
-        if (t == base + 1u) {
-            atomicAdd(&cnt2[node], (unsigned long long)(-(long long)k));
-        } else if (h2) {
-            const int2 r = rowinfo[node];
-            long long sub = 0;
-            for (uint32_t d = 0; d < k; ++d) {
-                const uint64_t x = lap::philox_r64(node, d, i, 0u, key0, key1);
-                sub += h2[col[r.x + (int64_t)lap::below(x, (uint64_t)r.y)]];
+    const uint32_t c = (byte >> (4u * nib)) & 0xFu;
+    return c < kPathSat ? c : tbl_get(tbl, log2, node, base + 1u + nib, base);
+}
+
+// Withdraws what the loop-included paths of a sample added before it was
+// withdrawn: every departure of the uniform-start path added one pass to
+// cnt2; every departure of the pi-start path added h2[w] to a2 and one to p2
+// (control variate).
+static __device__ void withdraw_paths(const uint8_t *pr, int32_t n, const unsigned long long *tbl, uint32_t log2,
+                                      uint32_t base, unsigned long long *cnt2, const int2 *rowinfo,
+                                      const int32_t *col, const long long *h2, unsigned long long *a2,
+                                      unsigned long long *p2, uint32_t i, uint32_t key0, uint32_t key1)
+{
+    for (int32_t c0 = 0; c0 < n; c0 += 16) {
+        const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(pr + c0);
+        if ((q.x | q.y) == 0ull) continue;
+        for (int b = 0; b < 16; ++b) {
+            const int32_t u = c0 + b;
+            if (u >= n) break;
+            const uint32_t byte = (uint32_t)(((b < 8 ? q.x : q.y) >> (8 * (b & 7))) & 0xFFu);
+            if (!byte) continue;
+            const uint32_t ju = path_count(byte, 0u, tbl, log2, (uint32_t)u, base);
+            const uint32_t jp = path_count(byte, 1u, tbl, log2, (uint32_t)u, base);
+            if (ju) atomicAdd(&cnt2[u], (unsigned long long)(-(long long)ju));
+            if (jp && h2) {
+                const int2 r = rowinfo[u];
+                long long sub = 0;
+                for (uint32_t d = 0; d < jp; ++d) {
+                    const uint64_t x = lap::philox_r64((uint32_t)u, d, i, 0u, key0, key1);
+                    sub += h2[col[r.x + (int64_t)lap::below(x, (uint64_t)r.y)]];
+                }
+                atomicAdd(&a2[u], (unsigned long long)(-sub));
+                atomicAdd(&p2[u], (unsigned long long)(-(long long)jp));
             }
-            atomicAdd(&a2[node], (unsigned long long)(-sub));
-            atomicAdd(&p2[node], (unsigned long long)(-(long long)k));
         }
     }
 }

@@ -99,7 +99,9 @@ uint32_t stack_cap_of(const lap_graph *g)
 uint64_t slot_bytes_of(const lap_graph *g, int kernel)
 {
     if (kernel == LAP_KERNEL_WIDE) return 8ull * (uint64_t)g->n;
-    return (n_pad_of(g) + 4ull * stack_cap_of(g) + (8ull << lap_table_log2(g->n)) + 255ull) & ~255ull;
+    // State bytes, path-count bytes (loop-included paths only), stack, count table.
+    return ((g->paths_opt ? 2ull : 1ull) * n_pad_of(g) + 4ull * stack_cap_of(g) + (8ull << lap_table_log2(g->n)) +
+            255ull) & ~255ull;
 }
 
 int choose_kernel(const lap_graph *g)
@@ -163,7 +165,9 @@ lap_status launch(lap_graph *g, LapSampleLaunch &p, int kernel)
     p.slot_bytes = slot_bytes_of(g, kernel);
     p.n_pad = n_pad_of(g);
     p.tbl_log2 = lap_table_log2(g->n);
-    p.stack_cap = kernel == LAP_KERNEL_COMPACT ? (uint32_t)((p.slot_bytes - p.n_pad - (8ull << p.tbl_log2)) / 4ull) : 0u;
+    p.stack_cap = kernel == LAP_KERNEL_COMPACT
+                      ? (uint32_t)((p.slot_bytes - (p.paths ? 2ull : 1ull) * p.n_pad - (8ull << p.tbl_log2)) / 4ull)
+                      : 0u;
     LAP_CUDA(g, cudaMemsetAsync(&g->d_acc->claim, 0, sizeof(unsigned int), g->stream));
     const cudaError_t e = kernel == LAP_KERNEL_WIDE ? lap_launch_sample(p, g->stream) : lap_launch_sample_compact(p, g->stream);
     if (e != cudaSuccess) {
@@ -359,6 +363,7 @@ lap_status lap_set_option(lap_graph *g, int32_t option, int64_t value)
     case LAP_OPT_PATHS:
         if (value > 1) return fail(g, LAP_ERR_INVALID_ARG, "paths must be 0 or 1");
         if (g->omega != 0) return fail(g, LAP_ERR_INVALID_ARG, "the walk mode can only be set before the first sample after lap_set_root");
+        if (g->paths_opt != (uint32_t)value) g->last_kernel = 0;     // the slot layout changes
         g->paths_opt = (uint32_t)value;
         return LAP_OK;
     default:

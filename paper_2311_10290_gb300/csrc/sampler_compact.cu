@@ -36,7 +36,7 @@ namespace {
 using namespace lap_compact;
 
 template <bool CV>
-__global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
+__global__ void __launch_bounds__(256, 2) lewalk_compact_kernel(LapSampleLaunch p)
 {
     const uint64_t slot = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (slot >= p.slots) return;
@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
     const int2 *__restrict__ rowinfo = p.g.rowinfo;
     const int32_t *__restrict__ col = p.g.col;
     uint8_t *__restrict__ st = reinterpret_cast<uint8_t *>(p.ws) + slot * p.slot_bytes;
-    uint32_t *__restrict__ stk = reinterpret_cast<uint32_t *>(st + p.n_pad);
+    uint8_t *__restrict__ pr = st + p.n_pad;     // path departure counts (loop-included paths)
+    uint32_t *__restrict__ stk = reinterpret_cast<uint32_t *>(st + (p.paths ? 2u : 1u) * p.n_pad);
     const uint32_t cap = p.stack_cap;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
     const uint64_t limit = p.step_limit;
@@ -148,6 +149,7 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
                 if (base != chunk) {
                     pq = *reinterpret_cast<const ulonglong2 *>(st + base);
                     chunk = base;
+                    if (p.paths) *reinterpret_cast<ulonglong2 *>(pr + base) = make_ulonglong2(0ull, 0ull);
                     continue;
                 }
                 uint32_t m = not_tree_mask(pq, ep) & (0xFFFFu << (s - base));
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
                 if (s < n) {
                     pq = *reinterpret_cast<const ulonglong2 *>(st + s);
                     chunk = s;
+                    if (p.paths) *reinterpret_cast<ulonglong2 *>(pr + s) = make_ulonglong2(0ull, 0ull);
                     continue;
                 }
             }
@@ -186,16 +189,22 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
             int32_t w;
             if (p.paths) {
                 // Loop-included path: departure j from h takes h's stack entry j.
-                const uint32_t j = tbl_get(tbl_of(stk, cap), tlog, (uint32_t)h, tag + 1u, tag);
+                const uint32_t pbyte = pr[h];
+                const uint32_t j = path_count(pbyte, 0u, tbl_of(stk, cap), tlog, (uint32_t)h, tag);
                 w = ld_col(col + row_off(pb) + (int64_t)lap::below(lap::philox_r64((uint32_t)h, j, i, 0u, key0, key1), row_deg(pb)), keep);
-                if (!tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, j + 1u, tag + 1u, tag)) {
+                const uint32_t jn = j + 1u;
+                const uint32_t cn = jn < kPathSat ? jn : kPathSat;
+                if (jn >= kPathSat && !tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 1u, tag)) {
                     withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1, tbl_of(stk, cap), tlog, tag);
-                    withdraw_paths(tbl_of(stk, cap), tlog, tag, n, p.cnt2, rowinfo, col, CV ? p.cv_h2 : nullptr, p.cv_a2, p.cv_p2, i, key0, key1);
+                    withdraw_paths(pr, n, tbl_of(stk, cap), tlog, tag, p.cnt2, rowinfo, col, CV ? p.cv_h2 : nullptr, p.cv_a2, p.cv_p2, i, key0, key1);
                     const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
                     if (ix < p.count) p.ovf_ids[ix] = i;
                     phase = P_CLAIM;
                     continue;
                 }
+                // Written after the table accepted a count of 15 or more, so that a
+                // withdrawn path finds its departures so far.
+                pr[h] = (uint8_t)((pbyte & (0xF0u >> (4u * 0u))) | (cn << (4u * 0u)));
                 atomicAdd(&p.cnt2[h], 1ull);
             } else {
                 const uint64_t r = lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1);
@@ -222,16 +231,22 @@ __global__ void __launch_bounds__(256) lewalk_compact_kernel(LapSampleLaunch p)
             ++y2;
             int32_t w;
             if (p.paths) {
-                const uint32_t j = tbl_get(tbl_of(stk, cap), tlog, (uint32_t)h, tag + 2u, tag);
+                const uint32_t pbyte = pr[h];
+                const uint32_t j = path_count(pbyte, 1u, tbl_of(stk, cap), tlog, (uint32_t)h, tag);
                 w = ld_col(col + row_off(pb) + (int64_t)lap::below(lap::philox_r64((uint32_t)h, j, i, 0u, key0, key1), row_deg(pb)), keep);
-                if (!tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, j + 1u, tag + 2u, tag)) {
+                const uint32_t jn = j + 1u;
+                const uint32_t cn = jn < kPathSat ? jn : kPathSat;
+                if (jn >= kPathSat && !tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 2u, tag)) {
                     withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1, tbl_of(stk, cap), tlog, tag);
-                    withdraw_paths(tbl_of(stk, cap), tlog, tag, n, p.cnt2, rowinfo, col, CV ? p.cv_h2 : nullptr, p.cv_a2, p.cv_p2, i, key0, key1);
+                    withdraw_paths(pr, n, tbl_of(stk, cap), tlog, tag, p.cnt2, rowinfo, col, CV ? p.cv_h2 : nullptr, p.cv_a2, p.cv_p2, i, key0, key1);
                     const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
                     if (ix < p.count) p.ovf_ids[ix] = i;
                     phase = P_CLAIM;
                     continue;
                 }
+                // Written after the table accepted a count of 15 or more, so that a
+                // withdrawn path finds its departures so far.
+                pr[h] = (uint8_t)((pbyte & (0xF0u >> (4u * 1u))) | (cn << (4u * 1u)));
             } else {
                 const uint64_t r = lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1);
                 w = ld_col(col + row_off(pb) + (int64_t)lap::below(r, row_deg(pb)), keep);
