@@ -8,14 +8,14 @@
 // Draw counts k <= 30 live in the byte.  From the 31st draw at a node on, the
 // byte holds kKSat and the count lives in a per-lane open-addressing table
 // after the path stack: 2^tbl_log2 entries {node + 1 : 32 | tag : 8 | k : 24}.
-// Each sample of a lane owns three consecutive tags (base, base+1, base+2):
-// base keys the Wilson draw counts; base+1 and base+2 key the departure
-// counts of the loop-included paths (uniform and pi start) when the absorbed
-// walks are taken on the sample's own stacks.  Entries with other tags read
-// as empty, so the table is cleared only when the tags wrap (and at the
-// lane's first sample).  A sample that needs more entries than a probe run of
-// kTblProbes finds, more than kKMax draws at a node, or a longer path than the
-// stack holds is withdrawn.
+// Each sample of a lane owns one tag (base), or three consecutive tags (base,
+// base+1, base+2) when the absorbed walks are taken on the sample's own
+// stacks: base keys the Wilson draw counts; base+1 and base+2 key the
+// departure counts of the loop-included paths (uniform and pi start).
+// Entries with other tags read as empty, so the table is cleared only when
+// the tags wrap (and at the lane's first sample).  A sample that needs more
+// entries than a probe run of kTblProbes finds, more than kKMax draws at a
+// node, or a longer path than the stack holds is withdrawn.
 #pragma once
 
 #include "lap_internal.h"
@@ -181,13 +181,17 @@ static __device__ __forceinline__ uint32_t tbl_home(uint32_t node, uint32_t log2
     return (node * 2654435761u) >> (32u - log2);
 }
 
-// An entry belongs to the current sample when its tag is base .. base + 2.
+// NT = tags a sample owns: 1 when only the Wilson draw counts use the table,
+// 3 with the loop-included paths.  An entry belongs to the current sample
+// when its tag is base .. base + NT - 1.
+template <uint32_t NT>
 static __device__ __forceinline__ bool tbl_live(unsigned long long e, uint32_t base)
 {
-    return (((uint32_t)e >> 24) - base) <= 2u;
+    return (((uint32_t)e >> 24) - base) < NT;
 }
 
 // Count of (node, tag); 0 if absent.
+template <uint32_t NT>
 static __device__ __forceinline__ uint32_t tbl_get(const unsigned long long *tbl, uint32_t log2, uint32_t node,
                                                    uint32_t tag, uint32_t base)
 {
@@ -195,13 +199,14 @@ static __device__ __forceinline__ uint32_t tbl_get(const unsigned long long *tbl
     uint32_t s = tbl_home(node, log2);
     for (uint32_t q = 0; q < kTblProbes; ++q, s = (s + 1u) & mask) {
         const unsigned long long e = tbl[s];
-        if (!tbl_live(e, base)) break;
+        if (!tbl_live<NT>(e, base)) break;
         if ((uint32_t)(e >> 32) == node + 1u && ((uint32_t)e >> 24) == tag) return (uint32_t)e & 0xFFFFFFu;
     }
     return 0u;
 }
 
 // Sets the count of (node, tag), inserting it; false when its probe run is full.
+template <uint32_t NT>
 static __device__ __forceinline__ bool tbl_put(unsigned long long *tbl, uint32_t log2, uint32_t node, uint32_t k,
                                                uint32_t tag, uint32_t base)
 {
@@ -209,7 +214,7 @@ static __device__ __forceinline__ bool tbl_put(unsigned long long *tbl, uint32_t
     uint32_t s = tbl_home(node, log2);
     for (uint32_t q = 0; q < kTblProbes; ++q, s = (s + 1u) & mask) {
         const unsigned long long e = tbl[s];
-        if (!tbl_live(e, base) || ((uint32_t)(e >> 32) == node + 1u && ((uint32_t)e >> 24) == tag)) {
+        if (!tbl_live<NT>(e, base) || ((uint32_t)(e >> 32) == node + 1u && ((uint32_t)e >> 24) == tag)) {
             tbl[s] = ((unsigned long long)(node + 1u) << 32) | ((unsigned long long)tag << 24) | k;
             return true;
         }
@@ -223,14 +228,16 @@ static __device__ __forceinline__ void tbl_clear(unsigned long long *tbl, uint32
     for (uint32_t j = 0; j < (1u << log2) / 2u; ++j) t[j] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Next sample's base tag; clears the table when the tags wrap around.
+// Next sample's base tag; clears the table when the next sample's tags would
+// pass 255.
+template <uint32_t NT>
 static __device__ __forceinline__ uint32_t tbl_next_tag(unsigned long long *tbl, uint32_t log2, uint32_t base)
 {
-    if (base >= 250u) {
+    if (base > 256u - 2u * NT) {
         tbl_clear(tbl, log2);
         return 1u;
     }
-    return base + 3u;
+    return base + NT;
 }
 
 // Withdraws a partly run sample: subtracts the k - 1 repeat visits every
@@ -297,7 +304,7 @@ static __device__ __forceinline__ uint32_t path_count(uint32_t byte, uint32_t ni
                                                       uint32_t log2, uint32_t node, uint32_t base)
 {
     const uint32_t c = (byte >> (4u * nib)) & 0xFu;
-    return c < kPathSat ? c : tbl_get(tbl, log2, node, base + 1u + nib, base);
+    return c < kPathSat ? c : tbl_get<3>(tbl, log2, node, base + 1u + nib, base);
 }
 
 // Withdraws what the loop-included paths of a sample added before it was

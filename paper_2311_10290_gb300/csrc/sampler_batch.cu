@@ -49,7 +49,7 @@ __device__ void stamp(uint8_t *st, int32_t from, int32_t to, uint32_t ep)
 // PROBE: autotuner launches; each lane stops `window_ns` after it starts
 // (possibly inside a sample) and adds the walk steps it took to ctl->steps.
 // Counts and slot state are scratch afterwards.
-template <bool PROBE>
+template <bool PROBE, bool PATHS>
 __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
 {
     if (threadIdx.x == 0) atomicMin(&p.ctl->t0, global_ns());
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
     if (slot >= p.lanes) return;
     uint8_t *__restrict__ st = reinterpret_cast<uint8_t *>(p.ws) + slot * p.slot_bytes;
     uint8_t *__restrict__ pr = st + p.n_pad;     // path departure counts (loop-included paths)
-    uint32_t *__restrict__ stk = reinterpret_cast<uint32_t *>(st + (p.paths ? 2u : 1u) * p.n_pad);
+    uint32_t *__restrict__ stk = reinterpret_cast<uint32_t *>(st + (PATHS ? 2u : 1u) * p.n_pad);
     const uint32_t cap = p.stack_cap;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
     const uint64_t keep = policy_evict_last();
@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
     uint32_t iter = 0;
     unsigned int bad = 0;
     const uint32_t tlog = p.tbl_log2;
+    constexpr uint32_t kNT = PATHS ? 3u : 1u;   // count-table tags per sample
     uint32_t tag = 255u;      // count-table tag of the current sample (the first claim clears the table)
 
     for (;;) {
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
                 if (b_path(b, ep)) sp = erase_loop(st, stk, sp, ep, (uint32_t)h, pq, chunk);
                 uint32_t kh = b_k(b, ep);
                 if (kh == kKSat) {
-                    kh = tbl_get(tbl_of(stk, cap), tlog, (uint32_t)h, tag, tag);
+                    kh = tbl_get<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, tag, tag);
                     if (kh < kKSat) { bad |= LAP_DEV_BAD_INDEX; phase = P_CLAIM; continue; }
                 }
                 if (kh) w = ld_col(col + off + (int64_t)lap::below(lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1), deg), keep);
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
                 bool fits = kn <= kKMax && sp < cap;
                 if (fits && kn >= kKSat) {
                     kb = kKSat;
-                    fits = tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, kn, tag, tag);
+                    fits = tbl_put<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, kn, tag, tag);
                 }
                 if (!fits) {
                     withdraw_sample(st, n, ep, rep1, rowinfo, col, nullptr, nullptr, i, key0, key1, tbl_of(stk, cap), tlog, tag);
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
                 if (base != chunk) {
                     pq = *reinterpret_cast<const ulonglong2 *>(st + base);
                     chunk = base;
-                    if (p.paths) *reinterpret_cast<ulonglong2 *>(pr + base) = make_ulonglong2(0ull, 0ull);
+                    if (PATHS) *reinterpret_cast<ulonglong2 *>(pr + base) = make_ulonglong2(0ull, 0ull);
                     continue;
                 }
                 uint32_t m = not_tree_mask(pq, ep) & (0xFFFFu << (s - base));
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
                 if (s < n) {
                     pq = *reinterpret_cast<const ulonglong2 *>(st + s);
                     chunk = s;
-                    if (p.paths) *reinterpret_cast<ulonglong2 *>(pr + s) = make_ulonglong2(0ull, 0ull);
+                    if (PATHS) *reinterpret_cast<ulonglong2 *>(pr + s) = make_ulonglong2(0ull, 0ull);
                     continue;
                 }
             }
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
             t = 0;
             h = (int32_t)lap::below(lap::philox_r64(0u, 0u, i, 1u, key0, key1), (uint64_t)n);
             if (h != v) {
-                if (!p.paths) atomicAdd(&cnt2[h], 1ull);
+                if (!PATHS) atomicAdd(&cnt2[h], 1ull);
                 pb = ld_row(rowinfo, h, keep);
                 phase = P_UWALK;
                 continue;
@@ -192,14 +193,14 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
             ++t;
             if (PROBE) ++probe_steps;
             int32_t w;
-            if (p.paths) {
+            if (PATHS) {
                 // Loop-included path: departure j from h takes h's stack entry j.
                 const uint32_t pbyte = pr[h];
                 const uint32_t j = path_count(pbyte, 0u, tbl_of(stk, cap), tlog, (uint32_t)h, tag);
                 w = ld_col(col + row_off(pb) + (int64_t)lap::below(lap::philox_r64((uint32_t)h, j, i, 0u, key0, key1), row_deg(pb)), keep);
                 const uint32_t jn = j + 1u;
                 const uint32_t cn = jn < kPathSat ? jn : kPathSat;
-                if (jn >= kPathSat && !tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 1u, tag)) {
+                if (jn >= kPathSat && !tbl_put<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 1u, tag)) {
                     withdraw_sample(st, n, ep, rep1, rowinfo, col, nullptr, nullptr, i, key0, key1, tbl_of(stk, cap), tlog, tag);
                     withdraw_paths(pr, n, tbl_of(stk, cap), tlog, tag, cnt2, rowinfo, col, nullptr, nullptr, nullptr, i, key0, key1);
                     const unsigned int ix = atomicAdd(&p.ctl->ovf_count, 1u);
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
             h = w;
             if (t > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
             if (h != v) {
-                if (!p.paths) atomicAdd(&cnt2[h], 1ull);
+                if (!PATHS) atomicAdd(&cnt2[h], 1ull);
                 pb = ld_row(rowinfo, h, keep);
                 continue;
             }
@@ -235,13 +236,13 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
         if (phase == P_PIWALK) {
             ++y2;
             if (PROBE) ++probe_steps;
-            if (p.paths) {
+            if (PATHS) {
                 const uint32_t pbyte = pr[h];
                 const uint32_t j = path_count(pbyte, 1u, tbl_of(stk, cap), tlog, (uint32_t)h, tag);
                 const int32_t w = ld_col(col + row_off(pb) + (int64_t)lap::below(lap::philox_r64((uint32_t)h, j, i, 0u, key0, key1), row_deg(pb)), keep);
                 const uint32_t jn = j + 1u;
                 const uint32_t cn = jn < kPathSat ? jn : kPathSat;
-                if (jn >= kPathSat && !tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 2u, tag)) {
+                if (jn >= kPathSat && !tbl_put<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 2u, tag)) {
                     withdraw_sample(st, n, ep, rep1, rowinfo, col, nullptr, nullptr, i, key0, key1, tbl_of(stk, cap), tlog, tag);
                     withdraw_paths(pr, n, tbl_of(stk, cap), tlog, tag, cnt2, rowinfo, col, nullptr, nullptr, nullptr, i, key0, key1);
                     const unsigned int ix = atomicAdd(&p.ctl->ovf_count, 1u);
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
             // Bytes [0, n) must carry the current epoch before it flips.
             if (n > extent) stamp(st, extent, n, ep);
             extent = n;
-            tag = tbl_next_tag(tbl_of(stk, cap), tlog, tag);
+            tag = tbl_next_tag<kNT>(tbl_of(stk, cap), tlog, tag);
             ep ^= kBEpoch;
             st[v] = (uint8_t)(ep | kBTree);
             s = 0;
@@ -321,7 +322,7 @@ int lap_batch_block(const LapBatchLaunch &p) { return p.block > 0 ? p.block : la
 uint64_t lap_batch_resident_lanes(int block, int num_sms)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lewalk_batch_kernel<false>, block, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lewalk_batch_kernel<false, true>, block, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -333,7 +334,9 @@ cudaError_t lap_launch_batch(const LapBatchLaunch &p, bool probe, cudaStream_t s
     if (p.lanes == 0 || p.n_units == 0) return cudaSuccess;
     const int block = lap_batch_block(p);
     const uint64_t grid = (p.lanes + block - 1) / block;
-    if (probe) lewalk_batch_kernel<true><<<(unsigned)grid, block, 0, st>>>(p);
-    else lewalk_batch_kernel<false><<<(unsigned)grid, block, 0, st>>>(p);
+    if (probe && p.paths) lewalk_batch_kernel<true, true><<<(unsigned)grid, block, 0, st>>>(p);
+    else if (probe) lewalk_batch_kernel<true, false><<<(unsigned)grid, block, 0, st>>>(p);
+    else if (p.paths) lewalk_batch_kernel<false, true><<<(unsigned)grid, block, 0, st>>>(p);
+    else lewalk_batch_kernel<false, false><<<(unsigned)grid, block, 0, st>>>(p);
     return cudaGetLastError();
 }

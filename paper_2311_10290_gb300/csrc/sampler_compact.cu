@@ -35,8 +35,11 @@ namespace {
 
 using namespace lap_compact;
 
-template <bool CV>
-__global__ void __launch_bounds__(256, 2) lewalk_compact_kernel(LapSampleLaunch p)
+// CV: control-variate sums; PATHS: the absorbed walks are loop-included
+// paths (LapSampleLaunch::paths).  Separate instantiations keep the plain
+// kernel free of the other modes' code.
+template <bool CV, bool PATHS>
+__global__ void __launch_bounds__(256, CV ? 2 : 4) lewalk_compact_kernel(LapSampleLaunch p)
 {
     const uint64_t slot = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (slot >= p.slots) return;
@@ -46,7 +49,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_compact_kernel(LapSampleLaunch 
     const int32_t *__restrict__ col = p.g.col;
     uint8_t *__restrict__ st = reinterpret_cast<uint8_t *>(p.ws) + slot * p.slot_bytes;
     uint8_t *__restrict__ pr = st + p.n_pad;     // path departure counts (loop-included paths)
-    uint32_t *__restrict__ stk = reinterpret_cast<uint32_t *>(st + (p.paths ? 2u : 1u) * p.n_pad);
+    uint32_t *__restrict__ stk = reinterpret_cast<uint32_t *>(st + (PATHS ? 2u : 1u) * p.n_pad);
     const uint32_t cap = p.stack_cap;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
     const uint64_t limit = p.step_limit;
@@ -71,6 +74,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_compact_kernel(LapSampleLaunch 
     unsigned long long acc1 = 0, acc2 = 0;
     unsigned int bad = 0;
     const uint32_t tlog = p.tbl_log2;
+    constexpr uint32_t kNT = PATHS ? 3u : 1u;   // count-table tags per sample
     uint32_t tag = 255u;      // count-table tag of the current sample (the first claim clears the table)
 
     for (;;) {
@@ -94,7 +98,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_compact_kernel(LapSampleLaunch 
                 if (b_path(b, ep)) sp = erase_loop(st, stk, sp, ep, (uint32_t)h, pq, chunk);
                 uint32_t kh = b_k(b, ep);
                 if (kh == kKSat) {
-                    kh = tbl_get(tbl_of(stk, cap), tlog, (uint32_t)h, tag, tag);
+                    kh = tbl_get<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, tag, tag);
                     if (kh < kKSat) { bad |= LAP_DEV_BAD_INDEX; phase = P_CLAIM; continue; }
                 }
                 if (kh) w = ld_col(col + off + (int64_t)lap::below(lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1), deg), keep);
@@ -103,7 +107,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_compact_kernel(LapSampleLaunch 
                 bool fits = kn <= kKMax && sp < cap;
                 if (fits && kn >= kKSat) {
                     kb = kKSat;
-                    fits = tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, kn, tag, tag);
+                    fits = tbl_put<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, kn, tag, tag);
                 }
                 if (!fits) {
                     withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1, tbl_of(stk, cap), tlog, tag);
@@ -149,7 +153,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_compact_kernel(LapSampleLaunch 
                 if (base != chunk) {
                     pq = *reinterpret_cast<const ulonglong2 *>(st + base);
                     chunk = base;
-                    if (p.paths) *reinterpret_cast<ulonglong2 *>(pr + base) = make_ulonglong2(0ull, 0ull);
+                    if (PATHS) *reinterpret_cast<ulonglong2 *>(pr + base) = make_ulonglong2(0ull, 0ull);
                     continue;
                 }
                 uint32_t m = not_tree_mask(pq, ep) & (0xFFFFu << (s - base));
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_compact_kernel(LapSampleLaunch 
                 if (s < n) {
                     pq = *reinterpret_cast<const ulonglong2 *>(st + s);
                     chunk = s;
-                    if (p.paths) *reinterpret_cast<ulonglong2 *>(pr + s) = make_ulonglong2(0ull, 0ull);
+                    if (PATHS) *reinterpret_cast<ulonglong2 *>(pr + s) = make_ulonglong2(0ull, 0ull);
                     continue;
                 }
             }
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_compact_kernel(LapSampleLaunch 
             t = 0;
             h = (int32_t)lap::below(lap::philox_r64(0u, 0u, i, 1u, key0, key1), (uint64_t)n);
             if (h != v) {
-                if (!p.paths) atomicAdd(&p.cnt2[h], 1ull);
+                if (!PATHS) atomicAdd(&p.cnt2[h], 1ull);
                 pb = ld_row(rowinfo, h, keep);
                 phase = P_UWALK;
                 continue;
@@ -187,14 +191,14 @@ __global__ void __launch_bounds__(256, 2) lewalk_compact_kernel(LapSampleLaunch 
         if (phase == P_UWALK) {
             ++t;
             int32_t w;
-            if (p.paths) {
+            if (PATHS) {
                 // Loop-included path: departure j from h takes h's stack entry j.
                 const uint32_t pbyte = pr[h];
                 const uint32_t j = path_count(pbyte, 0u, tbl_of(stk, cap), tlog, (uint32_t)h, tag);
                 w = ld_col(col + row_off(pb) + (int64_t)lap::below(lap::philox_r64((uint32_t)h, j, i, 0u, key0, key1), row_deg(pb)), keep);
                 const uint32_t jn = j + 1u;
                 const uint32_t cn = jn < kPathSat ? jn : kPathSat;
-                if (jn >= kPathSat && !tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 1u, tag)) {
+                if (jn >= kPathSat && !tbl_put<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 1u, tag)) {
                     withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1, tbl_of(stk, cap), tlog, tag);
                     withdraw_paths(pr, n, tbl_of(stk, cap), tlog, tag, p.cnt2, rowinfo, col, CV ? p.cv_h2 : nullptr, p.cv_a2, p.cv_p2, i, key0, key1);
                     const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_compact_kernel(LapSampleLaunch 
             h = w;
             if (t > limit) { bad |= LAP_DEV_STEP_LIMIT; phase = P_CLAIM; continue; }
             if (h != v) {
-                if (!p.paths) atomicAdd(&p.cnt2[h], 1ull);
+                if (!PATHS) atomicAdd(&p.cnt2[h], 1ull);
                 pb = ld_row(rowinfo, h, keep);
                 continue;
             }
@@ -230,13 +234,13 @@ __global__ void __launch_bounds__(256, 2) lewalk_compact_kernel(LapSampleLaunch 
         if (phase == P_PIWALK) {
             ++y2;
             int32_t w;
-            if (p.paths) {
+            if (PATHS) {
                 const uint32_t pbyte = pr[h];
                 const uint32_t j = path_count(pbyte, 1u, tbl_of(stk, cap), tlog, (uint32_t)h, tag);
                 w = ld_col(col + row_off(pb) + (int64_t)lap::below(lap::philox_r64((uint32_t)h, j, i, 0u, key0, key1), row_deg(pb)), keep);
                 const uint32_t jn = j + 1u;
                 const uint32_t cn = jn < kPathSat ? jn : kPathSat;
-                if (jn >= kPathSat && !tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 2u, tag)) {
+                if (jn >= kPathSat && !tbl_put<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 2u, tag)) {
                     withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1, tbl_of(stk, cap), tlog, tag);
                     withdraw_paths(pr, n, tbl_of(stk, cap), tlog, tag, p.cnt2, rowinfo, col, CV ? p.cv_h2 : nullptr, p.cv_a2, p.cv_p2, i, key0, key1);
                     const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
@@ -283,7 +287,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_compact_kernel(LapSampleLaunch 
             const unsigned int q = atomicAdd(&p.acc->claim, 1u);
             if (q >= p.count) break;
             i = p.first + q;
-            tag = tbl_next_tag(tbl_of(stk, cap), tlog, tag);
+            tag = tbl_next_tag<kNT>(tbl_of(stk, cap), tlog, tag);
             ep ^= kBEpoch;
             st[v] = (uint8_t)(ep | kBTree);
             s = 0;
@@ -306,7 +310,10 @@ cudaError_t lap_launch_sample_compact(const LapSampleLaunch &p, cudaStream_t st)
     if (p.count == 0 || p.slots == 0) return cudaSuccess;
     int block = p.block > 0 ? p.block : lap_pick_block(p.slots, p.num_sms);
     uint64_t grid = (p.slots + block - 1) / block;
-    if (p.cv_h1 || p.cv_h2) lewalk_compact_kernel<true><<<(unsigned)grid, block, 0, st>>>(p);
-    else lewalk_compact_kernel<false><<<(unsigned)grid, block, 0, st>>>(p);
+    const bool cv = p.cv_h1 || p.cv_h2;
+    if (cv && p.paths) lewalk_compact_kernel<true, true><<<(unsigned)grid, block, 0, st>>>(p);
+    else if (cv) lewalk_compact_kernel<true, false><<<(unsigned)grid, block, 0, st>>>(p);
+    else if (p.paths) lewalk_compact_kernel<false, true><<<(unsigned)grid, block, 0, st>>>(p);
+    else lewalk_compact_kernel<false, false><<<(unsigned)grid, block, 0, st>>>(p);
     return cudaGetLastError();
 }
