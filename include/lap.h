@@ -76,8 +76,10 @@ typedef enum {
                                   first sample after lap_set_root.  Lets several processes or GPUs
                                   draw disjoint sample-id ranges whose counts add up exactly. */
     LAP_OPT_KERNEL = 5,        /* 0 = automatic, 1 = 8-byte state per node, 2 = 1-byte state per node
-                                  (default when n < 2^27).  Kernel 2 keeps draw counts above 30 in a
-                                  256-entry table per sample.  A sample that does not fit kernel 2
+                                  (default when n < 2^27).  Kernel 2 keeps draw counts above 30 (and,
+                                  with LAP_OPT_PATHS = 1, path departure counts above 14) in a
+                                  table per sample of 8-byte entries, as many as the next power
+                                  of two >= n, 256 to 8192.  A sample that does not fit kernel 2
                                   (more such nodes than the table holds, or a loop-erased path
                                   longer than the stack) is withdrawn and re-run with kernel 1:
                                   results are identical either way. */
@@ -136,9 +138,10 @@ lap_status lap_set_option(lap_graph *g, int32_t option, int64_t value);
 
 /*
  * Device workspace for the per-sample Wilson state (8 bytes per node per
- * sample in flight with kernel 1; with kernel 2, n rounded up to 256, plus
- * 4 bytes per stack entry, plus 2048 bytes of draw-count table, rounded up to
- * 256).  lap_workspace_query returns the bytes the
+ * sample in flight with kernel 1; with kernel 2, n rounded up to 256 (twice
+ * that with LAP_OPT_PATHS = 1), plus 4 bytes per stack entry, plus the count
+ * table (8 bytes times the next power of two >= n, 2 KB to 64 KB), rounded up
+ * to 256).  lap_workspace_query returns the bytes the
  * current kernel needs to keep `slots` samples in flight.  lap_set_workspace lends the handle a caller-owned
  * device buffer (at least 8*n bytes, 256-byte aligned), which must stay alive
  * while the handle uses it; the handle zeroes it.  Without a workspace,

@@ -82,7 +82,9 @@ lap_status lap_batch_set_option(lap_batch *b, int32_t option, int64_t value);
 
 /* Device bytes of the Wilson-state workspace for `lanes` samples in flight
  * (one slot per lane: a state byte per node of the largest graph, rounded up
- * to 256, plus the path stack and a 2 KB table of draw counts above 30). */
+ * to 256 (twice that with LAP_BOPT_PATHS = 1), plus the path stack and a
+ * table of counts above 30: 8 bytes times the next power of two >= that n,
+ * 2 KB to 64 KB). */
 lap_status lap_batch_workspace_query(const lap_batch *b, uint64_t lanes, uint64_t *bytes);
 
 /* Lends the handle device memory for the workspace (256-byte aligned; the

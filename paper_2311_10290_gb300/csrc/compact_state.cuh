@@ -7,13 +7,12 @@
 //
 // Draw counts k <= 30 live in the byte.  From the 31st draw at a node on, the
 // byte holds kKSat and the count lives in a per-lane open-addressing table
-// after the path stack: 2^tbl_log2 entries {node + 1 : 32 | tag : 8 | k : 24}.
-// Each sample of a lane owns one tag (base), or three consecutive tags (base,
-// base+1, base+2) when the absorbed walks are taken on the sample's own
-// stacks: base keys the Wilson draw counts; base+1 and base+2 key the
-// departure counts of the loop-included paths (uniform and pi start).
-// Entries with other tags read as empty, so the table is cleared only when
-// the tags wrap (and at the lane's first sample).  A sample that needs more
+// after the path stack: 2^tbl_log2 entries {key : 32 | tag : 8 | k : 24}, the
+// key being the node and the kind of count (Wilson draws, or departures of
+// one of the loop-included paths when the absorbed walks are taken on the
+// sample's own stacks).  Each sample of a lane has its own tag (1..255), so
+// entries of earlier samples read as empty and the table is cleared only when
+// the tag wraps (and at the lane's first sample).  A sample that needs more
 // entries than a probe run of kTblProbes finds, more than kKMax draws at a
 // node, or a longer path than the stack holds is withdrawn.
 #pragma once
@@ -176,46 +175,43 @@ static __device__ __forceinline__ unsigned long long *tbl_of(uint32_t *stk, uint
     return reinterpret_cast<unsigned long long *>(stk + cap);
 }
 
-static __device__ __forceinline__ uint32_t tbl_home(uint32_t node, uint32_t log2)
+// Entry key: node + 1 in bits 0..27 (node < 2^27), the kind of count in bits
+// 28..29 (kTblDraws: Wilson draws; kTblUPath / kTblPiPath: departures of the
+// uniform-start / pi-start loop-included path).
+constexpr uint32_t kTblDraws = 0u, kTblUPath = 1u, kTblPiPath = 2u;
+static __device__ __forceinline__ uint32_t tbl_key(uint32_t node, uint32_t kind) { return (node + 1u) | (kind << 28); }
+
+static __device__ __forceinline__ uint32_t tbl_home(uint32_t key, uint32_t log2)
 {
-    return (node * 2654435761u) >> (32u - log2);
+    return (key * 2654435761u) >> (32u - log2);
 }
 
-// NT = tags a sample owns: 1 when only the Wilson draw counts use the table,
-// 3 with the loop-included paths.  An entry belongs to the current sample
-// when its tag is base .. base + NT - 1.
-template <uint32_t NT>
-static __device__ __forceinline__ bool tbl_live(unsigned long long e, uint32_t base)
-{
-    return (((uint32_t)e >> 24) - base) < NT;
-}
-
-// Count of (node, tag); 0 if absent.
-template <uint32_t NT>
+// Count of (node, kind) in the current sample (tag); 0 if absent.
 static __device__ __forceinline__ uint32_t tbl_get(const unsigned long long *tbl, uint32_t log2, uint32_t node,
-                                                   uint32_t tag, uint32_t base)
+                                                   uint32_t kind, uint32_t tag)
 {
     const uint32_t mask = (1u << log2) - 1u;
-    uint32_t s = tbl_home(node, log2);
+    const uint32_t key = tbl_key(node, kind);
+    uint32_t s = tbl_home(key, log2);
     for (uint32_t q = 0; q < kTblProbes; ++q, s = (s + 1u) & mask) {
         const unsigned long long e = tbl[s];
-        if (!tbl_live<NT>(e, base)) break;
-        if ((uint32_t)(e >> 32) == node + 1u && ((uint32_t)e >> 24) == tag) return (uint32_t)e & 0xFFFFFFu;
+        if (((uint32_t)e >> 24) != tag) break;                 // empty for this sample
+        if ((uint32_t)(e >> 32) == key) return (uint32_t)e & 0xFFFFFFu;
     }
     return 0u;
 }
 
-// Sets the count of (node, tag), inserting it; false when its probe run is full.
-template <uint32_t NT>
-static __device__ __forceinline__ bool tbl_put(unsigned long long *tbl, uint32_t log2, uint32_t node, uint32_t k,
-                                               uint32_t tag, uint32_t base)
+// Sets the count of (node, kind), inserting it; false when its probe run is full.
+static __device__ __forceinline__ bool tbl_put(unsigned long long *tbl, uint32_t log2, uint32_t node, uint32_t kind,
+                                               uint32_t k, uint32_t tag)
 {
     const uint32_t mask = (1u << log2) - 1u;
-    uint32_t s = tbl_home(node, log2);
+    const uint32_t key = tbl_key(node, kind);
+    uint32_t s = tbl_home(key, log2);
     for (uint32_t q = 0; q < kTblProbes; ++q, s = (s + 1u) & mask) {
         const unsigned long long e = tbl[s];
-        if (!tbl_live<NT>(e, base) || ((uint32_t)(e >> 32) == node + 1u && ((uint32_t)e >> 24) == tag)) {
-            tbl[s] = ((unsigned long long)(node + 1u) << 32) | ((unsigned long long)tag << 24) | k;
+        if (((uint32_t)e >> 24) != tag || (uint32_t)(e >> 32) == key) {
+            tbl[s] = ((unsigned long long)key << 32) | ((unsigned long long)tag << 24) | k;
             return true;
         }
     }
@@ -228,16 +224,14 @@ static __device__ __forceinline__ void tbl_clear(unsigned long long *tbl, uint32
     for (uint32_t j = 0; j < (1u << log2) / 2u; ++j) t[j] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Next sample's base tag; clears the table when the next sample's tags would
-// pass 255.
-template <uint32_t NT>
-static __device__ __forceinline__ uint32_t tbl_next_tag(unsigned long long *tbl, uint32_t log2, uint32_t base)
+// Next sample's tag; clears the table when the tags wrap around.
+static __device__ __forceinline__ uint32_t tbl_next_tag(unsigned long long *tbl, uint32_t log2, uint32_t tag)
 {
-    if (base > 256u - 2u * NT) {
+    if (tag >= 255u) {
         tbl_clear(tbl, log2);
         return 1u;
     }
-    return base + NT;
+    return tag + 1u;
 }
 
 // Withdraws a partly run sample: subtracts the k - 1 repeat visits every
@@ -250,7 +244,6 @@ static __device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsi
                                 uint32_t key0, uint32_t key1, const unsigned long long *tbl, uint32_t log2,
                                 uint32_t tag)
 {
-    // (tag is the sample's base tag: the Wilson draw counts.)
     for (int32_t base = 0; base < n; base += 16) {
         ulonglong2 q = *reinterpret_cast<ulonglong2 *>(st + base);
 #pragma unroll
@@ -276,7 +269,7 @@ static __device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsi
     // whose byte held kKSat).
     for (uint32_t j = 0; j < (1u << log2); ++j) {
         const unsigned long long e = tbl[j];
-        if (((uint32_t)e >> 24) != tag) continue;
+        if (((uint32_t)e >> 24) != tag || (uint32_t)(e >> 60) != kTblDraws) continue;
         const uint32_t node = (uint32_t)(e >> 32) - 1u, k = (uint32_t)e & 0xFFFFFFu;
         if ((int32_t)node >= n || k <= kKSat) continue;
         atomicAdd(&rep1[node], (unsigned long long)(-(long long)(k - kKSat)));
@@ -296,15 +289,15 @@ static __device__ void withdraw_sample(uint8_t *st, int32_t n, uint32_t ep, unsi
 // one more byte in a second region of the slot, reset chunk by chunk while
 // the Wilson scan passes over it: bits 0..3 count the departures of the
 // uniform-start path from the node, bits 4..7 those of the pi-start path; 15
-// means "15 or more, see the table" (tags base + 1 and base + 2).
+// means "15 or more, see the table" (kinds kTblUPath and kTblPiPath).
 constexpr uint32_t kPathSat = 15u;
 
 // Departure count of `nib` (0: uniform path, 1: pi path) of a node.
 static __device__ __forceinline__ uint32_t path_count(uint32_t byte, uint32_t nib, const unsigned long long *tbl,
-                                                      uint32_t log2, uint32_t node, uint32_t base)
+                                                      uint32_t log2, uint32_t node, uint32_t tag)
 {
     const uint32_t c = (byte >> (4u * nib)) & 0xFu;
-    return c < kPathSat ? c : tbl_get<3>(tbl, log2, node, base + 1u + nib, base);
+    return c < kPathSat ? c : tbl_get(tbl, log2, node, kTblUPath + nib, tag);
 }
 
 // Withdraws what the loop-included paths of a sample added before it was
@@ -312,7 +305,7 @@ static __device__ __forceinline__ uint32_t path_count(uint32_t byte, uint32_t ni
 // cnt2; every departure of the pi-start path added h2[w] to a2 and one to p2
 // (control variate).
 static __device__ void withdraw_paths(const uint8_t *pr, int32_t n, const unsigned long long *tbl, uint32_t log2,
-                                      uint32_t base, unsigned long long *cnt2, const int2 *rowinfo,
+                                      uint32_t tag, unsigned long long *cnt2, const int2 *rowinfo,
                                       const int32_t *col, const long long *h2, unsigned long long *a2,
                                       unsigned long long *p2, uint32_t i, uint32_t key0, uint32_t key1)
 {
@@ -324,8 +317,8 @@ static __device__ void withdraw_paths(const uint8_t *pr, int32_t n, const unsign
             if (u >= n) break;
             const uint32_t byte = (uint32_t)(((b < 8 ? q.x : q.y) >> (8 * (b & 7))) & 0xFFu);
             if (!byte) continue;
-            const uint32_t ju = path_count(byte, 0u, tbl, log2, (uint32_t)u, base);
-            const uint32_t jp = path_count(byte, 1u, tbl, log2, (uint32_t)u, base);
+            const uint32_t ju = path_count(byte, 0u, tbl, log2, (uint32_t)u, tag);
+            const uint32_t jp = path_count(byte, 1u, tbl, log2, (uint32_t)u, tag);
             if (ju) atomicAdd(&cnt2[u], (unsigned long long)(-(long long)ju));
             if (jp && h2) {
                 const int2 r = rowinfo[u];

@@ -91,7 +91,6 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
     uint32_t iter = 0;
     unsigned int bad = 0;
     const uint32_t tlog = p.tbl_log2;
-    constexpr uint32_t kNT = PATHS ? 3u : 1u;   // count-table tags per sample
     uint32_t tag = 255u;      // count-table tag of the current sample (the first claim clears the table)
 
     for (;;) {
@@ -105,7 +104,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
                 if (b_path(b, ep)) sp = erase_loop(st, stk, sp, ep, (uint32_t)h, pq, chunk);
                 uint32_t kh = b_k(b, ep);
                 if (kh == kKSat) {
-                    kh = tbl_get<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, tag, tag);
+                    kh = tbl_get(tbl_of(stk, cap), tlog, (uint32_t)h, kTblDraws, tag);
                     if (kh < kKSat) { bad |= LAP_DEV_BAD_INDEX; phase = P_CLAIM; continue; }
                 }
                 if (kh) w = ld_col(col + off + (int64_t)lap::below(lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1), deg), keep);
@@ -114,7 +113,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
                 bool fits = kn <= kKMax && sp < cap;
                 if (fits && kn >= kKSat) {
                     kb = kKSat;
-                    fits = tbl_put<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, kn, tag, tag);
+                    fits = tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, kTblDraws, kn, tag);
                 }
                 if (!fits) {
                     withdraw_sample(st, n, ep, rep1, rowinfo, col, nullptr, nullptr, i, key0, key1, tbl_of(stk, cap), tlog, tag);
@@ -200,7 +199,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
                 w = ld_col(col + row_off(pb) + (int64_t)lap::below(lap::philox_r64((uint32_t)h, j, i, 0u, key0, key1), row_deg(pb)), keep);
                 const uint32_t jn = j + 1u;
                 const uint32_t cn = jn < kPathSat ? jn : kPathSat;
-                if (jn >= kPathSat && !tbl_put<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 1u, tag)) {
+                if (jn >= kPathSat && !tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, kTblUPath, jn, tag)) {
                     withdraw_sample(st, n, ep, rep1, rowinfo, col, nullptr, nullptr, i, key0, key1, tbl_of(stk, cap), tlog, tag);
                     withdraw_paths(pr, n, tbl_of(stk, cap), tlog, tag, cnt2, rowinfo, col, nullptr, nullptr, nullptr, i, key0, key1);
                     const unsigned int ix = atomicAdd(&p.ctl->ovf_count, 1u);
@@ -242,7 +241,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
                 const int32_t w = ld_col(col + row_off(pb) + (int64_t)lap::below(lap::philox_r64((uint32_t)h, j, i, 0u, key0, key1), row_deg(pb)), keep);
                 const uint32_t jn = j + 1u;
                 const uint32_t cn = jn < kPathSat ? jn : kPathSat;
-                if (jn >= kPathSat && !tbl_put<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 2u, tag)) {
+                if (jn >= kPathSat && !tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, kTblPiPath, jn, tag)) {
                     withdraw_sample(st, n, ep, rep1, rowinfo, col, nullptr, nullptr, i, key0, key1, tbl_of(stk, cap), tlog, tag);
                     withdraw_paths(pr, n, tbl_of(stk, cap), tlog, tag, cnt2, rowinfo, col, nullptr, nullptr, nullptr, i, key0, key1);
                     const unsigned int ix = atomicAdd(&p.ctl->ovf_count, 1u);
@@ -297,7 +296,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
             // Bytes [0, n) must carry the current epoch before it flips.
             if (n > extent) stamp(st, extent, n, ep);
             extent = n;
-            tag = tbl_next_tag<kNT>(tbl_of(stk, cap), tlog, tag);
+            tag = tbl_next_tag(tbl_of(stk, cap), tlog, tag);
             ep ^= kBEpoch;
             st[v] = (uint8_t)(ep | kBTree);
             s = 0;

@@ -74,7 +74,6 @@ __global__ void __launch_bounds__(256, CV ? 2 : 4) lewalk_compact_kernel(LapSamp
     unsigned long long acc1 = 0, acc2 = 0;
     unsigned int bad = 0;
     const uint32_t tlog = p.tbl_log2;
-    constexpr uint32_t kNT = PATHS ? 3u : 1u;   // count-table tags per sample
     uint32_t tag = 255u;      // count-table tag of the current sample (the first claim clears the table)
 
     for (;;) {
@@ -98,7 +97,7 @@ __global__ void __launch_bounds__(256, CV ? 2 : 4) lewalk_compact_kernel(LapSamp
                 if (b_path(b, ep)) sp = erase_loop(st, stk, sp, ep, (uint32_t)h, pq, chunk);
                 uint32_t kh = b_k(b, ep);
                 if (kh == kKSat) {
-                    kh = tbl_get<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, tag, tag);
+                    kh = tbl_get(tbl_of(stk, cap), tlog, (uint32_t)h, kTblDraws, tag);
                     if (kh < kKSat) { bad |= LAP_DEV_BAD_INDEX; phase = P_CLAIM; continue; }
                 }
                 if (kh) w = ld_col(col + off + (int64_t)lap::below(lap::philox_r64((uint32_t)h, kh, i, 0u, key0, key1), deg), keep);
@@ -107,7 +106,7 @@ __global__ void __launch_bounds__(256, CV ? 2 : 4) lewalk_compact_kernel(LapSamp
                 bool fits = kn <= kKMax && sp < cap;
                 if (fits && kn >= kKSat) {
                     kb = kKSat;
-                    fits = tbl_put<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, kn, tag, tag);
+                    fits = tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, kTblDraws, kn, tag);
                 }
                 if (!fits) {
                     withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1, tbl_of(stk, cap), tlog, tag);
@@ -198,7 +197,7 @@ __global__ void __launch_bounds__(256, CV ? 2 : 4) lewalk_compact_kernel(LapSamp
                 w = ld_col(col + row_off(pb) + (int64_t)lap::below(lap::philox_r64((uint32_t)h, j, i, 0u, key0, key1), row_deg(pb)), keep);
                 const uint32_t jn = j + 1u;
                 const uint32_t cn = jn < kPathSat ? jn : kPathSat;
-                if (jn >= kPathSat && !tbl_put<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 1u, tag)) {
+                if (jn >= kPathSat && !tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, kTblUPath, jn, tag)) {
                     withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1, tbl_of(stk, cap), tlog, tag);
                     withdraw_paths(pr, n, tbl_of(stk, cap), tlog, tag, p.cnt2, rowinfo, col, CV ? p.cv_h2 : nullptr, p.cv_a2, p.cv_p2, i, key0, key1);
                     const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
@@ -240,7 +239,7 @@ __global__ void __launch_bounds__(256, CV ? 2 : 4) lewalk_compact_kernel(LapSamp
                 w = ld_col(col + row_off(pb) + (int64_t)lap::below(lap::philox_r64((uint32_t)h, j, i, 0u, key0, key1), row_deg(pb)), keep);
                 const uint32_t jn = j + 1u;
                 const uint32_t cn = jn < kPathSat ? jn : kPathSat;
-                if (jn >= kPathSat && !tbl_put<kNT>(tbl_of(stk, cap), tlog, (uint32_t)h, jn, tag + 2u, tag)) {
+                if (jn >= kPathSat && !tbl_put(tbl_of(stk, cap), tlog, (uint32_t)h, kTblPiPath, jn, tag)) {
                     withdraw_sample(st, n, ep, p.rep1, rowinfo, col, CV ? p.cv_h1 : nullptr, p.cv_a1, i, key0, key1, tbl_of(stk, cap), tlog, tag);
                     withdraw_paths(pr, n, tbl_of(stk, cap), tlog, tag, p.cnt2, rowinfo, col, CV ? p.cv_h2 : nullptr, p.cv_a2, p.cv_p2, i, key0, key1);
                     const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
@@ -287,7 +286,7 @@ __global__ void __launch_bounds__(256, CV ? 2 : 4) lewalk_compact_kernel(LapSamp
             const unsigned int q = atomicAdd(&p.acc->claim, 1u);
             if (q >= p.count) break;
             i = p.first + q;
-            tag = tbl_next_tag<kNT>(tbl_of(stk, cap), tlog, tag);
+            tag = tbl_next_tag(tbl_of(stk, cap), tlog, tag);
             ep ^= kBEpoch;
             st[v] = (uint8_t)(ep | kBTree);
             s = 0;

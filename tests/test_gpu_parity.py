@@ -132,6 +132,22 @@ def test_loop_included_paths_match_oracle(name, maker, root, omega, kernel):
         assert r["fallbacks"] == 0 or name == "path40_end"
 
 
+@pytest.mark.parametrize("paths", [False, True], ids=["own_draws", "stack_paths"])
+@pytest.mark.parametrize("slots", [1, 3])
+def test_count_table_tags_wrap_within_a_lane(slots, paths):
+    """A 50-node star rooted at a leaf: the hub draws ~49 times per sample, so
+    every sample keeps counts in the lane's table.  With 1 or 3 lanes each lane
+    runs hundreds of samples, so the per-sample tags (one per sample, three
+    with the paths) wrap and the table is cleared several times; the counts
+    stay the oracle's and nothing falls back."""
+    g = I.star(50)
+    omega = 700
+    r = gpu_run(g, 77, omega, root=7, slots=slots, kernel=2, paths=paths)
+    c = oracle_run(g, 7, 77, omega, threads=4, paths=paths)
+    assert_parity(g, r, c, omega)
+    assert r["fallbacks"] == 0
+
+
 def test_loop_included_paths_overflow_falls_back_exactly():
     """A 256-node path rooted at an end: the paths' departure counts and the
     saturated Wilson counts together overflow the 256-entry table, so samples
