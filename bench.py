@@ -106,6 +106,8 @@ def parse():
     ap.add_argument("--extra-workloads", default="rmat_22",
                     help="comma-separated extra single-graph workloads (plain throughput, CV vs plain)")
     ap.add_argument("--extra-samples", type=int, default=16384, help="samples per step of the extra workloads")
+    ap.add_argument("--ceiling-probe", type=int, default=1,
+                    help="measure the random 1-byte read+write ceiling the sampler is compared with (0: skip)")
     ap.add_argument("--extra-cv", type=int, default=0,
                     help="also measure the control variate against plain on the extra workloads (1: on)")
     return ap.parse_args()
@@ -640,6 +642,40 @@ def kemeny_sweep(torch, args):
             "generate_seconds": round(t_gen, 1), "rows": rows}
 
 
+# ------------------------------------------------------------ random-access ceiling
+
+def random_access_ceiling(torch, args):
+    """Ceiling of the Wilson step's memory pattern on this device: random
+    single-byte read-then-write pairs over a buffer far above L2
+    (lap_probe_random_rw, independent pairs, no dependent chain) at three
+    launch sizes; the best rate is what the sampler's walk steps/s are
+    compared with."""
+    from paper_2311_10290_gb300.lap import lap_probe_random_rw
+    free, _ = torch.cuda.mem_get_info()
+    nbytes = min(64 << 30, int(free * 0.5)) // 256 * 256
+    buf = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    rows, rounds = [], 64
+    for k in (8, 16, 32):
+        blocks = sms * k
+        lap_probe_random_rw(buf, blocks, 4, salt=1, stream=stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        lap_probe_random_rw(buf, blocks, rounds, salt=100 + k, stream=stream)
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        rows.append({"blocks": blocks, "threads_per_block": 256, "pairs": blocks * 256 * rounds * 4,
+                     "ms": round(t * 1e3, 3), "pairs_per_s": blocks * 256 * rounds * 4 / t})
+    del buf
+    torch.cuda.empty_cache()
+    best = max(rows, key=lambda r: r["pairs_per_s"])
+    return {"buffer_gb": round(nbytes / 1e9, 1), "pairs_per_s": best["pairs_per_s"], "rows": rows,
+            "note": "random 1-byte read + write pairs, 4 independent per thread and round, SplitMix64 addresses"}
+
+
 # ------------------------------------------------------------ extra workloads
 
 def extra_workload(torch, LapGraph, name, args, params):
@@ -901,6 +937,12 @@ def run_ours(args, rank, world):
     G.close()
     del flush, out
     torch.cuda.empty_cache()
+    if rank == 0 and args.ceiling_probe:
+        note("random-access ceiling probe")
+        c = random_access_ceiling(torch, args)
+        c["sampler_walk_steps_per_s"] = walk_steps / (kernel_s * args.steps)
+        c["sampler_frac_of_ceiling"] = c["sampler_walk_steps_per_s"] / c["pairs_per_s"]
+        res["random_access_ceiling"] = c
     # End to end through the C ABI with host buffers: each step copies the CSR
     # from pinned host memory (graph create), samples, finalizes and reads the
     # ECC vector and Kemeny's constant back to the host.
