@@ -1022,7 +1022,15 @@ def run_e2e(args, g, torch, LapGraph, rank, world):
         times.append(t1 - t0)
         steps_total += int(s[1]) + int(c2.sum()) + int(s[2])
     t = float(np.sum(times))
-    return {"value": steps_total * world / t, "unit": "walk steps/s",
+    if world > 1:
+        # Whole job: walk steps of all ranks over the slowest rank's time.
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        st = torch.tensor([steps_total], dtype=torch.int64, device="cuda")
+        dist.all_reduce(st)
+        t, steps_total = float(tt.item()), int(st.item())
+    return {"value": steps_total / t, "unit": "walk steps/s",
             "h2d_bytes_per_step": int(rp.numel() * 4 + cl.numel() * 4),
             "d2h_bytes_per_step": int(g.n * 8 + 8),
             "ms_per_step": 1e3 * t / len(times),
