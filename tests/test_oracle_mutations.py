@@ -1,10 +1,11 @@
 """The oracle's pins catch plausible mistakes: each case plants one mistake
 (a dropped term or factor, a wrong sign or index, a wrong Philox key word, a
-start drawn from the wrong law, a visit not counted, the SpanTree subtree
-test the other way round) in a copy of the oracle outside the repository and
-runs the pins of that part (tests/test_oracle_pins.py for the LEWalk sampler
-and finalize, tests/test_oracle_spantree_pins.py for Alg. 1 / Alg. 3) against
-the copy; at least one pin must fail.  The repository's oracle is not
+start drawn from the wrong law, a visit not counted, an eigenvalue dropped
+from the dense truth, the SpanTree subtree test the other way round) in a
+copy of the oracle outside the repository and runs the pins of that part
+(tests/test_oracle_pins.py for the LEWalk sampler, finalize and dense truth,
+tests/test_oracle_spantree_pins.py for Alg. 1 / Alg. 3) against the copy; at
+least one pin must fail.  The repository's oracle is not
 touched."""
 import os
 import shutil
@@ -53,6 +54,21 @@ MUTATIONS = [
     ("y2_not_divided_by_degree", "lewalk_oracle.c",
      "y2[u] = (double)cnt2[u] / (w * d);",
      "y2[u] = (double)cnt2[u] / w;", C_PINS),
+    ("path_departure_not_advanced", "lewalk_oracle.c",
+     "                draws[u] += 1;\n                u = oracle_neighbor(row_ptr, col, u, x);",
+     "                draws[u] += (u & 1);\n                u = oracle_neighbor(row_ptr, col, u, x);", C_PINS),
+    ("pinv_drops_an_eigenvalue", "dense.py",
+     "    inv[1:] = 1.0 / lam[1:]",
+     "    inv[2:] = 1.0 / lam[2:]", C_PINS),
+    ("ecc_trace_dropped", "dense.py",
+     "    return (n - 1) / (n * dg + dg.sum())",
+     "    return (n - 1) / (n * dg)", C_PINS),
+    ("kemeny_drops_an_eigenvalue", "dense.py",
+     "    return float(np.sum(1.0 / sig[1:]))",
+     "    return float(np.sum(1.0 / sig[2:]))", C_PINS),
+    ("rwb_missing_factor_n", "dense.py",
+     "    return tr, 1.0 / n + tr / ((n - 1) * (tr + n * ld))",
+     "    return tr, 1.0 / n + tr / ((n - 1) * (tr + ld))", C_PINS),
     ("subtree_test_printed_direction", "spantree.py",
      "                if inside(u, e1):",
      "                if inside(e1, u):", ST_PINS),
@@ -93,7 +109,7 @@ def run_pins_on_copy(tmp_path, fname, src, pins):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("fname,pins", [("lewalk_oracle.c", C_PINS), ("spantree.py", ST_PINS)])
+@pytest.mark.parametrize("fname,pins", [("lewalk_oracle.c", C_PINS), ("dense.py", C_PINS), ("spantree.py", ST_PINS)])
 def test_unchanged_copy_passes_the_pins(fname, pins, tmp_path):
     src = open(os.path.join(ROOT, "oracle", fname)).read()
     code, out = run_pins_on_copy(tmp_path, fname, src, pins)
