@@ -142,3 +142,32 @@ def test_hitting_time_potential_cancels_the_pi_walk_variance():
     var_start = float(pi @ hit ** 2 - (pi @ hit) ** 2)
     assert np.var(resid) < 0.1 * np.var(y2)
     assert np.var(resid) == pytest.approx(var_start, rel=0.2)
+
+
+def test_cv_kemeny_estimate_with_the_hitting_time_potential():
+    """finalize_cv's Kemeny estimate (ΣY1 − ΣY2 + β2 M2)/ω with h2 = the
+    hitting time h(., v) and β2 = 2^-16 (one unit of the fixed-point
+    potential): every π walk's own randomness cancels, leaving its start's
+    hitting time, and E[M2] = 0 keeps the estimate unbiased.  Across 300
+    batches of 10 samples the estimates stay within 6 standard errors of the
+    dense κ and vary less than 0.8 times as much as the plain estimates of the
+    same samples (about 0.5 on this graph; the opposite sign of the term
+    doubles the walk's randomness instead: about 2.5)."""
+    g = I.er(200, 0.03, seed=3)
+    v = oracle.root_max_degree(g.row_ptr)
+    hit = D.hitting_times_to(g.n, g.row_ptr, g.col, v)
+    h2 = CV.quantize_potential(hit)
+    z1 = np.zeros(g.n, dtype=np.int64)
+    beta2 = 2.0 ** -CV.FIXED_POINT_BITS
+    kc_t = D.kemeny(g.n, g.row_ptr, g.col)
+    plain, cv = [], []
+    for b in range(300):
+        cnt, a1, a2, p2, m2 = oracle.sample_cv(g.row_ptr, g.col, v, 5, 10 * b, 10, h2=h2)
+        m2_total = CV.martingale_m2(g.row_ptr, g.col, h2, a2, p2)
+        plain.append(oracle.finalize(g.row_ptr, v, 10, cnt.cnt1, cnt.cnt2, cnt.sum_y1, cnt.sum_y2)[2])
+        cv.append(CV.finalize_cv(g.row_ptr, v, 10, cnt.cnt1, cnt.cnt2, cnt.sum_y1, cnt.sum_y2, z1, m2_total,
+                                 0.0, beta2)[2])
+    plain, cv = np.array(plain), np.array(cv)
+    assert np.var(cv) < 0.8 * np.var(plain), (np.var(cv), np.var(plain))
+    assert abs(cv.mean() - kc_t) < 6 * cv.std(ddof=1) / np.sqrt(len(cv))
+    assert abs(plain.mean() - kc_t) < 6 * plain.std(ddof=1) / np.sqrt(len(plain))

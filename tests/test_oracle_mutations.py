@@ -4,6 +4,7 @@ start drawn from the wrong law, a visit not counted, an eigenvalue dropped
 from the dense truth, the SpanTree subtree test the other way round) in a
 copy of the oracle outside the repository and runs the pins of that part
 (tests/test_oracle_pins.py for the LEWalk sampler, finalize and dense truth,
+tests/test_oracle_cv_pins.py for the control variate, and
 tests/test_oracle_spantree_pins.py for Alg. 1 / Alg. 3) against the copy; at
 least one pin must fail.  The repository's oracle is not
 touched."""
@@ -18,6 +19,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 C_PINS = "test_oracle_pins.py"
 ST_PINS = "test_oracle_spantree_pins.py"
+CV_PINS = "test_oracle_cv_pins.py"
 
 # (name, file under oracle/, anchor, planted mistake, pins that must catch it)
 MUTATIONS = [
@@ -69,6 +71,21 @@ MUTATIONS = [
     ("rwb_missing_factor_n", "dense.py",
      "    return tr, 1.0 / n + tr / ((n - 1) * (tr + n * ld))",
      "    return tr, 1.0 / n + tr / ((n - 1) * (tr + ld))", C_PINS),
+    ("bf16_ties_away_from_even", "cv.py",
+     "    rounded = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16",
+     "    rounded = ((b + 0x8000) >> 16) << 16", CV_PINS),
+    ("relu_derivative_dropped", "cv.py",
+     "    dh2 = (dy @ W3) * (z2 > 0)",
+     "    dh2 = (dy @ W3)", CV_PINS),
+    ("adamw_second_moment_not_corrected", "cv.py",
+     "    vh = v / (1.0 - beta2 ** step)",
+     "    vh = v", CV_PINS),
+    ("martingale_z1_sign", "cv.py",
+     "    return d * np.asarray(a1, dtype=np.int64) - np.asarray(cnt1, dtype=np.int64) * s1",
+     "    return d * np.asarray(a1, dtype=np.int64) + np.asarray(cnt1, dtype=np.int64) * s1", CV_PINS),
+    ("cv_kemeny_term_sign", "cv.py",
+     "    kc = ((float(sum_y1) - float(sum_y2)) + beta2 * m2) / w",
+     "    kc = ((float(sum_y1) - float(sum_y2)) - beta2 * m2) / w", CV_PINS),
     ("subtree_test_printed_direction", "spantree.py",
      "                if inside(u, e1):",
      "                if inside(e1, u):", ST_PINS),
@@ -109,7 +126,8 @@ def run_pins_on_copy(tmp_path, fname, src, pins):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("fname,pins", [("lewalk_oracle.c", C_PINS), ("dense.py", C_PINS), ("spantree.py", ST_PINS)])
+@pytest.mark.parametrize("fname,pins", [("lewalk_oracle.c", C_PINS), ("dense.py", C_PINS), ("cv.py", CV_PINS),
+                                        ("spantree.py", ST_PINS)])
 def test_unchanged_copy_passes_the_pins(fname, pins, tmp_path):
     src = open(os.path.join(ROOT, "oracle", fname)).read()
     code, out = run_pins_on_copy(tmp_path, fname, src, pins)
