@@ -71,6 +71,12 @@ MUTATIONS = [
     ("rwb_missing_factor_n", "dense.py",
      "    return tr, 1.0 / n + tr / ((n - 1) * (tr + n * ld))",
      "    return tr, 1.0 / n + tr / ((n - 1) * (tr + ld))", C_PINS),
+    ("cv_draw_potential_of_the_wrong_node", "lewalk_oracle.c",
+     "if (cv && cv->h1) cv->a1[u] += cv->h1[next[u]];",
+     "if (cv && cv->h1) cv->a1[u] += cv->h1[u];", CV_PINS),
+    ("cv_pi_martingale_sign", "lewalk_oracle.c",
+     "m2 += (double)(d * cv->h2[w] - cv->S2[u]) / (double)d;",
+     "m2 += (double)(cv->S2[u] - d * cv->h2[w]) / (double)d;", CV_PINS),
     ("bf16_ties_away_from_even", "cv.py",
      "    rounded = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16",
      "    rounded = ((b + 0x8000) >> 16) << 16", CV_PINS),
