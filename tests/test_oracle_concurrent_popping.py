@@ -138,3 +138,54 @@ def test_dropping_the_aborted_arrows_breaks_the_counts():
         ref = oracle.sample(g.row_ptr, g.col, v, 123, i, 1)
         differ += [int(x) for x in ref.cnt1] != k
     assert differ >= 4
+
+
+@pytest.fixture(scope="module")
+def threaded(tmp_path_factory):
+    """tests/concurrent_popping.c built with gcc (pthreads, C11 atomics)."""
+    import ctypes
+    import os
+    import subprocess
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "concurrent_popping.c")
+    lib = str(tmp_path_factory.mktemp("popping") / "libpopping.so")
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-pthread", "-fPIC", "-shared", "-o", lib, src])
+    so = ctypes.CDLL(lib)
+    p = ctypes.c_void_p
+    so.concurrent_popping.restype = ctypes.c_int
+    so.concurrent_popping.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, p, ctypes.c_int32,
+                                      ctypes.c_uint64, ctypes.c_long, p, p]
+    return so
+
+
+# Larger graphs keep several threads inside one sample at once (aborts, waits
+# and lost claims all occur on these).
+THREAD_CASES = CASES + [
+    ("ba2000", lambda: I.ba(2000, 3, seed=1), -1),
+    ("er1000", I.er_1000, -1),
+]
+
+
+@pytest.mark.parametrize("walkers", [2, 4, 16])
+@pytest.mark.parametrize("name,maker,root", THREAD_CASES, ids=[c[0] for c in THREAD_CASES])
+def test_threads_sharing_one_sample_give_the_sequential_counts_and_tree(threaded, name, maker, root, walkers):
+    """The same protocol on real threads: one 64-bit word per node changed by
+    compare-and-swap (claiming a free node is the only contended write), the
+    draws given as a table in the oracle's keying.  Every run, whatever the
+    scheduling, ends with the sequential oracle's visits per node and tree."""
+    g = maker()
+    v = oracle.root_max_degree(g.row_ptr) if root < 0 else root
+    seed = 0xBEEF + walkers
+    for i in range(3):
+        ref = oracle.sample(g.row_ptr, g.col, v, seed, i, 1, keep_tree=True)
+        kmax = int(ref.cnt1.max()) + 1
+        draw = Stacks(g, seed, i)
+        table = np.array([[draw(u, j) for j in range(kmax)] for u in range(g.n)], dtype=np.int32)
+        for rep in range(3):
+            k = np.zeros(g.n, dtype=np.int32)
+            arrow = np.zeros(g.n, dtype=np.int32)
+            rc = threaded.concurrent_popping(g.n, v, kmax, table.ctypes.data, walkers, 1000 * i + rep, 10 ** 7,
+                                             k.ctypes.data, arrow.ctypes.data)
+            assert rc == 0, rc
+            assert np.array_equal(k, ref.cnt1.astype(np.int32))
+            tree = np.array(ref.tree[0], dtype=np.int32)
+            assert np.array_equal(arrow, tree)
