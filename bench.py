@@ -202,9 +202,36 @@ def cpu_oracle_rate(g, v, seed, target_seconds, first_id=1 << 30):
     c = oracle.sample_threads(g.row_ptr, g.col, v, seed, first_id + 1, count, cores)
     dt = time.perf_counter() - t0
     steps = c.sum_y1 + int(c.cnt2.sum()) + c.sum_y2
-    return {"value": steps / dt, "unit": "walk steps/s", "cores": cores, "kind": "oracle",
-            "sample": "%d samples (ids %d..%d) of the same graph and root, %d threads, %.1f s" %
-                      (count, first_id + 1, first_id + count, cores, dt)}
+    out = {"value": steps / dt, "unit": "walk steps/s", "cores": cores, "kind": "oracle",
+           "sample": "%d samples (ids %d..%d) of the same graph and root, %d threads, %.1f s" %
+                     (count, first_id + 1, first_id + count, cores, dt)}
+    # One thread on a quarter of the per-core share, for the per-core rate.
+    one = max(1, per_core // 4)
+    t0 = time.perf_counter()
+    c = oracle.sample(g.row_ptr, g.col, v, seed, first_id + 1 + count, one, keep_per_sample=False)
+    dt1 = time.perf_counter() - t0
+    steps1 = c.sum_y1 + int(c.cnt2.sum()) + c.sum_y2
+    out["single_thread"] = {"value": steps1 / dt1, "unit": "walk steps/s",
+                            "sample": "%d samples, 1 thread, %.1f s" % (one, dt1)}
+    return out
+
+
+def cpu_time_to_accuracy(omega, seed=7):
+    """The oracle on all host cores at the omega the GPU's time-to-accuracy run
+    found (same ids 0..omega-1 and seed as the GPU's timed run, so the same
+    counts): wall seconds for sampling plus finalize, and the errors."""
+    import oracle
+    from paper_2311_10290_gb300 import inputs
+    g = inputs.er_1000()
+    ecc_t, kc_t, _ = read_truth()
+    v = oracle.root_max_degree(g.row_ptr)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    c = oracle.sample_threads(g.row_ptr, g.col, v, seed, 0, omega, cores)
+    _, ec, kc = oracle.finalize(g.row_ptr, v, omega, c.cnt1, c.cnt2, c.sum_y1, c.sum_y2)
+    dt = time.perf_counter() - t0
+    return {"omega": omega, "seconds": dt, "cores": cores, "kind": "oracle",
+            "ecc_max_rel_err": float(np.max(np.abs(ec - ecc_t) / ecc_t)), "kc_rel_err": abs(kc - kc_t) / kc_t}
 
 
 # ------------------------------------------------------------ accuracy
@@ -955,6 +982,9 @@ def run_ours(args, rank, world):
     if rank == 0 and not args.no_tta:
         note("time to accuracy (plain)")
         res["time_to_accuracy"] = time_to_accuracy(torch, LapGraph)
+        if not args.no_cpu and world == 1 and res["time_to_accuracy"].get("omega"):
+            note("time to accuracy: the CPU oracle at the same omega")
+            res["time_to_accuracy"]["cpu_oracle"] = cpu_time_to_accuracy(res["time_to_accuracy"]["omega"])
     params = None
     if rank == 0 and args.cv_graphs > 0:
         note("control variate: training data and training")
