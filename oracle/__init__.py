@@ -42,7 +42,7 @@ def _load():
             lib.oracle_sample.restype = ctypes.c_int
             lib.oracle_sample.argtypes = [ctypes.c_int32, p, p, ctypes.c_int32, ctypes.c_uint64,
                                           ctypes.c_uint64, ctypes.c_uint64, p, ctypes.c_int32,
-                                          p, p, p, p, p, ctypes.c_uint64, ctypes.c_int]
+                                          p, p, p, p, p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int32]
             lib.oracle_cyclepop.restype = ctypes.c_int
             lib.oracle_cyclepop.argtypes = [ctypes.c_int32, p, p, ctypes.c_int32, ctypes.c_uint64,
                                             ctypes.c_uint64, ctypes.c_uint64, p, p, p]
@@ -90,10 +90,12 @@ class Counts:
 
 
 def sample(row_ptr, col, v, seed, first, count, order=None, keep_per_sample=True,
-           keep_tree=False, max_steps=0, paths=False):
+           keep_tree=False, max_steps=0, paths=False, path_start=-1):
     """Run sample ids [first, first+count) on one thread; returns Counts.
     paths=True: the two absorbed walks are the sample's loop-included paths
-    (see oracle_one_sample in lewalk_oracle.c)."""
+    (see oracle_one_sample in lewalk_oracle.c).  path_start >= 0: the first
+    absorbed walk (or path) starts at that node instead of a uniform draw, so
+    cnt2 / (count d_u) estimates row path_start of L_v^{-1}."""
     rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
     cl = np.ascontiguousarray(col, dtype=np.int32)
     n = rp.size - 1
@@ -105,7 +107,7 @@ def sample(row_ptr, col, v, seed, first, count, order=None, keep_per_sample=True
     rc = _load().oracle_sample(n, _ptr(rp), _ptr(cl), int(v), int(seed), int(first), int(count),
                                _ptr(od), 0 if od is None else od.size,
                                _ptr(out.cnt1), _ptr(out.cnt2), _ptr(y1), _ptr(y2), _ptr(tree),
-                               int(max_steps), int(bool(paths)))
+                               int(max_steps), int(bool(paths)), int(path_start))
     if rc != 0:
         raise RuntimeError("oracle_sample failed with code %d" % rc)
     out.sum_y1 = int(y1.sum(dtype=np.uint64))
@@ -157,7 +159,7 @@ def hitting_walks(row_ptr, col, v, seed, reps, max_steps=0):
     return sums
 
 
-def sample_threads(row_ptr, col, v, seed, first, count, threads, paths=False):
+def sample_threads(row_ptr, col, v, seed, first, count, threads, paths=False, path_start=-1):
     """Same counts as sample(), with the sample ids split into `threads`
     contiguous ranges run concurrently (ctypes releases the GIL)."""
     threads = max(1, min(int(threads), int(count))) if count else 1
@@ -165,7 +167,7 @@ def sample_threads(row_ptr, col, v, seed, first, count, threads, paths=False):
 
     def run(t):
         return sample(row_ptr, col, v, seed, bounds[t], bounds[t + 1] - bounds[t], keep_per_sample=False,
-                      paths=paths)
+                      paths=paths, path_start=path_start)
 
     with ThreadPoolExecutor(max_workers=threads) as ex:
         parts = list(ex.map(run, range(threads)))

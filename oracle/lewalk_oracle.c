@@ -117,13 +117,18 @@ typedef struct {
  * paths = 1: they are the loop-included paths of the sample's own stacks
  * (Section 4.2, "loop-erased walk" interpretation and "Sample from the
  * paths"; Section 5.2): same start draws, and the j-th departure of a path
- * from u takes stack entry j of u, i.e. draw (u, j, i, 0) of the Wilson run. */
+ * from u takes stack entry j of u, i.e. draw (u, j, i, 0) of the Wilson run.
+ * path_start >= 0: the first absorbed walk (or path) starts at that node
+ * instead of a uniform draw; its passes then estimate row path_start of
+ * L_v^{-1} (Section 4.2, "v-absorbed walk" and "loop-erased walk" lemmas:
+ * (L_v^{-1})_{su} = E[passes of u on a walk from s] / d_u). */
 static int oracle_one_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t v,
                              uint64_t seed, uint32_t i, const int32_t *order, int32_t n_order,
                              uint32_t *draws, int32_t *next, uint8_t *intree,
                              uint64_t *cnt1, uint64_t *cnt2,
                              uint64_t *y1_out, uint64_t *y2_out, int32_t *tree_out,
-                             uint64_t max_steps, const oracle_cv *cv, double *m2_out, int paths)
+                             uint64_t max_steps, const oracle_cv *cv, double *m2_out, int paths,
+                             int32_t path_start)
 {
     /* Alg. 2: InTree[u] = false, Next[u] = -1 for all u; InTree[v] = true. */
     for (int32_t u = 0; u < n; ++u) { intree[u] = 0; next[u] = -1; draws[u] = 0; }
@@ -160,7 +165,8 @@ static int oracle_one_sample(int32_t n, const int32_t *row_ptr, const int32_t *c
      * loop-included path from s.  draws[] now counts a path's departures. */
     {
         uint64_t t = 0;
-        int32_t u = (int32_t)oracle_below(oracle_r64(seed, 0u, 0u, i, 1u), (uint64_t)n);
+        int32_t u = path_start >= 0 ? path_start
+                                    : (int32_t)oracle_below(oracle_r64(seed, 0u, 0u, i, 1u), (uint64_t)n);
         if (paths)
             for (int32_t w = 0; w < n; ++w) draws[w] = 0;
         while (u != v) {
@@ -221,9 +227,10 @@ int oracle_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t
                   uint64_t seed, uint64_t first, uint64_t count,
                   const int32_t *order, int32_t n_order,
                   uint64_t *cnt1, uint64_t *cnt2,
-                  uint64_t *y1, uint64_t *y2, int32_t *tree, uint64_t max_steps, int paths)
+                  uint64_t *y1, uint64_t *y2, int32_t *tree, uint64_t max_steps, int paths,
+                  int32_t path_start)
 {
-    if (n <= 0 || v < 0 || v >= n || first + count > 0x100000000ull) return -2;
+    if (n <= 0 || v < 0 || v >= n || first + count > 0x100000000ull || path_start >= n) return -2;
     uint32_t *draws = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
     int32_t *next = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     uint8_t *intree = (uint8_t *)malloc((size_t)n);
@@ -233,7 +240,8 @@ int oracle_sample(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t
         uint64_t a = 0, b = 0;
         rc = oracle_one_sample(n, row_ptr, col, v, seed, (uint32_t)(first + q), order, n_order,
                                draws, next, intree, cnt1, cnt2, &a, &b,
-                               tree ? tree + (size_t)q * (size_t)n : NULL, max_steps, NULL, NULL, paths);
+                               tree ? tree + (size_t)q * (size_t)n : NULL, max_steps, NULL, NULL, paths,
+                               path_start);
         if (rc) break;
         if (y1) y1[q] = a;
         if (y2) y2[q] = b;
@@ -270,7 +278,7 @@ int oracle_sample_cv(int32_t n, const int32_t *row_ptr, const int32_t *col, int3
         uint64_t a = 0, b = 0;
         double mm = 0.0;
         rc = oracle_one_sample(n, row_ptr, col, v, seed, (uint32_t)(first + q), NULL, 0,
-                               draws, next, intree, cnt1, cnt2, &a, &b, NULL, 0, &cv, &mm, paths);
+                               draws, next, intree, cnt1, cnt2, &a, &b, NULL, 0, &cv, &mm, paths, -1);
         if (rc) break;
         if (y1) y1[q] = a;
         if (y2) y2[q] = b;

@@ -440,3 +440,30 @@ def test_rw_betweenness_closed_form_and_ldiag_route():
     tr, cb = D.from_ldiag(lp)
     assert tr == pytest.approx(float(lp.sum()), rel=1e-13)
     assert np.all(cb > 1.0 / g.n) and np.argmax(cb) == np.argmin(lp)
+
+
+@pytest.mark.parametrize("paths", [False, True], ids=["own_draws", "stack_paths"])
+def test_fixed_start_passes_estimate_a_row_of_lv_inverse(paths):
+    """Section 4.2 lemmas ("v-absorbed walk", "loop-erased walk"): the passes
+    of u on a v-absorbed walk from s -- or on the loop-included path from s
+    of a Wilson run's stacks -- have mean d_u (L_v^{-1})_{su}.  With the first
+    absorbed walk started at a fixed s, cnt2 / (omega d) matches row s of the
+    dense L_v^{-1} within 6 standard errors at every node (batch means), and
+    the pass at s itself is counted (the row's diagonal entry is >= 1 / d_s)."""
+    g = I.ba(80, 2, seed=9)
+    v = oracle.root_max_degree(g.row_ptr)
+    d = np.diff(g.row_ptr).astype(np.float64)
+    lv = D.lv_inverse(g.n, g.row_ptr, g.col, v)
+    for s in (int(np.argmin(d)), (v + 1) % g.n):
+        if s == v:
+            continue
+        rows = []
+        for b in range(20):
+            c = oracle.sample_threads(g.row_ptr, g.col, v, 31, 400 * b, 400, 4, paths=paths, path_start=s)
+            rows.append(c.cnt2.astype(np.float64) / (400 * d))
+        rows = np.array(rows)
+        mean, se = rows.mean(axis=0), rows.std(axis=0, ddof=1) / np.sqrt(len(rows))
+        keep = np.arange(g.n) != v
+        assert np.all(np.abs(mean - lv[s])[keep] <= 6 * se[keep] + 1e-12), np.max(np.abs(mean - lv[s]) / (se + 1e-300))
+        assert np.all(rows[:, s] >= 1.0 / d[s] - 1e-15)
+        assert np.all(rows[:, v] == 0.0)
