@@ -171,3 +171,24 @@ def test_cv_kemeny_estimate_with_the_hitting_time_potential():
     assert np.var(cv) < 0.8 * np.var(plain), (np.var(cv), np.var(plain))
     assert abs(cv.mean() - kc_t) < 6 * cv.std(ddof=1) / np.sqrt(len(cv))
     assert abs(plain.mean() - kc_t) < 6 * plain.std(ddof=1) / np.sqrt(len(plain))
+
+
+def test_hitting_walks_estimate_the_hitting_times():
+    """The control variate's hitting-time targets (Section 3.2, v-absorbed
+    walk lemma: E[length of a walk from u absorbed at v] = h(u, v) =
+    (L_v^{-1} d)_u): batch means of the oracle's walk lengths fall within 6
+    standard errors of the dense h(., v) at every node; on a star rooted at
+    its hub every walk from a leaf is exactly one step."""
+    g = I.ba(120, 2, seed=11)
+    v = oracle.root_max_degree(g.row_ptr)
+    hit = D.hitting_times_to(g.n, g.row_ptr, g.col, v)
+    reps = 40
+    batches = np.array([oracle.hitting_walks(g.row_ptr, g.col, v, 1000 + b, reps).astype(np.float64) / reps
+                        for b in range(25)])
+    mean, se = batches.mean(axis=0), batches.std(axis=0, ddof=1) / np.sqrt(len(batches))
+    keep = np.arange(g.n) != v
+    assert np.all(np.abs(mean - hit)[keep] <= 6 * se[keep] + 1e-9)
+    assert np.all(batches[:, v] == 0.0)
+    s = I.star(30)
+    sums = oracle.hitting_walks(s.row_ptr, s.col, 0, 5, 7)
+    assert sums[0] == 0 and np.all(sums[1:] == 7)

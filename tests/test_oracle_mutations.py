@@ -77,6 +77,9 @@ MUTATIONS = [
     ("cv_pi_martingale_sign", "lewalk_oracle.c",
      "m2 += (double)(d * cv->h2[w] - cv->S2[u]) / (double)d;",
      "m2 += (double)(cv->S2[u] - d * cv->h2[w]) / (double)d;", CV_PINS),
+    ("hitting_walk_last_step_dropped", "lewalk_oracle.c",
+     "            sums[u] += t;",
+     "            sums[u] += t - 1;", CV_PINS),
     ("bf16_ties_away_from_even", "cv.py",
      "    rounded = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16",
      "    rounded = ((b + 0x8000) >> 16) << 16", CV_PINS),
