@@ -677,7 +677,7 @@ def random_access_ceiling(torch, args):
     (lap_probe_random_rw, independent pairs, no dependent chain) at three
     launch sizes; the best rate is what the sampler's walk steps/s are
     compared with."""
-    from paper_2311_10290_gb300.lap import lap_probe_random_rw
+    from paper_2311_10290_gb300.probe import lap_probe_random_rw
     free, _ = torch.cuda.mem_get_info()
     nbytes = min(64 << 30, int(free * 0.5)) // 256 * 256
     buf = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")

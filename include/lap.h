@@ -370,7 +370,8 @@ lap_status lap_graph_info(const lap_graph *g, int32_t *n, int64_t *arcs, int32_t
  *                        (not validated here: pass a valid, connected graph)
  *   root                 landmark v, or < 0 for the highest-degree node
  *   seed, first_id       Philox seed and first sample id; ids
- *                        [first_id, first_id + n_samples) are drawn
+ *                        [first_id, first_id + n_samples) are drawn and
+ *                        must lie below 2^32 (else LAP_ERR_TOO_LARGE)
  *   cnt1, cnt2           device uint64[n], overwritten with the visit and
  *                        uniform-walk pass counts (as lap_counts)
  *   sums2                device uint64[2], overwritten with {sum Y1, sum Y2}
@@ -379,14 +380,19 @@ lap_status lap_graph_info(const lap_graph *g, int32_t *n, int64_t *arcs, int32_t
  * The graph must fit the scratch with at least one sample in flight
  * (24 n + 512 bytes, so n up to about 1.39 million): larger graphs return
  * LAP_ERR_TOO_LARGE.  Smaller graphs keep up to (32 MiB - 16 n) / (8 n)
- * samples in flight.  The call
- * synchronises the stream before returning.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make it before any stream capture.  All calls share the one array
- * and each clears what it needs, so calls that overlap on the GPU (other
- * streams or threads) race and give wrong results: serialise them.
- * Errors (LAP_ERR_INVALID_ARG, LAP_ERR_TOO_LARGE, LAP_ERR_STEP_LIMIT,
- * LAP_ERR_CUDA) are explained by lap_static_last_error().
+ * samples in flight.  The call synchronises the stream before returning: it
+ * reads row_ptr[n] (and, for root < 0, the chosen root) back to the host, and
+ * the device status after the samples.  The first call on a device (and the
+ * first after that device's context was re-created, e.g. by cudaDeviceReset)
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array, which keeps the last call's contents; each call clears what
+ * must start at zero, so calls that overlap on the GPU (other streams or
+ * threads) race and give wrong results: serialise them.
+ * Errors (LAP_ERR_INVALID_ARG, LAP_ERR_TOO_LARGE, LAP_ERR_STEP_LIMIT for a
+ * sample over the step budget or a node drawn from more than 2^30 times in
+ * one sample, LAP_ERR_CUDA) are explained by lap_static_last_error().
+ * Argument and size errors are found on the host before any CUDA call.
  */
 lap_status lap_sample_static(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32_t root,
                              uint64_t seed, uint64_t first_id, uint64_t n_samples,
@@ -401,26 +407,6 @@ const char *lap_static_last_error(void);
 /* One-line description of the last error on this handle (or of the last
  * failed lap_graph_create when g is NULL).  Never NULL. */
 const char *lap_last_error(const lap_graph *g);
-
-/*
- * lap_probe_random_rw - a measurement aid, not a step of the method.
- *
- * Launches `blocks` x 256 threads on `cuda_stream` (NULL: the default stream);
- * each thread does `rounds` rounds of 4 independent single-byte read-then-
- * write pairs at addresses in [0, bytes) of `device_buf` drawn from a
- * SplitMix64 hash of (salt, thread, round), so blocks * 256 * rounds * 4
- * pairs per launch.  This is the memory pattern of one Wilson step of the
- * 1-byte-state sampler (one random state-byte read, one random state-byte
- * write) without its dependent chain; timing the launch (CUDA events on the
- * same stream) gives the ceiling that pattern reaches on the device.
- *
- * device_buf: caller-owned device memory of `bytes` bytes, which the probe
- * modifies (every byte it touches is incremented).  Returns
- * LAP_ERR_INVALID_ARG for a NULL buffer, bytes == 0 or blocks == 0,
- * LAP_ERR_CUDA if the launch fails; asynchronous otherwise.
- */
-lap_status lap_probe_random_rw(void *device_buf, uint64_t bytes, uint32_t blocks, uint32_t rounds, uint64_t salt,
-                               void *cuda_stream);
 
 #ifdef __cplusplus
 }

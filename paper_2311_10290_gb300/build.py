@@ -18,6 +18,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblap.so")
+# The benchmark's random-access probe: a measurement aid in a library of its own.
+PROBE_DIR = os.path.join(PKG, "probe")
+PROBE_LIB = os.path.join(PKG, "liblap_probe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
@@ -69,6 +72,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         run([NVCC] + ARCH + ["-shared", "--cudart", "shared", "-o", tmp] + objs +
             ["-Xlinker", "-rpath,/usr/local/cuda/lib64", "-lcuda"])
         os.replace(tmp, LIB)
+    probe_src = os.path.join(PROBE_DIR, "probe.cu")
+    if force or _stale(PROBE_LIB, [probe_src, os.path.join(PROBE_DIR, "lap_probe.h")]):
+        tmp = PROBE_LIB + ".tmp%d" % os.getpid()
+        run([NVCC] + FLAGS[len(ARCH):] + list(extra) + ARCH + ["-I", PROBE_DIR, "-shared", "--cudart", "shared",
+                                                              "-o", tmp, probe_src,
+                                                              "-Xlinker", "-rpath,/usr/local/cuda/lib64"])
+        os.replace(tmp, PROBE_LIB)
     return LIB
 
 

@@ -19,27 +19,54 @@ __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void *g_scratch_addr[kMaxDevices] = {};
+void *g_scratch_ctx[kMaxDevices] = {};
+
+// The driver's cuCtxGetCurrent, fetched through the runtime so that the
+// library keeps no link-time dependency on the driver library.
+typedef int (*CtxGetCurrentFn)(void **);
+
+void *current_context()
+{
+    static CtxGetCurrentFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(f);
+    }();
+    void *ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
 
 uint64_t round256(uint64_t x) { return (x + 255ull) & ~255ull; }
 
 // Device address of g_static_scratch on the current device.  The host-side
 // symbol is only a stand-in, so the address is looked up once per device
-// with that device current.
+// with that device current.  The lookup is repeated when the device's
+// context has changed since (after a cudaDeviceReset the runtime creates a
+// new context, in which the array has a new address).
 lap_status scratch_address(void **out, std::string &err)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { err = std::string("cudaGetDevice: ") + cudaGetErrorString(e); return LAP_ERR_CUDA; }
     if (dev < 0 || dev >= kMaxDevices) { err = "device index out of range"; return LAP_ERR_INVALID_ARG; }
+    // The current context (NULL before this thread's first runtime call, or
+    // before the runtime has initialised the driver).
+    void *ctx = current_context();
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || !ctx || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess || !p) {
             err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
             return LAP_ERR_CUDA;
         }
+        ctx = current_context();
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return LAP_OK;
@@ -75,7 +102,10 @@ lap_status lap_sample_static(int32_t n, const int32_t *row_ptr, const int32_t *c
         return fail_static(LAP_ERR_INVALID_ARG, "n must be >= 2 and every pointer set");
     if (root >= n) return fail_static(LAP_ERR_INVALID_ARG, "root out of range");
     if (n_samples == 0) return fail_static(LAP_ERR_INVALID_ARG, "n_samples must be >= 1");
-    if (first_id + n_samples > (1ull << 32)) return fail_static(LAP_ERR_TOO_LARGE, "sample ids are limited to 2^32");
+    // Ids are 32-bit: [first_id, first_id + n_samples) must lie in [0, 2^32)
+    // (written so that no sum can wrap).
+    if (first_id >= (1ull << 32) || n_samples > (1ull << 32) - first_id)
+        return fail_static(LAP_ERR_TOO_LARGE, "sample ids [first_id, first_id + n_samples) must lie below 2^32");
 
     // Layout of the static scratch.
     const uint64_t rowinfo_bytes = round256(8ull * (uint64_t)n);
@@ -135,8 +165,6 @@ lap_status lap_sample_static(int32_t n, const int32_t *row_ptr, const int32_t *c
     p.g = LapDevGraph{rowinfo, col_idx, n, arcs};
     p.root = root;
     p.seed = seed;
-    p.first = (uint32_t)first_id;
-    p.count = (uint32_t)n_samples;
     p.slots = slots;
     p.ws = state;
     p.slot_epoch = slot_epoch;
@@ -145,15 +173,29 @@ lap_status lap_sample_static(int32_t n, const int32_t *row_ptr, const int32_t *c
     p.acc = acc;
     p.step_limit = (1ull << 20) + 1024ull * (uint64_t)n;
     p.num_sms = num_sms;
-    STATIC_CUDA(lap_launch_sample(p, st));
+    // Launches of at most 2^24 samples (a launch's sample count is 32-bit);
+    // each claims its ids from a counter that starts at zero.
+    const uint64_t chunk = 1ull << 24;
+    for (uint64_t done = 0; done < n_samples;) {
+        const uint64_t c = n_samples - done < chunk ? n_samples - done : chunk;
+        p.first = (uint32_t)(first_id + done);
+        p.count = (uint32_t)c;
+        STATIC_CUDA(cudaMemsetAsync(&acc->claim, 0, sizeof(unsigned int), st));
+        STATIC_CUDA(lap_launch_sample(p, st));
+        done += c;
+    }
     // cnt1 = omega (first visit of every non-root node) + repeats.
     STATIC_CUDA(lap_launch_counts(n, root, n_samples, rep, reinterpret_cast<unsigned long long *>(cnt1), st));
     STATIC_CUDA(cudaMemcpyAsync(sums2, &acc->sum_y1, 2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
     LapDevAcc h;
     STATIC_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
     STATIC_CUDA(cudaStreamSynchronize(st));
-    if (h.status & (LAP_DEV_STEP_LIMIT | LAP_DEV_K_OVERFLOW))
+    if (h.status & LAP_DEV_STEP_LIMIT)
         return fail_static(LAP_ERR_STEP_LIMIT, "a sample exceeded the per-sample step budget (is the graph connected?)");
+    if (h.status & LAP_DEV_K_OVERFLOW)
+        return fail_static(LAP_ERR_STEP_LIMIT, "a node was visited more than 2^30 times in one sample");
+    if (h.status & LAP_DEV_BAD_INDEX)
+        return fail_static(LAP_ERR_CUDA, "internal error: node index out of range caught in the sampler");
     g_static_error = "no error";
     return LAP_OK;
 }

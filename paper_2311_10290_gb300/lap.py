@@ -91,7 +91,6 @@ def library():
         "lap_mlp_loss_grad": (i32, [vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp, vp, vp]),
         "lap_adamw": (i32, [vp, vp, vp, vp, i64, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                             ctypes.c_float, ctypes.c_float, vp]),
-        "lap_probe_random_rw": (i32, [vp, u64, ctypes.c_uint32, ctypes.c_uint32, u64, vp]),
         "lap_static_scratch_bytes": (u64, []),
         "lap_static_last_error": (ctypes.c_char_p, []),
         "lap_batch_create": (i32, [i32, vp, vp, vp, vp, ctypes.POINTER(vp)]),
@@ -315,16 +314,6 @@ def lap_sample_static(n, row_ptr, col_idx, root, seed, first_id, n_samples, cnt1
                                      ctypes.c_void_p(sums2.data_ptr()), ctypes.c_void_p(int(stream)))
     if st != 0:
         raise LapError(st, lap_static_last_error())
-
-
-def lap_probe_random_rw(buf, blocks, rounds, salt=0, stream=0):
-    """Random single-byte read-then-write probe (see include/lap.h) over the
-    uint8 CUDA tensor `buf`; blocks * 256 * rounds * 4 pairs, asynchronous on
-    `stream` (a cudaStream_t as an integer)."""
-    st = library().lap_probe_random_rw(ctypes.c_void_p(buf.data_ptr()), int(buf.numel()), int(blocks), int(rounds),
-                                       int(salt), ctypes.c_void_p(int(stream)))
-    if st != 0:
-        raise LapError(st, "lap_probe_random_rw failed")
 
 
 def _dp(t):

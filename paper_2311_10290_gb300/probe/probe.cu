@@ -4,8 +4,13 @@
 // Wilson step of the 1-byte-state samplers (read a node's state byte, write a
 // state byte), without the dependent chain that limits a sampler lane.  The
 // benchmark times it to measure the ceiling this pattern reaches on the
-// device, the denominator its sampler throughput is compared with.
-#include "lap_internal.h"
+// device, the denominator its sampler throughput is compared with.  It is
+// built into its own library (liblap_probe.so), apart from the method's.
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "lap_probe.h"
 
 namespace {
 
@@ -39,12 +44,12 @@ __global__ void __launch_bounds__(256) random_rw_kernel(uint8_t *buf, uint64_t b
 
 }  // namespace
 
-extern "C" lap_status lap_probe_random_rw(void *device_buf, uint64_t bytes, uint32_t blocks, uint32_t rounds,
+extern "C" int lap_probe_random_rw(void *device_buf, uint64_t bytes, uint32_t blocks, uint32_t rounds,
                                           uint64_t salt, void *cuda_stream)
 {
-    if (!device_buf || bytes == 0 || blocks == 0) return LAP_ERR_INVALID_ARG;
-    if (rounds == 0) return LAP_OK;
+    if (!device_buf || bytes == 0 || blocks == 0) return LAP_PROBE_ERR_INVALID_ARG;
+    if (rounds == 0) return LAP_PROBE_OK;
     random_rw_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(static_cast<uint8_t *>(device_buf),
                                                                                bytes, rounds, salt);
-    return cudaGetLastError() == cudaSuccess ? LAP_OK : LAP_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? LAP_PROBE_OK : LAP_PROBE_ERR_CUDA;
 }

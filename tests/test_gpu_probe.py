@@ -8,7 +8,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-from paper_2311_10290_gb300.lap import LapError, lap_probe_random_rw  # noqa: E402
+from paper_2311_10290_gb300.probe import ProbeError, lap_probe_random_rw  # noqa: E402
 
 
 def splitmix64(z):
@@ -36,5 +36,5 @@ def test_probe_touches_exactly_its_addresses():
 
 def test_probe_rejects_empty_launch():
     buf = torch.zeros(1024, dtype=torch.uint8, device="cuda")
-    with pytest.raises(LapError):
+    with pytest.raises(ProbeError):
         lap_probe_random_rw(buf, 0, 1)
