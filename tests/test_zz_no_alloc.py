@@ -62,6 +62,21 @@ def test_two_calls_in_a_row_match_the_handle_api():
             assert np.array_equal(c1, e1) and np.array_equal(c2, e2) and np.array_equal(ds, es)
 
 
+def test_lanes_reuse_their_slot_within_one_call():
+    """n_samples several times the number of slots the scratch holds: every
+    lane runs several samples in its slot, one after another, so the per-slot
+    epoch bits (not a fresh zeroed state) separate the samples."""
+    g = I.ba(200_000, 5, seed=2)
+    slots = (lap_static_scratch_bytes() - 16 * g.n) // (8 * g.n)
+    count = 100
+    assert count >= 4 * slots
+    for first in (0, 7_000):    # two calls in a row on the same graph
+        v, c1, c2, s = handle_counts(g, -1, 31, first, count)
+        d1, d2, ds = static_counts(g, v, 31, first, count)
+        assert np.array_equal(c1, d1) and np.array_equal(c2, d2)
+        assert int(ds[0]) == int(s[1]) and int(ds[1]) == int(s[2])
+
+
 def test_graph_too_large_for_the_scratch_is_rejected():
     n = lap_static_scratch_bytes() // 24 + 1000
     g = I.path(int(n))
