@@ -123,19 +123,30 @@ def forward(params, x, quantize=True):
 
 
 def loss_and_grads(params, x, t, w=(1.0, 1.0), quantize=True):
-    """MSE loss (1/N) sum_i sum_k w_k (y_ik - t_ik)^2 and its gradients."""
+    """MSE loss (1/N) sum_i sum_k w_k (y_ik - t_ik)^2 and its gradients.
+
+    quantize=True states the BF16 training arithmetic: every operand of a
+    product (a tensor-core operand on the GPU) is BF16, sums are exact here
+    (FP32 there).  Besides the forward pass's rounding points, the backward
+    pass rounds the output error dY and the back-propagated errors dH2, dH1
+    to BF16 where they enter a product (the weight gradients dY^T H2,
+    dH2^T H1, dH1^T X and the propagations dY W3, dH2 W2); the bias
+    gradients sum the unrounded errors."""
     y, (xb, W1, W2, W3, z1, h1, z2, h2) = forward(params, x, quantize)
+    q = bf16 if quantize else (lambda a: a)
     wk = np.asarray(w, dtype=np.float64)
     nrow = x.shape[0]
     r = y - t
     loss = float(np.sum(wk * r * r) / nrow)
     dy = 2.0 * wk * r / nrow
-    g = {"W3": dy.T @ h2, "b3": dy.sum(axis=0)}
-    dh2 = (dy @ W3) * (z2 > 0)
-    g["W2"] = dh2.T @ h1
+    dyq = q(dy)
+    g = {"W3": dyq.T @ h2, "b3": dy.sum(axis=0)}
+    dh2 = (dyq @ W3) * (z2 > 0)
+    dh2q = q(dh2)
+    g["W2"] = dh2q.T @ h1
     g["b2"] = dh2.sum(axis=0)
-    dh1 = (dh2 @ W2) * (z1 > 0)
-    g["W1"] = dh1.T @ xb
+    dh1 = (dh2q @ W2) * (z1 > 0)
+    g["W1"] = q(dh1).T @ xb
     g["b1"] = dh1.sum(axis=0)
     return loss, g
 

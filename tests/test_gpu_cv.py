@@ -3,8 +3,9 @@ oracle_sample_cv, oracle_hitting_walks), and its measured gain.
 
 Integer sums (A1, A2, P2, hitting-walk lengths) and per-sample M2 are
 bit-exact; CV estimates agree to 1e-12 relative; features to 1e-5; the BF16
-MLP forward, loss and gradients agree with the FP64 oracle (same BF16
-rounding points) to 2e-2 in norm; AdamW (FP32) to 1e-5."""
+MLP forward outputs and gradient entries agree element by element with the
+oracle (same BF16 rounding points, see assert_elementwise), the loss to
+1e-3; AdamW (FP32) to 1e-5."""
 import numpy as np
 import pytest
 
@@ -124,6 +125,24 @@ def test_per_sample_m2_trace_bit_exact():
     assert np.array_equal(m2.cpu().numpy(), m2o)
 
 
+def assert_elementwise(got, ref, axis, what=""):
+    """Element-wise bound of the BF16 MLP against the FP64 oracle with the
+    same BF16 rounding points: |got - ref| <= 1e-2 |ref| + 2e-3 rms, the rms
+    taken per output column (axis=0) or per parameter tensor (axis=None).
+    Both sides round the inputs, weights and hidden activations to BF16 at
+    the same points, so they differ only by FP32 accumulation order (about
+    1e-7 relative per sum) and the rare hidden value whose FP32 and FP64
+    pre-activations round to neighbouring BF16 values (one BF16 ulp, 2^-8
+    relative, weighted by an outgoing weight of about 0.1-0.2: about 5e-4 of
+    the column's rms per such value).  A wrong tile, fragment or column
+    gives errors of the order of the rms itself."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    rms = np.sqrt(np.mean(ref * ref, axis=axis, keepdims=axis is not None))
+    bad = np.abs(got - ref) > 1e-2 * np.abs(ref) + 2e-3 * rms
+    assert not np.any(bad), (what, np.argwhere(bad)[:5], np.max(np.abs(got - ref) / (np.abs(ref) + rms)))
+
+
 def _params(seed):
     p = CV.init_params(seed)
     rng = np.random.default_rng(seed + 1)
@@ -141,8 +160,7 @@ def test_mlp_forward_matches_oracle(rows):
     lap_mlp_forward(torch.tensor(packed(p), dtype=torch.float32, device="cuda"), torch.from_numpy(x).cuda(), rows, y)
     ref, _ = CV.forward({k: np.float32(v).astype(np.float64) for k, v in p.items()}, x.astype(np.float64))
     got = y.cpu().numpy()
-    assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref) + 1e-6
-    assert np.max(np.abs(got - ref)) <= 2e-2 * (np.max(np.abs(ref)) + 1e-3)
+    assert_elementwise(got, ref, axis=0)
 
 
 @pytest.mark.parametrize("rows", [37, 640, 5003])
@@ -157,10 +175,10 @@ def test_mlp_loss_and_gradients_match_oracle(rows):
                       torch.from_numpy(t).cuda(), rows, 1.0, 0.5, grad, loss)
     pf = {k: np.float32(v).astype(np.float64) for k, v in p.items()}
     lo, go = CV.loss_and_grads(pf, x.astype(np.float64), t.astype(np.float64), w=(1.0, 0.5))
-    assert loss.item() == pytest.approx(lo, rel=1e-2)
+    assert loss.item() == pytest.approx(lo, rel=1e-3)
     g = unpack(grad.cpu().numpy())
     for k in go:
-        assert np.linalg.norm(g[k] - go[k]) <= 2e-2 * np.linalg.norm(go[k]) + 1e-7, k
+        assert_elementwise(g[k], go[k], axis=None, what=k)
 
 
 def test_adamw_matches_oracle():

@@ -49,6 +49,54 @@ def test_mlp_gradients_match_finite_differences():
             assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), (k, idx, fd, an)
 
 
+def test_bf16_training_reduces_to_the_exact_gradients_on_bf16_values():
+    """With inputs, weights, targets and every intermediate exactly
+    representable in BF16 (small dyadic values), the BF16 statement of the
+    backward pass equals the exact one, which the finite-difference pin
+    fixes."""
+    rng = np.random.default_rng(4)
+    H, F, O = CV.HIDDEN, CV.N_FEAT, CV.N_OUT
+
+    def sparse(rows, cols, per_row):
+        """Entries +-1/2, `per_row` per row; with per_row = 2 and rows = cols,
+        two per column too (two permutations), so every product has at most
+        two nonzero terms and stays a short dyadic number."""
+        m = np.zeros((rows, cols))
+        for k in range(per_row):
+            perm = rng.permutation(max(rows, cols))[:rows] % cols if rows != cols else rng.permutation(cols)
+            m[np.arange(rows), perm] = rng.choice([-0.5, 0.5], rows)
+        return m
+
+    p = {"W1": sparse(H, F, 1), "b1": rng.choice([-0.5, 0.0, 0.5], H),
+         "W2": sparse(H, H, 2), "b2": rng.choice([-0.5, 0.0, 0.5], H),
+         "W3": sparse(O, H, 2), "b3": np.array([0.5, -0.25])}
+    x = rng.integers(-1, 2, (4, F)).astype(np.float64)
+    t = rng.integers(-4, 5, (4, O)) / 2.0
+    lq, gq = CV.loss_and_grads(p, x, t, w=(1.0, 0.5), quantize=True)
+    le, ge = CV.loss_and_grads(p, x, t, w=(1.0, 0.5), quantize=False)
+    assert lq == le
+    for k in ge:
+        assert np.array_equal(gq[k], ge[k]), k
+
+
+def test_bf16_backward_rounds_the_output_error_only_where_it_enters_a_product():
+    """One row, one hidden unit active, y - t chosen so that dY = 1 + 2^-10
+    (not a BF16 value: it rounds to 1): the W3 gradient takes the rounded
+    dY (1 * h2), the b3 gradient the unrounded one."""
+    p = {"W1": np.zeros((CV.HIDDEN, CV.N_FEAT)), "b1": np.zeros(CV.HIDDEN),
+         "W2": np.zeros((CV.HIDDEN, CV.HIDDEN)), "b2": np.zeros(CV.HIDDEN),
+         "W3": np.zeros((CV.N_OUT, CV.HIDDEN)), "b3": np.zeros(CV.N_OUT)}
+    p["b1"][0] = 1.0
+    p["W2"][0, 0] = 1.0           # h1[0] = 1, h2[0] = 1, every other unit 0
+    x = np.zeros((1, CV.N_FEAT))
+    t = np.array([[-(1.0 + 2.0 ** -10) / 2.0, 0.0]])     # y = 0, dY0 = 2 (y - t) = 1 + 2^-10
+    _, g = CV.loss_and_grads(p, x, t, w=(1.0, 1.0), quantize=True)
+    assert g["b3"][0] == 1.0 + 2.0 ** -10
+    assert g["W3"][0, 0] == 1.0
+    _, ge = CV.loss_and_grads(p, x, t, w=(1.0, 1.0), quantize=False)
+    assert ge["W3"][0, 0] == 1.0 + 2.0 ** -10
+
+
 def test_adamw_first_step_closed_form():
     w = np.array([0.5, -1.0, 2.0])
     g = np.array([0.3, -0.001, 0.0])

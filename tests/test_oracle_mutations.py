@@ -84,8 +84,11 @@ MUTATIONS = [
      "    rounded = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16",
      "    rounded = ((b + 0x8000) >> 16) << 16", CV_PINS),
     ("relu_derivative_dropped", "cv.py",
-     "    dh2 = (dy @ W3) * (z2 > 0)",
-     "    dh2 = (dy @ W3)", CV_PINS),
+     "    dh2 = (dyq @ W3) * (z2 > 0)",
+     "    dh2 = (dyq @ W3)", CV_PINS),
+    ("bf16_backward_rounding_point_moved", "cv.py",
+     """    g = {"W3": dyq.T @ h2, "b3": dy.sum(axis=0)}""",
+     """    g = {"W3": dy.T @ h2, "b3": dyq.sum(axis=0)}""", CV_PINS),
     ("adamw_second_moment_not_corrected", "cv.py",
      "    vh = v / (1.0 - beta2 ** step)",
      "    vh = v", CV_PINS),
