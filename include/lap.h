@@ -85,7 +85,7 @@ typedef enum {
                                   results are identical either way. */
     LAP_OPT_STACK = 6,         /* loop-erased path capacity per sample of kernel 2; 0 = default
                                   (16 sqrt(n) rounded up to a power of two, at least 1024) */
-    LAP_OPT_PATHS = 7          /* 0 (default): the uniform-start and pi-start v-absorbed walks take
+    LAP_OPT_PATHS = 7,         /* 0 (default): the uniform-start and pi-start v-absorbed walks take
                                   their own draws, as Alg. 2 and Alg. 4 print them.  1: they are the
                                   loop-included paths of the sample's own Wilson stacks (Section 4.2,
                                   "loop-erased walk" lemma and "Sample from the paths"; Section 5.2):
@@ -93,6 +93,16 @@ typedef enum {
                                   stack entry j, the draw (u, j, i, 0) of the Wilson run.  Same
                                   expectations (so the same estimands), correlated with the Wilson
                                   counts, which lowers the variance of y1 - 2 y2 and of Y1 - Y2.
+                                  Only before the first sample after lap_set_root. */
+    LAP_OPT_PATH_START = 8     /* -1 (default): the first absorbed walk (or loop-included path) of
+                                  each sample starts at a uniform draw (Alg. 2).  s in [0, n): it
+                                  starts at node s, so its passes of u have mean d_u (L_v^{-1})_{su}
+                                  (Section 4.2, "v-absorbed walk" and "loop-erased walk" lemmas)
+                                  and lap_lv_row returns row s of L_v^{-1}; with root t,
+                                  (L_t^{-1})_{ss} is the effective resistance between s and t.  The
+                                  ECC outputs (lap_ecc, lap_ldiag, lap_kirchhoff,
+                                  lap_rw_betweenness, the CV ECC) are then refused
+                                  (LAP_ERR_INVALID_ARG); Wilson counts and lap_kemeny are unchanged.
                                   Only before the first sample after lap_set_root. */
 } lap_option;
 
@@ -203,6 +213,19 @@ lap_status lap_sync(lap_graph *g);
 lap_status lap_ecc(lap_graph *g, double *out, int out_on_device);
 lap_status lap_ldiag(lap_graph *g, double *out, int out_on_device);
 lap_status lap_kemeny(lap_graph *g, double *out1);
+
+/*
+ * Passes of the first absorbed walk per node, scaled: out[u] = cnt2[u] /
+ * (omega d_u) (n doubles, host or device memory by out_on_device).  With a
+ * fixed start s (LAP_OPT_PATH_START) this estimates row s of L_v^{-1},
+ * (L_v^{-1})_{su} (Section 4.2, "v-absorbed walk" lemma: the walk from s
+ * passes u d_u (L_v^{-1})_{su} times on average; the same for the
+ * loop-included path, "loop-erased walk" lemma); out[v] = 0.  With the uniform
+ * start it is y2(u) ~ (1/n) e_u^T L_v^{-1} 1 of Alg. 2.  Synchronises.
+ * Errors: LAP_ERR_NO_ROOT, LAP_ERR_NO_SAMPLES, LAP_ERR_INVALID_ARG, sticky
+ * errors.
+ */
+lap_status lap_lv_row(lap_graph *g, double *out, int out_on_device);
 
 /*
  * Two more quantities of the same diagonal (Section 5, "Discussions"):

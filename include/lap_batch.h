@@ -139,6 +139,24 @@ lap_status lap_batch_kirchhoff(lap_batch *b, double *out);
 lap_status lap_batch_counts(lap_batch *b, int32_t graph, uint64_t *cnt1, uint64_t *cnt2, uint64_t *sums,
                             int on_device);
 
+/*
+ * Single-source rows of L_v^{-1} per graph (Section 4.2, "v-absorbed walk" and
+ * "loop-erased walk" lemmas), as LAP_OPT_PATH_START and lap_lv_row of a
+ * lap_graph handle:
+ *   lap_batch_set_path_start  start = s in [0, n[g]): from the next run on, the
+ *                             first absorbed walk (or loop-included path) of
+ *                             every sample of graph g starts at node s; -1
+ *                             (default) restores the uniform start.  Graph g's
+ *                             ECC, ldiag and Kirchhoff outputs are then not
+ *                             estimates; its Wilson counts and Kemeny's
+ *                             constant are unchanged.  Synchronises.
+ *   lap_batch_lv_row          out[u] = cnt2[u] / (omega d_u) for graph g
+ *                             (double[n[g]], host or device): row s of L_v^{-1}
+ *                             with a fixed start, y2(u) of Alg. 2 without.
+ */
+lap_status lap_batch_set_path_start(lap_batch *b, int32_t graph, int32_t start);
+lap_status lap_batch_lv_row(lap_batch *b, int32_t graph, double *out, int on_device);
+
 /* Graph g's node count, arc count, root and node offset in the result arrays. */
 lap_status lap_batch_graph_info(const lap_batch *b, int32_t graph, int32_t *n, int64_t *arcs, int32_t *root,
                                 int64_t *offset);

@@ -380,6 +380,7 @@ lap_status rerun_withdrawn(lap_batch *b, uint32_t count)
             p.num_sms = b->num_sms;
             p.ids = b->d_rerun_ids + jb.a;
             p.paths = b->paths_opt;
+            p.ustart = d.ustart;
             B_CUDA(b, lap_launch_sample(p, st));
         }
         for (int k = 0; k < kRerunStreams && k < (int)group.size(); ++k) {
@@ -950,6 +951,34 @@ lap_status lap_batch_counts(lap_batch *b, int32_t graph, uint64_t *cnt1, uint64_
         sums[2] = h.sum_y2;
         sums[3] = b->seed;
     }
+    B_CUDA(b, cudaStreamSynchronize(b->stream));
+    return LAP_OK;
+}
+
+lap_status lap_batch_set_path_start(lap_batch *b, int32_t graph, int32_t start)
+{
+    if (!b) return bfail(nullptr, LAP_ERR_INVALID_ARG, "NULL handle");
+    if (graph < 0 || graph >= b->G) return bfail(b, LAP_ERR_INVALID_ARG, "graph index out of range");
+    LapBatchGraph &d = b->h_graphs[(size_t)graph];
+    if (start < -1 || start >= d.n) return bfail(b, LAP_ERR_INVALID_ARG, "path start must be -1 or a node id of the graph");
+    d.ustart = start >= 0 ? (uint32_t)start + 1u : 0u;
+    // The kernels read the descriptors at run time: update the device copy.
+    B_CUDA(b, cudaMemcpyAsync(b->d_graphs + graph, &d, sizeof(d), cudaMemcpyHostToDevice, b->stream));
+    B_CUDA(b, cudaStreamSynchronize(b->stream));
+    return LAP_OK;
+}
+
+lap_status lap_batch_lv_row(lap_batch *b, int32_t graph, double *out, int on_device)
+{
+    lap_status s = finish(b);
+    if (s != LAP_OK) return s;
+    if (graph < 0 || graph >= b->G) return bfail(b, LAP_ERR_INVALID_ARG, "graph index out of range");
+    if (!out) return bfail(b, LAP_ERR_INVALID_ARG, "output pointer is NULL");
+    const LapBatchGraph &d = b->h_graphs[(size_t)graph];
+    double *dst = on_device ? out : reinterpret_cast<double *>(b->d_scratch);
+    B_CUDA(b, lap_launch_lv_row(d.rowinfo, d.n, b->omega, d.cnt2, dst, b->stream));
+    if (!on_device)
+        B_CUDA(b, cudaMemcpyAsync(out, dst, sizeof(double) * (size_t)d.n, cudaMemcpyDeviceToHost, b->stream));
     B_CUDA(b, cudaStreamSynchronize(b->stream));
     return LAP_OK;
 }

@@ -93,6 +93,17 @@ __global__ void rwb_kernel(int32_t n, const double *__restrict__ ldiag, const do
         out[u] = __dadd_rn(inv_n, __ddiv_rn(t, __dmul_rn(nm1, __dadd_rn(t, __dmul_rn((double)n, ldiag[u])))));
 }
 
+// out[u] = cnt2[u] / (omega d_u): with the first absorbed walk started at a
+// fixed s, the passes of u have mean d_u (L_v^{-1})_{su} (Section 4.2,
+// "v-absorbed walk" lemma), so this is row s of L_v^{-1}; with the uniform
+// start it is y2(u) of Alg. 2.
+__global__ void lv_row_kernel(const int2 *__restrict__ rowinfo, int32_t n, double omega,
+                              const unsigned long long *__restrict__ cnt2, double *out)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+        out[u] = y_of(cnt2[u], __dmul_rn(omega, (double)rowinfo[u].y));
+}
+
 __global__ void counts_kernel(int32_t n, int32_t root, unsigned long long omega,
                               const unsigned long long *__restrict__ rep1, unsigned long long *cnt1)
 {
@@ -236,5 +247,12 @@ cudaError_t lap_launch_rep_from_counts(int32_t n, int32_t root, uint64_t omega, 
 cudaError_t lap_launch_rw_betweenness(int32_t n, const double *ldiag, const double *red, double *out, cudaStream_t st)
 {
     rwb_kernel<<<grid_for(n), kBlock, 0, st>>>(n, ldiag, red + kParts + 1, out);
+    return cudaGetLastError();
+}
+
+cudaError_t lap_launch_lv_row(const int2 *rowinfo, int32_t n, uint64_t omega, const unsigned long long *cnt2,
+                              double *out, cudaStream_t st)
+{
+    lv_row_kernel<<<grid_for(n), kBlock, 0, st>>>(rowinfo, n, (double)omega, cnt2, out);
     return cudaGetLastError();
 }

@@ -333,7 +333,8 @@ lap_status lap_set_stream(lap_graph *g, void *cuda_stream)
 lap_status lap_set_option(lap_graph *g, int32_t option, int64_t value)
 {
     if (!g) return fail(nullptr, LAP_ERR_INVALID_ARG, "NULL handle");
-    if (value < 0) return fail(g, LAP_ERR_INVALID_ARG, "option value must be >= 0");
+    if (value < 0 && !(option == LAP_OPT_PATH_START && value == -1))
+        return fail(g, LAP_ERR_INVALID_ARG, "option value must be >= 0");
     switch (option) {
     case LAP_OPT_STEP_LIMIT:
         g->step_limit = value > (int64_t)(1ull << 62) ? (1ull << 62) : (uint64_t)value;
@@ -365,6 +366,11 @@ lap_status lap_set_option(lap_graph *g, int32_t option, int64_t value)
         if (g->omega != 0) return fail(g, LAP_ERR_INVALID_ARG, "the walk mode can only be set before the first sample after lap_set_root");
         if (g->paths_opt != (uint32_t)value) g->last_kernel = 0;     // the slot layout changes
         g->paths_opt = (uint32_t)value;
+        return LAP_OK;
+    case LAP_OPT_PATH_START:
+        if (value >= g->n) return fail(g, LAP_ERR_INVALID_ARG, "path start must be -1 or a node id");
+        if (g->omega != 0) return fail(g, LAP_ERR_INVALID_ARG, "the walk start can only be set before the first sample after lap_set_root");
+        g->path_start = (int32_t)value;
         return LAP_OK;
     default:
         return fail(g, LAP_ERR_INVALID_ARG, "unknown option");
@@ -539,6 +545,7 @@ static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, 
     p.block = g->block_opt;
     p.num_sms = g->num_sms;
     p.paths = g->paths_opt;
+    p.ustart = g->path_start >= 0 ? (uint32_t)g->path_start + 1u : 0u;
     p.y1_out = reinterpret_cast<unsigned long long *>(y1_dev);
     p.y2_out = reinterpret_cast<unsigned long long *>(y2_dev);
     p.m2_out = m2_dev;
@@ -588,6 +595,9 @@ static lap_status ensure_results(lap_graph *g)
     lap_status s = check_sticky(g);
     if (s != LAP_OK) return s;
     if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (g->path_start >= 0)
+        return fail(g, LAP_ERR_INVALID_ARG, "with a fixed walk start (LAP_OPT_PATH_START) the uniform-walk counts "
+                                            "estimate a row of L_v^{-1}, not the ECC terms: use lap_lv_row");
     if (g->omega == 0) return fail(g, LAP_ERR_NO_SAMPLES, "no samples drawn");
     if ((s = poll_status(g)) != LAP_OK) return s;
     if (!g->results_valid) {
@@ -645,6 +655,27 @@ lap_status lap_rw_betweenness(lap_graph *g, double *out, int out_on_device)
         LAP_CUDA(g, cudaStreamSynchronize(g->stream));
         return LAP_OK;
     }
+    return copy_out(g, out, g->d_aux, sizeof(double) * (size_t)g->n, 0);
+}
+
+lap_status lap_lv_row(lap_graph *g, double *out, int out_on_device)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (!out) return fail(g, LAP_ERR_INVALID_ARG, "output pointer is NULL");
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (g->omega == 0) return fail(g, LAP_ERR_NO_SAMPLES, "no samples drawn");
+    if ((s = poll_status(g)) != LAP_OK) return s;
+    if (out_on_device) {
+        LAP_CUDA(g, lap_launch_lv_row(g->d_rowinfo, g->n, g->omega, g->d_cnt2, out, g->stream));
+        LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+        return LAP_OK;
+    }
+    if (!g->d_aux && dalloc(&g->d_aux, (size_t)g->n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(g, LAP_ERR_OOM, "device allocation failed");
+    }
+    LAP_CUDA(g, lap_launch_lv_row(g->d_rowinfo, g->n, g->omega, g->d_cnt2, g->d_aux, g->stream));
     return copy_out(g, out, g->d_aux, sizeof(double) * (size_t)g->n, 0);
 }
 
@@ -994,6 +1025,8 @@ lap_status lap_cv_estimates(lap_graph *g, double beta1, double beta2, double *ld
     if (s != LAP_OK) return s;
     if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
     if (g->omega == 0) return fail(g, LAP_ERR_NO_SAMPLES, "no samples drawn");
+    if (g->path_start >= 0 && (ldiag || ecc))
+        return fail(g, LAP_ERR_INVALID_ARG, "with a fixed walk start (LAP_OPT_PATH_START) there are no ECC estimates");
     if ((s = poll_status(g)) != LAP_OK) return s;
     double *m2d = g->d_red + 1024 + 4;
     LAP_CUDA(g, cudaMemsetAsync(m2d, 0, sizeof(double), g->stream));

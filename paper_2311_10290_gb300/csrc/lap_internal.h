@@ -86,6 +86,8 @@ struct LapSampleLaunch {
     unsigned long long *cv_p2;
     double *m2_out;              // optional [count]: per-sample M2 (with y1_out)
     uint32_t flags;              // wide kernel: LAP_SAMPLE_* below
+    uint32_t ustart;             // 0: the first absorbed walk (or path) starts at a uniform draw
+                                 // (Alg. 2); s + 1: it starts at node s (single-source rows of L_v^{-1})
 };
 enum : uint32_t {
     LAP_SAMPLE_ONE_PER_LANE = 1u,   // lane j runs exactly sample first + j (j < count), so its
@@ -111,7 +113,7 @@ struct LapBatchGraph {
     int32_t n;
     int32_t root;
     uint32_t count;               // samples of the graph in the current run
-    uint32_t pad;
+    uint32_t ustart;              // as LapSampleLaunch::ustart, for this graph
 };
 
 // Control block of a batch launch (one cache line).
@@ -226,6 +228,8 @@ cudaError_t lap_launch_finalize(const int2 *rowinfo, int32_t n, int32_t root, ui
                                 const unsigned long long *rep1, const unsigned long long *cnt2,
                                 double *ldiag, double *ecc, double *red, cudaStream_t st);
 cudaError_t lap_launch_rw_betweenness(int32_t n, const double *ldiag, const double *red, double *out, cudaStream_t st);
+cudaError_t lap_launch_lv_row(const int2 *rowinfo, int32_t n, uint64_t omega, const unsigned long long *cnt2,
+                              double *out, cudaStream_t st);
 cudaError_t lap_launch_counts(int32_t n, int32_t root, uint64_t omega, const unsigned long long *rep1,
                               unsigned long long *cnt1, cudaStream_t st);
 cudaError_t lap_launch_rep_from_counts(int32_t n, int32_t root, uint64_t omega, const unsigned long long *cnt1,
@@ -247,7 +251,7 @@ struct lap_graph {
     double *d_ldiag = nullptr;
     double *d_ecc = nullptr;
     double *d_red = nullptr;                // reduction scratch
-    double *d_aux = nullptr;                // [n] random-walk betweenness (allocated on first use)
+    double *d_aux = nullptr;                // [n] random-walk betweenness, lap_lv_row (allocated on first use)
     unsigned int *d_slot_epoch = nullptr;   // per-slot epoch parity of the Wilson state
     uint64_t slot_epoch_cap = 0;
 
@@ -269,6 +273,7 @@ struct lap_graph {
     int block_opt = 0;
     int kernel_opt = 0;                     // 0 auto, LAP_KERNEL_WIDE, LAP_KERNEL_COMPACT
     uint32_t paths_opt = 0;                 // LAP_OPT_PATHS
+    int32_t path_start = -1;                // LAP_OPT_PATH_START (-1: uniform start)
     uint32_t stack_cap = 0;                 // 0: default, about 16 sqrt(n)
     int last_kernel = 0;                    // layout the workspace currently holds
     bool compact_disabled = false;          // set after a compact launch overflowed

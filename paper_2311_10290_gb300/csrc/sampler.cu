@@ -204,10 +204,11 @@ __global__ void __launch_bounds__(256) lewalk_kernel(LapSampleLaunch p)
                 phase = P_CLAIM;
                 continue;
             }
-            // Alg. 2: uniformly sample s in V; walk until v, counting passes.
+            // Alg. 2: uniformly sample s in V (or take the fixed start of a
+            // single-source row); walk until v, counting passes.
             t = 0;
-            const uint64_t r = lap::philox_r64(0u, 0u, i, 1u, key0, key1);
-            u = (int32_t)lap::below(r, (uint64_t)n);
+            u = p.ustart ? (int32_t)(p.ustart - 1u)
+                         : (int32_t)lap::below(lap::philox_r64(0u, 0u, i, 1u, key0, key1), (uint64_t)n);
             if (u == v) phase = P_PISTART;
             else {
                 if (p.paths) pa = st[u];

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
     unsigned long long *rep1 = nullptr, *cnt2 = nullptr;
     int64_t arcs = 0;
     uint64_t limit = 0;
-    uint32_t count_g = 0, unit_end = 0;
+    uint32_t count_g = 0, unit_end = 0, ustart = 0;
 
     uint32_t phase = P_CLAIM;
     uint32_t i = 0;
@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
         }
         if (phase == P_USTART_IMMEDIATE) {
             t = 0;
-            h = (int32_t)lap::below(lap::philox_r64(0u, 0u, i, 1u, key0, key1), (uint64_t)n);
+            h = ustart ? (int32_t)(ustart - 1u)
+                         : (int32_t)lap::below(lap::philox_r64(0u, 0u, i, 1u, key0, key1), (uint64_t)n);
             if (h != v) {
                 if (!PATHS) atomicAdd(&cnt2[h], 1ull);
                 pb = ld_row(rowinfo, h, keep);
@@ -289,6 +290,7 @@ __global__ void __launch_bounds__(256, 2) lewalk_batch_kernel(LapBatchLaunch p)
                     arcs = d->arcs;
                     limit = d->step_limit;
                     count_g = d->count;
+                    ustart = d->ustart;
                 }
                 i = u.y;
                 unit_end = u.y + p.claim < count_g ? u.y + p.claim : count_g;

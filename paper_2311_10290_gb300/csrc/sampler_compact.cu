@@ -176,9 +176,11 @@ __global__ void __launch_bounds__(256, CV ? 2 : 4) lewalk_compact_kernel(LapSamp
             phase = P_USTART_IMMEDIATE;
         }
         if (phase == P_USTART_IMMEDIATE) {
-            // Alg. 2: uniformly sample s in V; walk until v, counting passes.
+            // Alg. 2: uniformly sample s in V (or take the fixed start of a
+            // single-source row); walk until v, counting passes.
             t = 0;
-            h = (int32_t)lap::below(lap::philox_r64(0u, 0u, i, 1u, key0, key1), (uint64_t)n);
+            h = p.ustart ? (int32_t)(p.ustart - 1u)
+                         : (int32_t)lap::below(lap::philox_r64(0u, 0u, i, 1u, key0, key1), (uint64_t)n);
             if (h != v) {
                 if (!PATHS) atomicAdd(&p.cnt2[h], 1ull);
                 pb = ld_row(rowinfo, h, keep);

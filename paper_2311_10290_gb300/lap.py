@@ -27,6 +27,7 @@ STATUS = {
 }
 LAP_OPT_STEP_LIMIT, LAP_OPT_SLOTS, LAP_OPT_BLOCK, LAP_OPT_CURSOR, LAP_OPT_KERNEL, LAP_OPT_STACK = 1, 2, 3, 4, 5, 6
 LAP_OPT_PATHS = 7
+LAP_OPT_PATH_START = 8
 LAP_STAT_SLOTS, LAP_STAT_KERNEL, LAP_STAT_FALLBACKS = 1, 2, 3
 LAP_MLP_PARAMS = 4866
 LAP_BOPT_LANES, LAP_BOPT_CLAIM, LAP_BOPT_ORDER, LAP_BOPT_BLOCK, LAP_BOPT_STACK, LAP_BOPT_PATHS = 1, 2, 3, 4, 5, 6
@@ -68,6 +69,9 @@ def library():
         "lap_ecc": (i32, [vp, vp, ctypes.c_int]),
         "lap_ldiag": (i32, [vp, vp, ctypes.c_int]),
         "lap_kemeny": (i32, [vp, vp]),
+        "lap_lv_row": (i32, [vp, vp, ctypes.c_int]),
+        "lap_batch_set_path_start": (i32, [vp, i32, i32]),
+        "lap_batch_lv_row": (i32, [vp, i32, vp, ctypes.c_int]),
         "lap_counts": (i32, [vp, vp, vp, vp, ctypes.c_int]),
         "lap_hops": (i32, [vp, vp, ctypes.c_int]),
         "lap_set_counts": (i32, [vp, vp, vp, vp, ctypes.c_int]),
@@ -218,6 +222,10 @@ def lap_ecc(h, n, out=None):
 
 def lap_ldiag(h, n, out=None):
     return _out(h, library().lap_ldiag, n, np.float64, out)
+
+
+def lap_lv_row(h, n, out=None):
+    return _out(h, library().lap_lv_row, n, np.float64, out)
 
 
 def lap_hops(h, n, out=None):
@@ -483,6 +491,19 @@ def lap_batch_completion(h, n_graphs):
     return a
 
 
+def lap_batch_set_path_start(h, graph, start):
+    _bcheck(library().lap_batch_set_path_start(h, int(graph), int(start)), h)
+
+
+def lap_batch_lv_row(h, graph, n, out=None):
+    if out is not None and _is_torch(out):
+        _bcheck(library().lap_batch_lv_row(h, int(graph), _dp(out), 1), h)
+        return out
+    a = np.zeros(n) if out is None else out
+    _bcheck(library().lap_batch_lv_row(h, int(graph), _host_ptr(a), 0), h)
+    return a
+
+
 def lap_batch_counts(h, graph, n, per_node=True):
     """Host (cnt1, cnt2, sums {omega, sum Y1, sum Y2, seed}) of one graph;
     per_node=False reads only the sums."""
@@ -605,6 +626,9 @@ class LapGraph:
 
     def kemeny(self):
         return lap_kemeny(self.h)
+
+    def lv_row(self, out=None):
+        return lap_lv_row(self.h, self.n, out)
 
     def counts(self, per_node=True):
         return lap_counts(self.h, self.n, per_node)
@@ -738,6 +762,12 @@ class LapBatch:
 
     def counts(self, graph, per_node=True):
         return lap_batch_counts(self.h, graph, int(self.n[graph]), per_node)
+
+    def set_path_start(self, graph, start):
+        lap_batch_set_path_start(self.h, graph, start)
+
+    def lv_row(self, graph, out=None):
+        return lap_batch_lv_row(self.h, graph, int(self.n[graph]), out)
 
     def mean_wilson_steps(self):
         """Per graph: sum Y1 / omega, the estimate of Tr((I - P_v)^{-1}), the
