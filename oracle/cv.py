@@ -216,3 +216,80 @@ def finalize_cv(row_ptr, v, omega, cnt1, cnt2, sum_y1, sum_y2, z1, m2, beta1, be
     ecc = (n - 1) / (n * ld + tr)
     kc = ((float(sum_y1) - float(sum_y2)) + beta2 * m2) / w
     return ld, ecc, kc
+
+
+# ------------------------------------------- training targets and coefficients
+
+def training_targets(cnt1, omega, hit_sums, reps, sum_y2, v):
+    """Targets of the network's two heads for one graph (float32 [n, 2]):
+    t0(u) = cnt1(u) / omega, the mean number of Wilson visits of u, whose
+    expectation is d_u (L_v^{-1})_uu (Section 3.4, LE-walk lemma); t1(u) =
+    (hit_sums(u) / reps) / Ybar2 with Ybar2 = max(sum_y2 / omega, 1e-9), the
+    mean v-absorbed walk length from u (expectation h(u, v), Section 3.2)
+    over the estimate of E[Y2] = sum_u pi(u) h(u, v).  FP64, then rounded to
+    float32; the root's row is zero."""
+    c1 = np.asarray(cnt1, dtype=np.float64)
+    hit = np.asarray(hit_sums, dtype=np.float64)
+    mean_y2 = float(sum_y2) / float(omega)
+    if not mean_y2 > 1e-9:
+        mean_y2 = 1e-9
+    t = np.zeros((c1.size, 2), dtype=np.float64)
+    t[:, 0] = c1 / float(omega)
+    t[:, 1] = (hit / float(reps)) / mean_y2
+    t[v] = 0.0
+    return t.astype(np.float32)
+
+
+def potentials(y, row_ptr, v, scale2):
+    """Potentials from the network's outputs y [n, 2] (float32): phi1(u) =
+    y0(u) / d_u (the predicted visits per unit degree, ~ (L_v^{-1})_uu) and
+    phi2(u) = y1(u) * scale2 (the predicted hitting time; scale2 is the mean
+    pi-walk length the targets were divided by), phi2(v) = 0."""
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    d = (rp[1:] - rp[:-1]).astype(np.float64)
+    yy = np.asarray(y, dtype=np.float32).astype(np.float64)
+    phi1 = yy[:, 0] / d
+    phi2 = yy[:, 1] * float(scale2)
+    phi2[v] = 0.0
+    return phi1, phi2
+
+
+def betas_from_batches(V, Z, y, m):
+    """Least-squares coefficients of the two control variates.
+
+    V, Z: [batches, n] per-batch visits V_bu and martingale sums Z_bu =
+    Z1_b(u) / d_u.  The ECC estimator uses cnt1 - beta1 Z1/d, so beta1 is the
+    regression slope of V on Z pooled over nodes, each node centred on its
+    own batch mean: beta1 = sum_u cov_b(V_u, Z_u) / sum_u var_b(Z_u).
+    y, m: per-sample Y1 - Y2 and M2.  The Kemeny estimator uses y + beta2 m,
+    so beta2 = -cov(y, m) / var(m).  A zero denominator gives 0."""
+    V = np.asarray(V, dtype=np.float64)
+    Z = np.asarray(Z, dtype=np.float64)
+    Vc = V - V.mean(axis=0)
+    Zc = Z - Z.mean(axis=0)
+    den1 = float(np.sum(Zc * Zc))
+    beta1 = float(np.sum(Vc * Zc)) / den1 if den1 > 0 else 0.0
+    c = np.cov(np.asarray(y, dtype=np.float64), np.asarray(m, dtype=np.float64))
+    beta2 = -float(c[0, 1]) / float(c[1, 1]) if c[1, 1] > 0 else 0.0
+    return beta1, beta2
+
+
+def fit_betas(row_ptr, col, v, seed, first, per, batches, h1, h2):
+    """The coefficients from `batches` pilot batches of `per` samples with ids
+    first + b * per + [0, per) (the CPU sampler with both potentials), by
+    betas_from_batches."""
+    import oracle
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    d = rp[1:] - rp[:-1]
+    V, Z, ys, ms = [], [], [], []
+    for b in range(batches):
+        cnt, a1, _, _, m2 = oracle.sample_cv(row_ptr, col, v, seed, first + b * per, per, h1=h1, h2=h2)
+        z1 = martingale_z1(row_ptr, col, h1, cnt.cnt1, a1)
+        V.append(cnt.cnt1.astype(np.float64))
+        Z.append(z1.astype(np.float64) / d)
+        ys.append(cnt.y1.astype(np.int64) - cnt.y2.astype(np.int64))
+        ms.append(m2)
+    V, Z = np.array(V), np.array(Z)
+    V[:, v] = 0.0
+    Z[:, v] = 0.0
+    return betas_from_batches(V, Z, np.concatenate(ys), np.concatenate(ms))

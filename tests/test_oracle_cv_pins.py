@@ -240,3 +240,71 @@ def test_hitting_walks_estimate_the_hitting_times():
     s = I.star(30)
     sums = oracle.hitting_walks(s.row_ptr, s.col, 0, 5, 7)
     assert sums[0] == 0 and np.all(sums[1:] == 7)
+
+
+def test_betas_recover_exact_linear_relations():
+    """Noise-free data on a line: V = c_u + 2.5 Z (an offset per node, which
+    the per-node centring removes) gives beta1 = 2.5; y = 7 - 1.5 m gives
+    beta2 = 1.5 (the Kemeny variate enters as + beta2 m).  Constant Z or m
+    give 0."""
+    rng = np.random.default_rng(3)
+    Z = rng.standard_normal((6, 40))
+    V = rng.uniform(0, 100, 40)[None, :] + 2.5 * Z
+    m = rng.standard_normal(500)
+    y = 7.0 - 1.5 * m
+    b1, b2 = CV.betas_from_batches(V, Z, y, m)
+    assert b1 == pytest.approx(2.5, rel=1e-13) and b2 == pytest.approx(1.5, rel=1e-13)
+    b1, b2 = CV.betas_from_batches(V, np.ones((6, 40)), y, np.full(500, 3.0))
+    assert b1 == 0.0 and b2 == 0.0
+
+
+def test_fitted_beta2_with_the_hitting_time_potential_is_one_unit():
+    """With h2 = round(2^16 h(., v)), Y2 - 2^-16 M2 is the start's hitting
+    time, and the visits of the (independent) Wilson run do not depend on
+    M2, so the least-squares beta2 is 2^-16 (one unit of the fixed-point
+    potential) up to sampling error (about 0.5% here)."""
+    g = I.ba(400, 2, seed=7)
+    v = oracle.root_max_degree(g.row_ptr)
+    h2 = CV.quantize_potential(D.hitting_times_to(g.n, g.row_ptr, g.col, v))
+    h1 = np.random.default_rng(0).integers(0, 2 ** 16, size=g.n)
+    b1, b2 = CV.fit_betas(g.row_ptr, g.col, v, 5, 1 << 20, 500, 8, h1, h2)
+    assert b2 * 2.0 ** CV.FIXED_POINT_BITS == pytest.approx(1.0, abs=0.05)
+    assert np.isfinite(b1)
+
+
+def test_targets_and_potentials_on_exact_expectations_give_the_estimands():
+    """Fed the exact expectations (visits d_u (L_v^{-1})_uu per sample,
+    hitting times h(u, v) per walk, E[Y2] = (1/2m) d^T L_v^{-1} d per
+    sample), the targets are d_u (L_v^{-1})_uu and h(u, v) / E[Y2], and the
+    potentials made from them with scale E[Y2] are (L_v^{-1})_uu and h(u, v)
+    (float32 rounding of the targets: 1e-7)."""
+    g = I.er(30, 0.2, seed=1)
+    v = oracle.root_max_degree(g.row_ptr)
+    e = D.expectations(g.n, g.row_ptr, g.col, v)
+    hit = D.hitting_times_to(g.n, g.row_ptr, g.col, v)
+    omega, reps = 1000, 16
+    t = CV.training_targets(e["visits"] * omega, omega, hit * reps, reps, e["y2"] * omega, v)
+    lv = D.lv_inverse(g.n, g.row_ptr, g.col, v)
+    d = g.degree.astype(np.float64)
+    keep = np.arange(g.n) != v
+    np.testing.assert_allclose(t[keep, 0], (d * np.diag(lv))[keep], rtol=1e-6)
+    np.testing.assert_allclose(t[keep, 1], (hit / e["y2"])[keep], rtol=1e-6)
+    assert np.all(t[v] == 0.0)
+    phi1, phi2 = CV.potentials(t, g.row_ptr, v, e["y2"])
+    np.testing.assert_allclose(phi1[keep], np.diag(lv)[keep], rtol=1e-6)
+    np.testing.assert_allclose(phi2, hit, rtol=1e-6, atol=0)
+    assert phi2[v] == 0.0
+
+
+def test_targets_on_a_hub_rooted_star_are_exact():
+    """Rooted at the hub of a star, every leaf is visited exactly once per
+    sample and every hitting walk from a leaf takes one step: t0 = 1 and
+    t1 = 1 / (sum Y2 / omega) exactly."""
+    g = I.star(40)
+    omega, reps = 300, 4
+    c = oracle.sample(g.row_ptr, g.col, 0, 3, 0, omega)
+    hit = oracle.hitting_walks(g.row_ptr, g.col, 0, 4, reps)
+    t = CV.training_targets(c.cnt1, omega, hit, reps, c.sum_y2, 0)
+    assert np.all(t[1:, 0] == 1.0)
+    assert np.all(t[1:, 1] == np.float32(1.0 / (c.sum_y2 / omega)))
+    assert np.all(t[0] == 0.0)

@@ -95,6 +95,15 @@ MUTATIONS = [
     ("martingale_z1_sign", "cv.py",
      "    return d * np.asarray(a1, dtype=np.int64) - np.asarray(cnt1, dtype=np.int64) * s1",
      "    return d * np.asarray(a1, dtype=np.int64) + np.asarray(cnt1, dtype=np.int64) * s1", CV_PINS),
+    ("beta1_variate_not_centred", "cv.py",
+     "    Zc = Z - Z.mean(axis=0)",
+     "    Zc = Z", CV_PINS),
+    ("beta2_sign", "cv.py",
+     "    beta2 = -float(c[0, 1]) / float(c[1, 1]) if c[1, 1] > 0 else 0.0",
+     "    beta2 = float(c[0, 1]) / float(c[1, 1]) if c[1, 1] > 0 else 0.0", CV_PINS),
+    ("hitting_target_not_divided_by_reps", "cv.py",
+     "    t[:, 1] = (hit / float(reps)) / mean_y2",
+     "    t[:, 1] = hit / mean_y2", CV_PINS),
     ("cv_kemeny_term_sign", "cv.py",
      "    kc = ((float(sum_y1) - float(sum_y2)) + beta2 * m2) / w",
      "    kc = ((float(sum_y1) - float(sum_y2)) - beta2 * m2) / w", CV_PINS),
