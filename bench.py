@@ -394,11 +394,21 @@ def cv_train(torch, LapGraph, count):
 def cv_prepare(G, params, seed, pilot, batches):
     """Potentials from the network, coefficients from pilot samples (disjoint ids)."""
     from paper_2311_10290_gb300 import cv as CVG
-    mean_y2 = CVG.pilot_mean_y2(G, seed + 1, samples=min(pilot, 4096))
-    phi1, phi2 = CVG.potentials(G, params, mean_y2)
+    phi1, phi2 = CVG.pilot_potentials(G, params, seed + 1, samples=min(pilot, 4096))
     beta1, beta2 = CVG.fit_betas(G, phi1, phi2, seed=seed, pilot=pilot, batches=batches)
-    G.cv_set_potentials(phi1, phi2)
     return phi1, phi2, beta1, beta2
+
+
+def _neighbour_sums_of_potential(g, phi1):
+    """Measurement helper: S1(u) = sum over N(u) of round(2^16 phi1), the
+    neighbour sums the library forms for its Wilson-draw variate, to split the
+    per-batch visit counts into their control-variate parts."""
+    h = np.rint(np.ldexp(phi1.cpu().numpy(), 16)).astype(np.int64)
+    rp = g.row_ptr.astype(np.int64)
+    src = np.repeat(np.arange(g.n), rp[1:] - rp[:-1])
+    out = np.zeros(g.n, dtype=np.int64)
+    np.add.at(out, src, h[g.col])
+    return out.astype(np.float64)
 
 
 def cv_measurement(torch, LapGraph, g, v, params, samples_per_batch, batches):
@@ -406,7 +416,6 @@ def cv_measurement(torch, LapGraph, g, v, params, samples_per_batch, batches):
     Kemeny from per-sample traces; ECC from per-node variances of the visit
     estimator between `batches` independent batches.  The coefficients come
     from separate pilot samples, so both estimators stay unbiased."""
-    from paper_2311_10290_gb300.cv import _neighbour_sum_host
     from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, lap_counts
     free, _ = torch.cuda.mem_get_info()
     G = LapGraph(g.row_ptr, g.col, workspace_bytes=int(free * 0.5))
@@ -424,7 +433,7 @@ def cv_measurement(torch, LapGraph, g, v, params, samples_per_batch, batches):
         G.set_root(v)
         G.set_option(LAP_OPT_CURSOR, samples_per_batch)          # ids after the Kemeny trace's
         d = np.diff(g.row_ptr.astype(np.int64)).astype(np.float64)
-        s1 = _neighbour_sum_host(G, phi1)
+        s1 = _neighbour_sums_of_potential(g, phi1)
         prev_c, prev_a = np.zeros(g.n), np.zeros(g.n)
         V, Z = [], []
         for _ in range(batches):

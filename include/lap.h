@@ -330,6 +330,54 @@ lap_status lap_features(lap_graph *g, float *feat_dev);
  * estimates h(u, v) = (L_v^{-1} d)_u.  Synchronises. */
 lap_status lap_hitting_walks(lap_graph *g, uint32_t reps, uint64_t seed, uint64_t *sums_dev);
 
+/*
+ * Training targets of the control variate's network for one graph (device
+ * float[n][2]), from the samples drawn since lap_set_root and `reps`
+ * v-absorbed walks from every node (lap_hitting_walks with `seed`):
+ *   targets[u][0] = cnt1[u] / omega            (mean Wilson visits, d_u (L_v^{-1})_uu;
+ *                                               LE-walk lemma of Section 3.4)
+ *   targets[u][1] = (walk sum[u] / reps) / Ybar2 (hitting time h(u, v), Section 3.2,
+ *                                               over Ybar2 = max(sum Y2 / omega, 1e-9),
+ *                                               the estimate of E[Y2] = sum_u pi(u) h(u, v))
+ * Both are computed in FP64 and rounded to float; row v is zero (leave it
+ * out of training).  Synchronises.  Errors: LAP_ERR_NO_ROOT,
+ * LAP_ERR_NO_SAMPLES, LAP_ERR_INVALID_ARG, LAP_ERR_STEP_LIMIT, LAP_ERR_OOM.
+ */
+lap_status lap_cv_targets(lap_graph *g, uint32_t reps, uint64_t seed, float *targets_dev);
+
+/*
+ * Potentials from the network's outputs y_dev[n][2] (device float, as
+ * lap_mlp_forward writes them for the node features):
+ *   phi1[u] = y[u][0] / d_u                 (~ (L_v^{-1})_uu),
+ *   phi2[u] = y[u][1] * (sum Y2 / omega)    (~ h(u, v)), phi2[v] = 0,
+ * the scale being the mean pi-walk length of the samples drawn since
+ * lap_set_root (draw a few pilot samples first, e.g. at LAP_OPT_CURSOR ids
+ * kept apart from the estimate's).  Device double[n] outputs, either may be
+ * NULL (phi2 then needs no samples).  Synchronises.
+ */
+lap_status lap_cv_potentials(lap_graph *g, const float *y_dev, double *phi1_dev, double *phi2_dev);
+
+/*
+ * Coefficients of the two control variates from pilot samples, so that they
+ * do not depend on the samples of the estimate (which keeps it unbiased):
+ * sets the potentials (as lap_cv_set_potentials; either may be NULL), draws
+ * `batches` batches of pilot / batches samples with ids from first_id on,
+ * then
+ *   beta1 = sum_u sum_b (V_bu - Vbar_u)(Z_bu - Zbar_u) / sum_u sum_b (Z_bu - Zbar_u)^2,
+ *           V_bu = visits of u in batch b, Z_bu = Z1_b(u) / d_u (least squares
+ *           of the ECC variate, pooled over nodes; 0 without phi1),
+ *   beta2 = -cov(Y1 - Y2, M2) / var(M2) over the pilot samples (least
+ *           squares of the Kemeny variate; 0 without phi2),
+ * and resets the handle as lap_set_root does (counts and cursor cleared, the
+ * potentials kept).  Needs lap_set_root and no sample drawn since;
+ * 2 <= batches <= 64, 1 <= pilot / batches <= 2^24, ids below 2^32.
+ * Synchronises; allocates and frees temporary device buffers (16 n batches +
+ * 24 pilot bytes).  Errors: LAP_ERR_NO_ROOT, LAP_ERR_INVALID_ARG,
+ * LAP_ERR_TOO_LARGE, LAP_ERR_OOM, LAP_ERR_STEP_LIMIT, LAP_ERR_CUDA.
+ */
+lap_status lap_cv_fit_betas(lap_graph *g, const double *phi1_dev, const double *phi2_dev, uint64_t seed,
+                            uint64_t first_id, uint64_t pilot, uint32_t batches, double *beta1, double *beta2);
+
 /* Potentials phi1 (Wilson draws, ECC) and phi2 (pi walks, Kemeny) as device
  * double[n]; either may be NULL (that term off).  They are quantised to
  * h = round(2^16 phi).  Only before the first sample after lap_set_root;

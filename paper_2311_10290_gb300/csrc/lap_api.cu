@@ -975,6 +975,128 @@ lap_status lap_hitting_walks(lap_graph *g, uint32_t reps, uint64_t seed, uint64_
     return LAP_OK;
 }
 
+lap_status lap_cv_targets(lap_graph *g, uint32_t reps, uint64_t seed, float *targets_dev)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (!targets_dev || reps == 0) return fail(g, LAP_ERR_INVALID_ARG, "targets_dev must be set and reps >= 1");
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (g->omega == 0) return fail(g, LAP_ERR_NO_SAMPLES, "no samples drawn");
+    if ((s = poll_status(g)) != LAP_OK) return s;
+    if (!g->d_aux && dalloc(&g->d_aux, (size_t)g->n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(g, LAP_ERR_OOM, "device allocation failed");
+    }
+    uint64_t *hit = reinterpret_cast<uint64_t *>(g->d_aux);
+    if ((s = lap_hitting_walks(g, reps, seed, hit)) != LAP_OK) return s;
+    LapDevAcc h;
+    LAP_CUDA(g, cudaMemcpyAsync(&h, g->d_acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    // E[Y2] estimated from the samples drawn; kept away from 0 for graphs
+    // whose pi-walks all start at the root.
+    double mean_y2 = (double)h.sum_y2 / (double)g->omega;
+    if (!(mean_y2 > 1e-9)) mean_y2 = 1e-9;
+    LAP_CUDA(g, lap_launch_cv_targets(g->n, g->root, g->omega, g->d_rep1,
+                                      reinterpret_cast<const unsigned long long *>(hit), reps, mean_y2, targets_dev,
+                                      g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    return LAP_OK;
+}
+
+lap_status lap_cv_potentials(lap_graph *g, const float *y_dev, double *phi1_dev, double *phi2_dev)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (!y_dev || (!phi1_dev && !phi2_dev)) return fail(g, LAP_ERR_INVALID_ARG, "y_dev and one output must be set");
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    double scale2 = 0.0;
+    if (phi2_dev) {
+        if (g->omega == 0) return fail(g, LAP_ERR_NO_SAMPLES, "phi2 is scaled by the mean Y2 of the samples drawn: none drawn");
+        if ((s = poll_status(g)) != LAP_OK) return s;
+        LapDevAcc h;
+        LAP_CUDA(g, cudaMemcpyAsync(&h, g->d_acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+        LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+        scale2 = (double)h.sum_y2 / (double)g->omega;
+    }
+    LAP_CUDA(g, lap_launch_cv_potentials(g->d_rowinfo, g->n, g->root, y_dev, scale2, phi1_dev, phi2_dev, g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    return LAP_OK;
+}
+
+lap_status lap_cv_fit_betas(lap_graph *g, const double *phi1_dev, const double *phi2_dev, uint64_t seed,
+                            uint64_t first_id, uint64_t pilot, uint32_t batches, double *beta1, double *beta2)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (!beta1 || !beta2 || (!phi1_dev && !phi2_dev)) return fail(g, LAP_ERR_INVALID_ARG, "beta outputs and one potential must be set");
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (g->omega != 0) return fail(g, LAP_ERR_INVALID_ARG, "the pilot batches must be the first samples after lap_set_root");
+    if (batches < 2 || batches > 64) return fail(g, LAP_ERR_INVALID_ARG, "batches must be in [2, 64]");
+    const uint64_t per = pilot / batches;
+    if (per < 1 || per > (1ull << 24)) return fail(g, LAP_ERR_INVALID_ARG, "pilot / batches must be in [1, 2^24]");
+    const uint64_t total = per * batches;
+    if (first_id >= (1ull << 32) || total > (1ull << 32) - first_id)
+        return fail(g, LAP_ERR_TOO_LARGE, "pilot sample ids must lie below 2^32");
+    const int32_t root = g->root;
+    const size_t n = (size_t)g->n;
+    if ((s = lap_cv_set_potentials(g, phi1_dev, phi2_dev)) != LAP_OK) return s;
+    g->cursor = first_id;
+
+    double *vb = nullptr, *zb = nullptr, *m2 = nullptr, *red = nullptr;
+    long long *prev = nullptr;
+    unsigned long long *y1 = nullptr, *y2 = nullptr;
+    auto release = [&]() {
+        cudaStreamSynchronize(g->stream);
+        cudaFree(vb); cudaFree(zb); cudaFree(m2); cudaFree(red); cudaFree(prev); cudaFree(y1); cudaFree(y2);
+    };
+    bool ok = dalloc(&y1, (size_t)total) == cudaSuccess && dalloc(&y2, (size_t)total) == cudaSuccess &&
+              dalloc(&red, 2 * 1024 + 8) == cudaSuccess;
+    if (ok && phi2_dev) ok = dalloc(&m2, (size_t)total) == cudaSuccess;
+    if (ok && phi1_dev)
+        ok = dalloc(&vb, n * batches) == cudaSuccess && dalloc(&zb, n * batches) == cudaSuccess &&
+             dalloc(&prev, 2 * n) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        release();
+        return fail(g, LAP_ERR_OOM, "pilot buffers: device allocation failed");
+    }
+    if (cudaMemsetAsync(red, 0, sizeof(double) * (2 * 1024 + 8), g->stream) != cudaSuccess ||
+        (prev && cudaMemsetAsync(prev, 0, sizeof(long long) * 2 * n, g->stream) != cudaSuccess)) {
+        release();
+        return fail(g, LAP_ERR_CUDA, "cudaMemsetAsync failed");
+    }
+    for (uint32_t b = 0; b < batches && s == LAP_OK; ++b) {
+        s = sample_chunk(g, per, seed, reinterpret_cast<uint64_t *>(y1 + b * per),
+                         reinterpret_cast<uint64_t *>(y2 + b * per), m2 ? m2 + b * per : nullptr);
+        if (s == LAP_OK) s = resolve_pending(g);      // re-runs of withdrawn samples complete the batch
+        if (s == LAP_OK && phi1_dev) {
+            const cudaError_t e = lap_launch_beta1_batch(g->d_rowinfo, g->n, root, g->omega, g->d_rep1,
+                                                         reinterpret_cast<const long long *>(g->d_cv_a1), g->d_cv_S1,
+                                                         prev, prev + n, vb + b * n, zb + b * n, g->stream);
+            if (e != cudaSuccess) s = cuda_fail(g, e, "beta1 batch");
+        }
+    }
+    if (s == LAP_OK) s = poll_status(g);
+    double out[4] = {0.0, 0.0, 0.0, 0.0};
+    if (s == LAP_OK) {
+        cudaError_t e = cudaSuccess;
+        if (phi1_dev) e = lap_launch_beta1_reduce(g->n, (int32_t)batches, vb, zb, red, red + 2 * 1024 + 2, g->stream);
+        if (e == cudaSuccess && phi2_dev) e = lap_launch_beta2_reduce(y1, y2, m2, (int64_t)total, red, red + 2 * 1024 + 4, g->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, red + 2 * 1024 + 2, sizeof(out), cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) s = cuda_fail(g, e, "beta reductions");
+    }
+    release();
+    if (s != LAP_OK) return s;
+    // Least squares: beta1 = cov(V, Z1/d) / var(Z1/d) pooled over nodes;
+    // beta2 = -cov(Y1 - Y2, M2) / var(M2) (the Kemeny CV adds + beta2 M2).
+    *beta1 = out[1] > 0.0 ? out[0] / out[1] : 0.0;
+    *beta2 = out[3] > 0.0 ? -out[2] / out[3] : 0.0;
+    // Back to the state after lap_set_root, the potentials kept: the pilot
+    // samples are not part of any estimate.
+    return lap_set_root(g, root, nullptr);
+}
+
 lap_status lap_cv_set_potentials(lap_graph *g, const double *phi1_dev, const double *phi2_dev)
 {
     lap_status s = check_sticky(g);

@@ -218,6 +218,18 @@ cudaError_t lap_launch_cv_finalize(const int2 *rowinfo, int32_t n, int32_t root,
                                    const long long *a1, const long long *S1, double beta1,
                                    const long long *a2, const long long *p2, const long long *S2,
                                    double *ldiag, double *ecc, double *red, double *m2_out, cudaStream_t st);
+cudaError_t lap_launch_cv_targets(int32_t n, int32_t root, uint64_t omega, const unsigned long long *rep1,
+                                  const unsigned long long *hit, uint32_t reps, double mean_y2, float *targets,
+                                  cudaStream_t st);
+cudaError_t lap_launch_cv_potentials(const int2 *rowinfo, int32_t n, int32_t root, const float *y, double scale2,
+                                     double *phi1, double *phi2, cudaStream_t st);
+cudaError_t lap_launch_beta1_batch(const int2 *rowinfo, int32_t n, int32_t root, uint64_t omega,
+                                   const unsigned long long *rep1, const long long *a1, const long long *S1,
+                                   long long *prev_c1, long long *prev_a1, double *vb, double *zb, cudaStream_t st);
+cudaError_t lap_launch_beta1_reduce(int32_t n, int32_t batches, const double *vb, const double *zb, double *red,
+                                    double *out, cudaStream_t st);
+cudaError_t lap_launch_beta2_reduce(const unsigned long long *y1, const unsigned long long *y2, const double *m2,
+                                    int64_t count, double *red, double *out, cudaStream_t st);
 cudaError_t lap_launch_mlp(const float *P, const float *X, const float *T, int64_t n, float wk0, float wk1,
                            float *Y, float *G, float *loss, cudaStream_t st);
 cudaError_t lap_launch_adamw(float *w, float *m, float *v, const float *g, int64_t count, int32_t step, float lr,

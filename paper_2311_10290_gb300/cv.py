@@ -3,26 +3,29 @@
 The paper has no control variate.  This module trains the MLP
 (8 node features -> 64 -> 64 -> 2) whose outputs become the potentials of the
 martingale control variates in include/lap.h (lap_cv_set_potentials), fits
-the two coefficients on pilot samples, and applies them.  Every numeric step
-runs in the CUDA library: features (lap_features), targets (lap_sample and
-lap_hitting_walks), the network's forward/backward on BF16 tensor cores
-(lap_mlp_forward, lap_mlp_loss_grad), AdamW (lap_adamw) and the estimators
-(lap_cv_estimates).  This module only moves data and chooses hyperparameters.
+the two coefficients on pilot samples, and applies them.  It only sequences
+calls of the CUDA library and moves data between them; every value of the
+method is computed there: features (lap_features), training targets
+(lap_sample, lap_cv_targets), the network's forward/backward on BF16 tensor
+cores (lap_mlp_forward, lap_mlp_loss_grad), AdamW (lap_adamw), potentials
+(lap_cv_potentials), coefficients (lap_cv_fit_betas) and the estimators
+(lap_cv_estimates).  What stays here: the training schedule (epochs,
+minibatches of a once-shuffled row order, a cosine learning rate) and the
+parameter initialisation.
 
-Targets, produced by the sampler itself on generated graphs:
-  head 0: t0(u) = cnt1[u] / omega     (expected Wilson visits, d_u (L_v^{-1})_uu)
-  head 1: t1(u) = hit(u) / mean Y2    (hitting time h(u, v) from v-absorbed
-                                       walks, divided by E[Y2] = sum pi h)
-Potentials:  phi1(w) = pred0(w) / d_w  (~ (L_v^{-1})_ww) for the Wilson draws,
-             phi2(w) = pred1(w) * mean Y2 (~ h(w, v)), phi2(v) = 0, for the
-             pi-start walks.
+Targets, produced by the sampler itself on generated graphs (lap_cv_targets):
+  head 0: cnt1[u] / omega     (expected Wilson visits, d_u (L_v^{-1})_uu)
+  head 1: hit(u) / mean Y2    (hitting time h(u, v) from v-absorbed walks,
+                               divided by the estimate of E[Y2] = sum pi h)
+Potentials (lap_cv_potentials): phi1 = pred0 / d (~ (L_v^{-1})_ww) for the
+Wilson draws, phi2 = pred1 * mean Y2 (~ h(w, v)), phi2(v) = 0, for the
+pi-start walks.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from .lap import (LAP_MLP_PARAMS, LAP_OPT_CURSOR, LapGraph, lap_adamw, lap_counts, lap_mlp_forward,
-                  lap_mlp_loss_grad)
+from .lap import LAP_MLP_PARAMS, LAP_OPT_CURSOR, LapGraph, lap_adamw, lap_mlp_forward, lap_mlp_loss_grad
 
 N_FEAT, N_OUT = 8, 2
 PILOT_CURSOR = 1 << 31          # pilot sample ids never overlap the estimate's ids
@@ -42,20 +45,13 @@ def init_params(seed=0):
 
 def training_targets(G: LapGraph, omega=512, reps=16, seed=7):
     """(features [n, 8], targets [n, 2], mask of usable rows) for one graph
-    whose root is set; all produced by the library's kernels."""
-    import torch
-    v = G.root
+    whose root is set; all produced by the library's kernels.  The root's
+    row is left out (its targets are zero by definition)."""
     G.sample(omega, seed)
-    c1, _, sums = lap_counts(G.h, G.n)
-    hit = G.hitting_walks(reps, seed + 1).cpu().numpy().astype(np.float64) / reps
-    mean_y2 = max(float(sums[2]) / omega, 1e-9)
-    t = np.zeros((G.n, 2), dtype=np.float32)
-    t[:, 0] = c1.astype(np.float64) / omega
-    t[:, 1] = hit / mean_y2
+    t = G.cv_targets(reps, seed + 1)
     mask = np.ones(G.n, dtype=bool)
-    mask[v] = False
-    feats = G.features()
-    return feats, torch.from_numpy(t).cuda(), mask
+    mask[G.root] = False
+    return G.features(), t, mask
 
 
 def train(datasets, epochs=8, batch=8192, lr=3e-3, weight_decay=1e-4, seed=0, weights=(1.0, 1.0), log=None):
@@ -104,81 +100,24 @@ def predict(G: LapGraph, params):
     return y
 
 
-def potentials(G: LapGraph, params, mean_y2):
-    """phi1 ~ (L_v^{-1})_ww and phi2 ~ h(w, v) from the network (float64, CUDA)."""
-    import torch
-    y = predict(G, params).double()
-    deg = torch.from_numpy(np.diff(G.row_ptr_host.astype(np.int64)).astype(np.float64)).cuda()
-    phi1 = (y[:, 0] / deg).contiguous()
-    phi2 = (y[:, 1] * float(mean_y2)).contiguous()
-    phi2[G.root] = 0.0
-    return phi1, phi2
-
-
-def pilot_mean_y2(G: LapGraph, seed, samples=2048):
-    """Mean pi-start walk length E[Y2] from pilot samples whose ids (from
-    PILOT_CURSOR + 2^30) are disjoint from both the estimate's and fit_betas';
-    resets the root (counts and cursor) afterwards."""
+def pilot_potentials(G: LapGraph, params, seed, samples=2048):
+    """phi1 ~ (L_v^{-1})_ww and phi2 ~ h(w, v) (float64 CUDA tensors) from the
+    network, phi2 scaled by the mean pi-walk length of `samples` pilot samples
+    whose ids (from PILOT_CURSOR + 2^30) are disjoint from both the estimate's
+    and fit_betas'; resets the root (counts and cursor) afterwards."""
     root = G.root
     G.set_root(root)
     G.set_option(LAP_OPT_CURSOR, PILOT_CURSOR + (1 << 30))
-    _, y2 = G.sample_trace(samples, seed)
+    G.sample(samples, seed)
+    phi1, phi2 = G.cv_potentials(predict(G, params))
     G.set_root(root)
-    return float(y2.double().mean().item())
+    return phi1, phi2
 
 
 def fit_betas(G: LapGraph, phi1, phi2, seed, pilot=4096, batches=8):
     """Coefficients from pilot samples (ids from PILOT_CURSOR, disjoint from the
-    estimate's): beta2 minimises Var(Y1 - Y2 + beta2 M2) over per-sample
-    traces; beta1 pools, over nodes, per-node covariances of the visit count
-    with Z1/d between `batches` independent pilot batches."""
-    import torch
-    root = G.root
-    G.set_root(root)
-    G.set_option(LAP_OPT_CURSOR, PILOT_CURSOR)
-    G.cv_set_potentials(phi1, phi2)
-    d = np.diff(G.row_ptr_host.astype(np.int64)).astype(np.float64)
-    per = max(1, pilot // batches)
-    ys, ms = [], []
-    prev_c1 = np.zeros(G.n)
-    prev_a1 = np.zeros(G.n)
-    vis, zed = [], []
-    from .lap import lap_counts as counts
-    s1 = None
-    for b in range(batches):
-        y1, y2, m2 = G.sample_trace_cv(per, seed)
-        ys.append((y1 - y2).double().cpu().numpy())
-        ms.append(m2.cpu().numpy())
-        c1, _, _ = counts(G.h, G.n)
-        a1, _, _ = G.cv_sums()
-        c1 = c1.astype(np.float64)
-        a1 = a1.astype(np.float64)
-        if s1 is None:
-            s1 = _neighbour_sum_host(G, phi1)
-        dc1 = c1 - prev_c1
-        da1 = a1 - prev_a1
-        prev_c1, prev_a1 = c1, a1
-        vis.append(dc1)
-        zed.append((d * da1 - dc1 * s1) / d)
-    y = np.concatenate(ys)
-    m = np.concatenate(ms)
-    c = np.cov(y, m)
-    beta2 = -c[0, 1] / c[1, 1] if c[1, 1] > 0 else 0.0
-    V = np.array(vis)
-    Z = np.array(zed)
-    Vc = V - V.mean(axis=0)
-    Zc = Z - Z.mean(axis=0)
-    num = float(np.sum(Vc * Zc))
-    den = float(np.sum(Zc * Zc))
-    beta1 = num / den if den > 0 else 0.0
-    G.set_root(root)
-    return float(beta1), float(beta2)
-
-
-def _neighbour_sum_host(G, phi1):
-    h = np.rint(np.ldexp(phi1.cpu().numpy(), 16)).astype(np.int64)
-    rp = G.row_ptr_host.astype(np.int64)
-    src = np.repeat(np.arange(G.n), rp[1:] - rp[:-1])
-    out = np.zeros(G.n, dtype=np.int64)
-    np.add.at(out, src, h[G.col_host])
-    return out.astype(np.float64)
+    estimate's), computed by lap_cv_fit_betas: beta2 minimises the variance of
+    Y1 - Y2 + beta2 M2 over the per-sample traces; beta1 pools, over nodes,
+    per-node covariances of the visit count with Z1/d between `batches`
+    pilot batches.  Leaves the handle reset with the potentials set."""
+    return G.cv_fit_betas(phi1, phi2, seed, PILOT_CURSOR, pilot, batches)

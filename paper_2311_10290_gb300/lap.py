@@ -88,6 +88,10 @@ def library():
         "lap_features": (i32, [vp, vp]),
         "lap_hitting_walks": (i32, [vp, ctypes.c_uint32, u64, vp]),
         "lap_cv_set_potentials": (i32, [vp, vp, vp]),
+        "lap_cv_targets": (i32, [vp, ctypes.c_uint32, u64, vp]),
+        "lap_cv_potentials": (i32, [vp, vp, vp, vp]),
+        "lap_cv_fit_betas": (i32, [vp, vp, vp, u64, u64, u64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]),
         "lap_cv_sums": (i32, [vp, vp, vp, vp, ctypes.c_int]),
         "lap_cv_estimates": (i32, [vp, ctypes.c_double, ctypes.c_double, vp, vp, ctypes.c_int, vp, vp]),
         "lap_sample_trace_cv": (i32, [vp, u64, u64, vp, vp, vp]),
@@ -341,6 +345,24 @@ def lap_hitting_walks(h, reps, seed, sums_dev):
 def lap_cv_set_potentials(h, phi1_dev=None, phi2_dev=None):
     """phi1_dev, phi2_dev: float64 CUDA tensors [n] or None."""
     _check(library().lap_cv_set_potentials(h, _dp(phi1_dev), _dp(phi2_dev)), h)
+
+
+def lap_cv_targets(h, reps, seed, targets_dev):
+    """targets_dev: float32 CUDA tensor [n, 2] (overwritten)."""
+    _check(library().lap_cv_targets(h, int(reps), int(seed), _dp(targets_dev)), h)
+
+
+def lap_cv_potentials(h, y_dev, phi1_dev=None, phi2_dev=None):
+    """y_dev: float32 CUDA tensor [n, 2]; phi1_dev, phi2_dev: float64 CUDA tensors [n] or None."""
+    _check(library().lap_cv_potentials(h, _dp(y_dev), _dp(phi1_dev), _dp(phi2_dev)), h)
+
+
+def lap_cv_fit_betas(h, phi1_dev, phi2_dev, seed, first_id, pilot, batches):
+    """Returns (beta1, beta2)."""
+    b1, b2 = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(library().lap_cv_fit_betas(h, _dp(phi1_dev), _dp(phi2_dev), int(seed), int(first_id), int(pilot),
+                                      int(batches), ctypes.byref(b1), ctypes.byref(b2)), h)
+    return b1.value, b2.value
 
 
 def lap_cv_sums(h, n):
@@ -666,6 +688,21 @@ class LapGraph:
 
     def cv_set_potentials(self, phi1=None, phi2=None):
         lap_cv_set_potentials(self.h, phi1, phi2)
+
+    def cv_targets(self, reps, seed):
+        t = self._torch.empty((self.n, 2), dtype=self._torch.float32, device="cuda")
+        lap_cv_targets(self.h, reps, seed, t)
+        return t
+
+    def cv_potentials(self, y, want_phi1=True, want_phi2=True):
+        torch = self._torch
+        phi1 = torch.empty(self.n, dtype=torch.float64, device="cuda") if want_phi1 else None
+        phi2 = torch.empty(self.n, dtype=torch.float64, device="cuda") if want_phi2 else None
+        lap_cv_potentials(self.h, y, phi1, phi2)
+        return phi1, phi2
+
+    def cv_fit_betas(self, phi1, phi2, seed, first_id, pilot, batches):
+        return lap_cv_fit_betas(self.h, phi1, phi2, seed, first_id, pilot, batches)
 
     def cv_sums(self):
         return lap_cv_sums(self.h, self.n)

@@ -213,13 +213,9 @@ def test_trained_network_reduces_kemeny_variance():
     g = I.ba(1500, 3, seed=999)
     G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 28)
     try:
-        v = G.set_root()
-        y1, y2 = G.sample_trace(1024, 5)          # plain pilot: mean Y2 for the potential scale
-        mean_y2 = y2.double().mean().item()
-        G.set_root(v)
-        phi1, phi2 = CVG.potentials(G, params, mean_y2)
+        G.set_root()
+        phi1, phi2 = CVG.pilot_potentials(G, params, seed=5, samples=1024)
         beta1, beta2 = CVG.fit_betas(G, phi1, phi2, seed=77, pilot=4096)
-        G.cv_set_potentials(phi1, phi2)
         a, b, m = G.sample_trace_cv(8192, 5)
         est = (a - b).double().cpu().numpy()
         cv = est + beta2 * m.cpu().numpy()
@@ -231,3 +227,69 @@ def test_trained_network_reduces_kemeny_variance():
     kc = D.kemeny(g.n, g.row_ptr, g.col)
     se = np.std(cv) / np.sqrt(cv.size)
     assert abs(kc_cv - kc) < 6 * se, (kc_cv, kc, se)
+
+
+def test_cv_targets_match_oracle():
+    """lap_cv_targets: FP64 ratios of the handle's counts and of fresh
+    hitting walks, rounded to float32: bit-exact with the oracle's statement
+    on the same counts and walks."""
+    g = I.ba(3000, 3, seed=12)
+    omega, reps, seed = 200, 6, 41
+    G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 26)
+    try:
+        v = G.set_root()
+        G.sample(omega, seed)
+        t = G.cv_targets(reps, seed + 1).cpu().numpy()
+    finally:
+        G.close()
+    c = oracle.sample(g.row_ptr, g.col, v, seed, 0, omega)
+    hit = oracle.hitting_walks(g.row_ptr, g.col, v, seed + 1, reps)
+    want = CV.training_targets(c.cnt1, omega, hit, reps, c.sum_y2, v)
+    assert np.array_equal(t, want)
+
+
+def test_cv_potentials_match_oracle():
+    """lap_cv_potentials: phi1 = y0 / d, phi2 = y1 * (sum Y2 / omega) of the
+    samples drawn, phi2(v) = 0: bit-exact with the oracle's statement."""
+    g = I.er(500, 0.02, seed=8)
+    rng = np.random.default_rng(9)
+    y = rng.uniform(0.1, 5.0, (g.n, 2)).astype(np.float32)
+    G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 24)
+    try:
+        v = G.set_root()
+        G.sample(300, 2)
+        phi1, phi2 = G.cv_potentials(torch.from_numpy(y).cuda())
+        _, _, sums = G.counts()
+    finally:
+        G.close()
+    w1, w2 = CV.potentials(y, g.row_ptr, v, float(sums[2]) / 300.0)
+    assert np.array_equal(phi1.cpu().numpy(), w1) and np.array_equal(phi2.cpu().numpy(), w2)
+
+
+@pytest.mark.parametrize("kernel", [1, 2], ids=["wide", "compact"])
+def test_cv_fit_betas_match_oracle(kernel):
+    """lap_cv_fit_betas draws the pilot batches on the GPU and reduces them
+    there; its per-batch integers equal the oracle's bit for bit, so the
+    coefficients differ only by the order of FP64 sums (1e-9 relative).  The
+    handle is left as after lap_set_root: the next samples start at id 0."""
+    g = I.ba(3000, 3, seed=13)
+    rng = np.random.default_rng(14)
+    phi1 = rng.uniform(0.0, 2.0, g.n)
+    phi2 = rng.uniform(0.0, 40.0, g.n)
+    first, per, batches, seed = (1 << 31) + 5, 150, 6, 21
+    G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 26)
+    try:
+        G.set_option(LAP_OPT_KERNEL, kernel)
+        v = G.set_root()
+        b1, b2 = G.cv_fit_betas(torch.from_numpy(phi1).cuda(), torch.from_numpy(phi2).cuda(), seed, first,
+                                per * batches, batches)
+        G.sample(20, 3)
+        c1, _, s = G.counts()
+    finally:
+        G.close()
+    w1, w2 = CV.fit_betas(g.row_ptr, g.col, v, seed, first, per, batches, CV.quantize_potential(phi1),
+                          CV.quantize_potential(phi2))
+    assert b1 == pytest.approx(w1, rel=1e-9) and b2 == pytest.approx(w2, rel=1e-9)
+    assert b1 != 0.0 and b2 != 0.0
+    c = oracle.sample(g.row_ptr, g.col, v, 3, 0, 20)
+    assert int(s[0]) == 20 and np.array_equal(c1, c.cnt1)
