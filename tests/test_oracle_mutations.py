@@ -4,8 +4,9 @@ start drawn from the wrong law, a visit not counted, an eigenvalue dropped
 from the dense truth, the SpanTree subtree test the other way round) in a
 copy of the oracle outside the repository and runs the pins of that part
 (tests/test_oracle_pins.py for the LEWalk sampler, finalize and dense truth,
-tests/test_oracle_cv_pins.py for the control variate, and
-tests/test_oracle_spantree_pins.py for Alg. 1 / Alg. 3) against the copy; at
+tests/test_oracle_cv_pins.py for the control variate,
+tests/test_oracle_spantree_pins.py for Alg. 1 / Alg. 3 and
+tests/test_oracle_cg_pins.py for the sparse solves) against the copy; at
 least one pin must fail.  The repository's oracle is not
 touched."""
 import os
@@ -20,6 +21,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 C_PINS = "test_oracle_pins.py"
 ST_PINS = "test_oracle_spantree_pins.py"
 CV_PINS = "test_oracle_cv_pins.py"
+CG_PINS = "test_oracle_cg_pins.py"
 
 # (name, file under oracle/, anchor, planted mistake, pins that must catch it)
 MUTATIONS = [
@@ -122,6 +124,12 @@ MUTATIONS = [
     ("spantree_kemeny_sign", "spantree.py",
      "    return ld, ecc, t1 - t2",
      "    return ld, ecc, t1 + t2", ST_PINS),
+    ("cg_residual_update_uses_the_direction", "cg.py",
+     "        r -= alpha * q",
+     "        r -= alpha * p", CG_PINS),
+    ("cg_uniform_target_not_divided_by_n", "cg.py",
+     "    y2 = r1 / n",
+     "    y2 = r1", CG_PINS),
 ]
 
 
@@ -148,7 +156,7 @@ def run_pins_on_copy(tmp_path, fname, src, pins):
 
 @pytest.mark.slow
 @pytest.mark.parametrize("fname,pins", [("lewalk_oracle.c", C_PINS), ("dense.py", C_PINS), ("cv.py", CV_PINS),
-                                        ("spantree.py", ST_PINS)])
+                                        ("spantree.py", ST_PINS), ("cg.py", CG_PINS)])
 def test_unchanged_copy_passes_the_pins(fname, pins, tmp_path):
     src = open(os.path.join(ROOT, "oracle", fname)).read()
     code, out = run_pins_on_copy(tmp_path, fname, src, pins)
