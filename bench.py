@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ws-frac", type=float, default=0.6, help="fraction of free HBM lent as Wilson state")
     ap.add_argument("--ws-gb", type=float, default=0.0, help="cap on the Wilson-state workspace in GB (profiler runs)")
+    ap.add_argument("--kernel", type=int, default=0, help="LAP_OPT_KERNEL for the timed steps (0: the library's choice)")
+    ap.add_argument("--walkers", type=int, default=8, help="LAP_OPT_WALKERS (kernel 3)")
     ap.add_argument("--cv-graphs", type=int, default=200, help="training graphs for the learned control variate (0: skip)")
     ap.add_argument("--cv-batch", type=int, default=16384, help="samples per batch in the CV-vs-plain measurement")
     ap.add_argument("--batched-graphs", type=int, default=512, help="graphs of the uneven batch (0: skip)")
@@ -111,6 +113,10 @@ def parse():
     ap.add_argument("--extra-cv", type=int, default=0,
                     help="also measure the control variate against plain on the extra workloads (1: on)")
     return ap.parse_args()
+
+
+KERNEL_NAMES = {1: "lewalk_kernel (8-byte state)", 2: "lewalk_compact_kernel (1-byte state)",
+                3: "lewalk_group_kernel (several walkers per sample, 2-byte state)"}
 
 
 def peaks():
@@ -340,6 +346,142 @@ def time_to_accuracy(torch, LapGraph, seeds=10, target=1e-2, params=None, paths=
         res["note"] = ("gpu_seconds: CV sampling + CV finalize at omega; prepare_seconds: pilot samples, "
                        "features, MLP forward and coefficient fit (wall)")
     return res
+
+
+def large_truth(torch, LapGraph, g, v, seeds, omega_max):
+    """Plain runs of `seeds` disjoint id ranges of omega_max samples each (ids
+    [s * omega_max, (s + 1) * omega_max), Philox seed 1): their pooled
+    integer counts, the statistical part of the ground truth.  Returns
+    (pooled cnt1 as int64, pooled sum Y1, samples, GPU seconds)."""
+    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR
+    cnt = np.zeros(g.n, dtype=np.int64)
+    sy1, secs = 0, 0.0
+    H = LapGraph(g.row_ptr, g.col, workspace_bytes=int(torch.cuda.mem_get_info()[0] * 0.45))
+    try:
+        for s in range(seeds):
+            H.set_root(v)
+            H.set_option(LAP_OPT_CURSOR, s * omega_max)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            H.sample(omega_max, 1)
+            b.record()
+            c1, _, sums = H.counts()
+            secs += a.elapsed_time(b) / 1e3
+            cnt += c1.astype(np.int64)
+            sy1 += int(sums[1])
+    finally:
+        H.close()
+    return cnt, sy1, seeds * omega_max, secs
+
+
+def large_ecc_truth(torch, g, v, cnt1, omega_pool, sum_y1, exact):
+    """ECC and Kemeny ground truth from pooled plain counts plus the exact
+    parts of the sparse solves: (L^+)_uu = cnt1_pool(u) / (omega_pool d_u)
+    - 2 y2(u) + lvv (u != v), (L^+)_vv = lvv (Section 3.1, element-wise
+    Theorem 1), c(u) = (n-1) / (n (L^+)_uu + Tr L^+) (Section 2), and
+    kappa = sum Y1 / omega_pool - E[Y2] (Alg. 4)."""
+    d = torch.from_numpy(np.diff(g.row_ptr.astype(np.int64)).astype(np.float64)).cuda()
+    y2 = torch.from_numpy(exact["y2"]).cuda()
+    ld = torch.from_numpy(cnt1).cuda().double() / (float(omega_pool) * d) - 2.0 * y2 + exact["lvv"]
+    ld[v] = exact["lvv"]
+    tr = ld.sum()
+    ecc = (g.n - 1) / (g.n * ld + tr)
+    kc = float(sum_y1) / float(omega_pool) - exact["ey2"]
+    return ecc, kc
+
+
+def time_to_accuracy_large(torch, LapGraph, g, v, truth, omega_max, form, params=None, seeds=10, target=1e-2):
+    """Time to relative error 1e-2 on a large graph (Section 6 protocol: error
+    metrics of ECC (max over nodes) and Kemeny; mean over seeds).  Each seed
+    draws its own id range, disjoint from the truth pool's, on the grid
+    omega = round(256 * 2^(k/2)) up to omega_max; the errors are taken
+    against the ground truth of `pool` (plain counts of other ids) with the
+    exact sparse-solve parts; the smallest omega whose mean errors are both
+    <= target is then timed in one fresh run (sampling plus finalize)."""
+    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, LAP_OPT_PATHS
+    grid = []
+    k = 0
+    while True:
+        w = int(round(256 * 2.0 ** (k / 2.0)))
+        if w > omega_max:
+            break
+        grid.append(w)
+        k += 1
+    ecc_t, kc_t, truth_samples = truth
+    ws = int(torch.cuda.mem_get_info()[0] * 0.45)
+    H = LapGraph(g.row_ptr, g.col, workspace_bytes=ws)
+    base = 1 << 30                              # ids far after the truth pool's
+    errs = np.zeros((seeds, len(grid), 2))
+    betas = (0.0, 0.0)
+    prep = 0.0
+    try:
+        H.set_option(LAP_OPT_PATHS, 1 if form == "paths" else 0)
+        H.set_root(v)
+        if params is not None:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, b1, b2 = cv_prepare(H, params, 4242, pilot=8192, batches=8)
+            torch.cuda.synchronize()
+            prep = time.perf_counter() - t0
+            betas = (b1, b2)
+        est = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        for s in range(seeds):
+            H.set_root(v)
+            H.set_option(LAP_OPT_CURSOR, base + s * omega_max)
+            done = 0
+            for j, w in enumerate(grid):
+                H.sample(w - done, 1)
+                done = w
+                if params is None:
+                    H.ecc(est)
+                    kc = H.kemeny()
+                else:
+                    _, _, kc, _ = H.cv_estimates(*betas, ecc_out=est)
+                errs[s, j, 0] = float(torch.max(torch.abs(est - ecc_t) / ecc_t))
+                errs[s, j, 1] = abs(kc - kc_t) / abs(kc_t)
+        mean = errs.mean(axis=0)
+        found = None
+        for j, w in enumerate(grid):
+            if mean[j, 0] <= target and mean[j, 1] <= target:
+                found = w
+                break
+        res = {"form": form, "seeds": seeds, "grid_max": omega_max, "truth_samples": truth_samples,
+               "curve": [{"omega": w, "ecc_max_rel": round(float(mean[j, 0]), 5), "kc_rel": round(float(mean[j, 1]), 7)}
+                         for j, w in enumerate(grid)]}
+        if params is not None:
+            res["betas"] = list(betas)
+            res["prepare_seconds"] = round(prep, 2)
+        if found is None:
+            res["reached"] = False
+            return res
+        # One fresh run to the found omega (ids of the first seed), timed on the device.
+        H.set_root(v)
+        H.set_option(LAP_OPT_CURSOR, base)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        H.sample(found, 1)
+        if params is None:
+            H.ecc(est)
+            H.kemeny()
+        else:
+            H.cv_estimates(*betas, ecc_out=est)
+        b.record()
+        torch.cuda.synchronize()
+        secs = a.elapsed_time(b) / 1e3
+        _, c2, sums = H.counts()
+        alg = (BYTES_WILSON_STEP * int(sums[1]) + BYTES_TREE_INSERT * (g.n - 1) * found +
+               BYTES_WALK_STEP * (int(c2.sum()) + int(sums[2])))
+        pk = peaks()[0]
+        j = grid.index(found)
+        res.update({"reached": True, "omega": found, "gpu_seconds": secs,
+                    "ecc_max_rel_err_mean": float(mean[j, 0]), "kc_rel_err_mean": float(mean[j, 1]),
+                    "roofline": {"bound": "hbm", "achieved": alg / secs / 1e9, "peak": pk, "unit": "GB/s",
+                                 "frac": alg / secs / 1e9 / pk,
+                                 "note": "algorithmic bytes of the timed run (sampling plus finalize) over its time"}})
+        return res
+    finally:
+        H.close()
 
 
 def note(msg):
@@ -872,9 +1014,12 @@ def run_ours(args, rank, world):
     if args.ws_gb > 0:
         ws = min(ws, int(args.ws_gb * 1e9))
     G = LapGraph(g.row_ptr, g.col, workspace_bytes=ws)
+    from paper_2311_10290_gb300.lap import LAP_OPT_KERNEL, LAP_OPT_WALKERS, LAP_STAT_KERNEL
+    if args.kernel:
+        G.set_option(LAP_OPT_KERNEL, args.kernel)
+        G.set_option(LAP_OPT_WALKERS, args.walkers)
     v = G.set_root()
-    from paper_2311_10290_gb300.lap import LAP_STAT_KERNEL
-    kernel_name = {1: "lewalk_kernel (8-byte state)", 2: "lewalk_compact_kernel (1-byte state)"}[G.stat(LAP_STAT_KERNEL)]
+    kernel_name = KERNEL_NAMES[G.stat(LAP_STAT_KERNEL)]
     B = args.batch
     total_steps = args.warmup + args.steps
     from paper_2311_10290_gb300.shard import allreduce_counts, id_range

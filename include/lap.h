@@ -82,7 +82,15 @@ typedef enum {
                                   of two >= n, 256 to 8192.  A sample that does not fit kernel 2
                                   (more such nodes than the table holds, or a loop-erased path
                                   longer than the stack) is withdrawn and re-run with kernel 1:
-                                  results are identical either way. */
+                                  results are identical either way.  3 = several walkers per sample
+                                  (LAP_OPT_WALKERS lanes share one Wilson run; 2 bytes of state per
+                                  node): more samples' worth of independent memory chains when a
+                                  call has few samples.  Kernel 3 needs n < 2^22 and covers the
+                                  plain estimators only (LAP_OPT_PATHS = 0, no control variate;
+                                  otherwise kernel 2 runs).  Its samples that do not fit (a node
+                                  drawn 1023 times, a path longer than a walker's stack, a walker
+                                  without progress for 4 s) are withdrawn and re-run with kernel 1.
+                                  Counts are identical with every kernel. */
     LAP_OPT_STACK = 6,         /* loop-erased path capacity per sample of kernel 2; 0 = default
                                   (16 sqrt(n) rounded up to a power of two, at least 1024) */
     LAP_OPT_PATHS = 7,         /* 0 (default): the uniform-start and pi-start v-absorbed walks take
@@ -94,6 +102,11 @@ typedef enum {
                                   expectations (so the same estimands), correlated with the Wilson
                                   counts, which lowers the variance of y1 - 2 y2 and of Y1 - Y2.
                                   Only before the first sample after lap_set_root. */
+    LAP_OPT_WALKERS = 9,       /* lanes per sample of kernel 3: 2, 4 or 8 (default 8).  They run the
+                                  sample's Wilson run together (Section 3.4, stack representation:
+                                  the popped cycles, so every node's draws and the tree, do not
+                                  depend on the order in which walkers find them), then one runs
+                                  the uniform-start walk and one the pi-start walk. */
     LAP_OPT_PATH_START = 8     /* -1 (default): the first absorbed walk (or loop-included path) of
                                   each sample starts at a uniform draw (Alg. 2).  s in [0, n): it
                                   starts at node s, so its passes of u have mean d_u (L_v^{-1})_{su}
@@ -386,6 +399,13 @@ lap_status lap_cv_set_potentials(lap_graph *g, const double *phi1_dev, const dou
 
 /* Raw control-variate sums a1[n], a2[n], p2[n] (int64; NULL skips). */
 lap_status lap_cv_sums(lap_graph *g, int64_t *a1, int64_t *a2, int64_t *p2, int on_device);
+
+/* Replaces the control-variate sums a1[n], a2[n], p2[n] (int64, lap_cv_sums'
+ * layout; host or device) with given totals, for example the sums of
+ * several handles or processes that drew disjoint sample ids with the same
+ * potentials (call after lap_set_counts, which clears them).  Needs the
+ * potentials set.  Synchronises. */
+lap_status lap_cv_set_sums(lap_graph *g, const int64_t *a1, const int64_t *a2, const int64_t *p2, int on_device);
 
 /* Control-variate estimates: ldiag[n], ecc[n] (either may be NULL), kemeny[1]
  * and m2_total[1] (host doubles; may be NULL).  Synchronises. */

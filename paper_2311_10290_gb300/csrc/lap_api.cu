@@ -99,14 +99,26 @@ uint32_t stack_cap_of(const lap_graph *g)
 uint64_t slot_bytes_of(const lap_graph *g, int kernel)
 {
     if (kernel == LAP_KERNEL_WIDE) return 8ull * (uint64_t)g->n;
+    if (kernel == LAP_KERNEL_GROUP)
+        // Control block, 16-bit words, one path stack per walker.
+        return (64ull + 2ull * n_pad_of(g) + 4ull * stack_cap_of(g) * (uint64_t)g->walkers + 255ull) & ~255ull;
     // State bytes, path-count bytes (loop-included paths only), stack, count table.
     return ((g->paths_opt ? 2ull : 1ull) * n_pad_of(g) + 4ull * stack_cap_of(g) + (8ull << lap_table_log2(g->n)) +
             255ull) & ~255ull;
 }
 
+// Kernel 3 covers the plain estimators (own draws, no control variate) on
+// graphs with n < 2^22 (its stack entries hold 22-bit node ids).
+bool group_ok(const lap_graph *g)
+{
+    return g->n < (1 << 22) && !g->paths_opt && !g->cv1 && !g->cv2 && !g->compact_disabled &&
+           (!g->ws || g->ws_bytes >= slot_bytes_of(g, LAP_KERNEL_GROUP));
+}
+
 int choose_kernel(const lap_graph *g)
 {
     if (g->kernel_opt == LAP_KERNEL_WIDE) return LAP_KERNEL_WIDE;
+    if (g->kernel_opt == LAP_KERNEL_GROUP && group_ok(g)) return LAP_KERNEL_GROUP;
     if (g->n >= (1 << 27) || g->compact_disabled) return LAP_KERNEL_WIDE;
     if (g->ws && g->ws_bytes < slot_bytes_of(g, LAP_KERNEL_COMPACT)) return LAP_KERNEL_WIDE;
     return LAP_KERNEL_COMPACT;
@@ -133,6 +145,13 @@ lap_status ensure_workspace(lap_graph *g, int kernel)
     }
     const uint64_t slots = g->ws_bytes / per_slot;
     if (slots == 0) return fail(g, LAP_ERR_OOM, "workspace smaller than one sample's state");
+    if (kernel == LAP_KERNEL_GROUP) {
+        // Kernel 3 clears a slot at each sample start; the next kernel of
+        // another layout zeroes the workspace again.
+        g->last_kernel = kernel;
+        g->ws_zeroed = false;
+        return LAP_OK;
+    }
     if (slots > g->slot_epoch_cap) {
         cudaFree(g->d_slot_epoch);
         g->d_slot_epoch = nullptr;
@@ -167,9 +186,13 @@ lap_status launch(lap_graph *g, LapSampleLaunch &p, int kernel)
     p.tbl_log2 = lap_table_log2(g->n);
     p.stack_cap = kernel == LAP_KERNEL_COMPACT
                       ? (uint32_t)((p.slot_bytes - (p.paths ? 2ull : 1ull) * p.n_pad - (8ull << p.tbl_log2)) / 4ull)
+                  : kernel == LAP_KERNEL_GROUP
+                      ? (uint32_t)(((p.slot_bytes - 64ull - 2ull * p.n_pad) / 4ull / (uint64_t)g->walkers) & ~3ull)
                       : 0u;
     LAP_CUDA(g, cudaMemsetAsync(&g->d_acc->claim, 0, sizeof(unsigned int), g->stream));
-    const cudaError_t e = kernel == LAP_KERNEL_WIDE ? lap_launch_sample(p, g->stream) : lap_launch_sample_compact(p, g->stream);
+    const cudaError_t e = kernel == LAP_KERNEL_WIDE    ? lap_launch_sample(p, g->stream)
+                          : kernel == LAP_KERNEL_GROUP ? lap_launch_sample_group(p, g->walkers, g->stream)
+                                                       : lap_launch_sample_compact(p, g->stream);
     if (e != cudaSuccess) {
         char buf[256];
         snprintf(buf, sizeof(buf), "sampler launch (kernel %d, %llu lanes, block %d, cv %d): %s", kernel,
@@ -197,6 +220,10 @@ lap_status resolve_pending(lap_graph *g)
     lap_status s = ensure_workspace(g, LAP_KERNEL_WIDE);
     if (s != LAP_OK) return s;
     LapSampleLaunch p = g->pending_launch;
+    // The workspace and the slot table are those ensure_workspace just set
+    // up for the 8-byte layout (the table may have been (re)allocated).
+    p.ws = g->ws;
+    p.slot_epoch = g->d_slot_epoch;
     p.ids = g->d_ovf_ids;
     p.trace_base = p.first;
     p.count = h.ovf_count;
@@ -347,8 +374,14 @@ lap_status lap_set_option(lap_graph *g, int32_t option, int64_t value)
         if ((uint64_t)value >= (1ull << 32)) return fail(g, LAP_ERR_TOO_LARGE, "sample ids are limited to 2^32");
         g->cursor = (uint64_t)value;
         return LAP_OK;
+    case LAP_OPT_WALKERS:
+        if (value != 2 && value != 4 && value != 8) return fail(g, LAP_ERR_INVALID_ARG, "walkers must be 2, 4 or 8");
+        if (g->walkers != (int)value) g->last_kernel = 0;     // the slot layout changes
+        g->walkers = (int)value;
+        return LAP_OK;
     case LAP_OPT_KERNEL:
-        if (value > 2) return fail(g, LAP_ERR_INVALID_ARG, "kernel must be 0, 1 or 2");
+        if (value > 3) return fail(g, LAP_ERR_INVALID_ARG, "kernel must be 0, 1, 2 or 3");
+        if (value == LAP_KERNEL_GROUP && g->n >= (1 << 22)) return fail(g, LAP_ERR_INVALID_ARG, "kernel 3 needs n < 2^22");
         if (value == LAP_KERNEL_COMPACT && g->n >= (1 << 27)) return fail(g, LAP_ERR_INVALID_ARG, "kernel 2 needs n < 2^27");
         g->kernel_opt = (int)value;
         return LAP_OK;
@@ -559,7 +592,7 @@ static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, 
         p.cv_a2 = g->d_cv_a2;
         p.cv_p2 = g->d_cv_p2;
     }
-    if (kernel == LAP_KERNEL_COMPACT) {
+    if (kernel == LAP_KERNEL_COMPACT || kernel == LAP_KERNEL_GROUP) {
         if (g->ovf_cap < n_samples) {
             cudaFree(g->d_ovf_ids);
             g->d_ovf_ids = nullptr;
@@ -573,7 +606,7 @@ static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, 
         p.ovf_ids = g->d_ovf_ids;
     }
     if ((s = launch(g, p, kernel)) != LAP_OK) return s;
-    if (kernel == LAP_KERNEL_COMPACT) {
+    if (kernel == LAP_KERNEL_COMPACT || kernel == LAP_KERNEL_GROUP) {
         g->pending = true;
         g->pending_launch = p;
     }
@@ -1137,6 +1170,23 @@ lap_status lap_cv_sums(lap_graph *g, int64_t *a1, int64_t *a2, int64_t *p2, int 
     if (a2) LAP_CUDA(g, cudaMemcpyAsync(a2, g->d_cv_a2, nb, kind, g->stream));
     if (p2) LAP_CUDA(g, cudaMemcpyAsync(p2, g->d_cv_p2, nb, kind, g->stream));
     LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    return LAP_OK;
+}
+
+lap_status lap_cv_set_sums(lap_graph *g, const int64_t *a1, const int64_t *a2, const int64_t *p2, int on_device)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (!g->d_cv_a1) return fail(g, LAP_ERR_INVALID_ARG, "no potentials set");
+    if (!a1 || !a2 || !p2) return fail(g, LAP_ERR_INVALID_ARG, "a1, a2 and p2 must be set");
+    if ((s = poll_status(g)) != LAP_OK) return s;
+    const size_t nb = sizeof(int64_t) * (size_t)g->n;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    LAP_CUDA(g, cudaMemcpyAsync(g->d_cv_a1, a1, nb, kind, g->stream));
+    LAP_CUDA(g, cudaMemcpyAsync(g->d_cv_a2, a2, nb, kind, g->stream));
+    LAP_CUDA(g, cudaMemcpyAsync(g->d_cv_p2, p2, nb, kind, g->stream));
+    LAP_CUDA(g, cudaStreamSynchronize(g->stream));
+    g->results_valid = false;
     return LAP_OK;
 }
 

@@ -97,6 +97,8 @@ enum : uint32_t {
 cudaError_t lap_launch_sample(const LapSampleLaunch &p, cudaStream_t st);
 // sampler_compact.cu
 cudaError_t lap_launch_sample_compact(const LapSampleLaunch &p, cudaStream_t st);
+// sampler_group.cu: `walkers` lanes per sample (2, 4 or 8); p.slots counts groups
+cudaError_t lap_launch_sample_group(const LapSampleLaunch &p, int walkers, cudaStream_t st);
 
 // ------------------------------------------------------------ batches
 // One graph of a batch (device descriptor).  Pointers index the batch's
@@ -192,7 +194,7 @@ inline int lap_pick_block(uint64_t lanes, int num_sms)
     return block;
 }
 
-enum LapKernel : int { LAP_KERNEL_WIDE = 1, LAP_KERNEL_COMPACT = 2 };
+enum LapKernel : int { LAP_KERNEL_WIDE = 1, LAP_KERNEL_COMPACT = 2, LAP_KERNEL_GROUP = 3 };
 
 // Compact kernels: log2 of the entries of the per-lane table of draw counts
 // above 30 (after the path stack; see compact_state.cuh): the next power of
@@ -283,7 +285,8 @@ struct lap_graph {
     uint64_t step_limit = 0;                // 0: default
     uint64_t slots_opt = 0;
     int block_opt = 0;
-    int kernel_opt = 0;                     // 0 auto, LAP_KERNEL_WIDE, LAP_KERNEL_COMPACT
+    int kernel_opt = 0;                     // 0 auto, LAP_KERNEL_WIDE, LAP_KERNEL_COMPACT, LAP_KERNEL_GROUP
+    int walkers = 8;                        // LAP_OPT_WALKERS (kernel 3)
     uint32_t paths_opt = 0;                 // LAP_OPT_PATHS
     int32_t path_start = -1;                // LAP_OPT_PATH_START (-1: uniform start)
     uint32_t stack_cap = 0;                 // 0: default, about 16 sqrt(n)

@@ -1,0 +1,402 @@
+// Several-walkers LEWalk sampler ("kernel 3"): W lanes of one warp run one
+// sample's Wilson LE_v run together, then two of them run the sample's
+// uniform-start and pi-start v-absorbed walks (Alg. 2 and Alg. 4).  The
+// counts are those of the sequential run, bit for bit.
+//
+// Why it is exact.  In the stack representation of Section 3.4 (Fig. 1),
+// node u's j-th draw is the j-th entry of u's stack, here the Philox draw
+// (u, j, i, 0); Wilson's run pops cycles of stack tops, and the set of popped
+// cycles -- hence each node's number of draws (its visits) and the tree --
+// does not depend on the order in which cycles are found.  The walkers follow
+// the concurrent popping protocol:
+//   - a walker owns the nodes of its loop-erased path; at its head u it takes
+//     u's pending arrow if an aborted walker left one (no new draw), else
+//     draws u's next stack entry (a visit of u);
+//   - the arrow's target w is claimed with a compare-and-swap if free; if w
+//     is in the tree the path joins the tree; if w is on the walker's own
+//     path the closed cycle is popped (its nodes' arrows are consumed);
+//   - if w is on another walker's path, a lower-numbered walker waits and
+//     tries again, a higher-numbered one aborts: its nodes are released with
+//     their current arrows pending (the arrow of a node is always its last
+//     draw, k - 1), so no stack entry is lost.
+// Waits go from lower- to higher-numbered walkers only, so they cannot form a
+// cycle; the highest-numbered active walker always progresses.
+//
+// State per node and sample in flight, 16 bits, cleared at each sample start:
+//   bit 15 InTree | bit 14 pending | bits 10..13 owner (walker + 1, 0 = free) |
+//   bits 0..9 draws k
+// A path node's arrow is never stored: it is draw k - 1.  A walker keeps its
+// path on a private stack (entries node | k << 22), the head in a register.
+// Start nodes come from a per-sample chunk cursor (32 nodes per chunk); past
+// the last chunk the cursor wraps around (sweeps pick up nodes released by
+// aborts and popped cycles behind it) until every node is in the tree.
+//
+// A sample that does not fit (a node drawn 1023 times, a path longer than the
+// walker's stack, or a walker without progress for kStallNs) is withdrawn
+// exactly as in the 1-byte kernel: the group subtracts k - 1 for every node
+// and lists the id for a re-run with the 8-byte kernel.
+#include "lap_internal.h"
+#include "philox.cuh"
+
+namespace {
+
+constexpr uint32_t kGTree = 0x8000u, kGPend = 0x4000u, kGOwnShift = 10u, kGOwn = 0xFu << 10, kGK = 0x3FFu;
+constexpr uint32_t kGKMax = 0x3FFu;
+constexpr int kNodeBits = 22;
+constexpr uint32_t kGNode = (1u << kNodeBits) - 1u;
+constexpr uint32_t kChunk = 32;                                   // nodes per scan chunk (64 bytes)
+constexpr unsigned long long kStallNs = 4000000000ull;            // 4 s without progress: withdraw
+constexpr unsigned int kWithdraw = 1u;
+
+struct GroupCtl {              // first 64 bytes of a slot
+    unsigned int cursor;       // scan chunks claimed so far (grows past the chunk count: sweeps)
+    unsigned int tree;         // nodes in the tree, the root included
+    unsigned int status;       // kWithdraw
+    unsigned int pad0;
+    unsigned long long y1;     // the walkers' draws
+    unsigned long long pad[5];
+};
+
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t ld_word(const uint16_t *a)
+{
+    uint16_t v;
+    asm volatile("ld.global.cg.u16 %0, [%1];" : "=h"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_word(uint16_t *a, uint32_t v)
+{
+    asm volatile("st.global.cg.u16 [%0], %1;" ::"l"(a), "h"((uint16_t)v) : "memory");
+}
+__device__ __forceinline__ uint4 ld_chunk4(const uint16_t *a)
+{
+    uint4 v;
+    asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned int ld_u32(const unsigned int *a)
+{
+    unsigned int v;
+    asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_u64(const unsigned long long *a)
+{
+    unsigned long long v;
+    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t cas_word(uint16_t *a, uint32_t expect, uint32_t val)
+{
+    return atomicCAS(reinterpret_cast<unsigned short int *>(a), (unsigned short int)expect, (unsigned short int)val);
+}
+__device__ __forceinline__ bool w_free(uint32_t w) { return (w & (kGTree | kGOwn)) == 0u; }
+__device__ __forceinline__ uint32_t w_owner(uint32_t w) { return (w & kGOwn) >> kGOwnShift; }
+
+// Bit b set when word b of the 32 words (two per 32-bit lane of the four
+// vectors) is neither in the tree nor owned.
+__device__ __forceinline__ uint32_t free_mask2(uint32_t x)
+{
+    const uint32_t e = __vcmpeq2(x & ((kGTree | kGOwn) * 0x00010001u), 0u);   // 0xFFFF per free half
+    return (e & 1u) | ((e >> 15) & 2u);
+}
+__device__ __forceinline__ uint32_t free_mask(uint4 a, uint4 b, uint4 c, uint4 d)
+{
+    const uint32_t q[16] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w, d.x, d.y, d.z, d.w};
+    uint32_t m = 0;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) m |= free_mask2(q[t]) << (2 * t);
+    return m;
+}
+
+__device__ __forceinline__ uint64_t ld_row(const int2 *rowinfo, int32_t u)
+{
+    return *reinterpret_cast<const unsigned long long *>(rowinfo + u);
+}
+
+enum : uint32_t { G_SCAN = 0, G_STEP, G_MOVE, G_DONE };
+
+template <int W>
+__global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
+{
+    static_assert(W == 2 || W == 4 || W == 8, "walkers per sample");
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t gbase = lane & ~(uint32_t)(W - 1);
+    const unsigned gmask = ((1u << W) - 1u) << gbase;
+    const uint32_t j = lane - gbase;                    // walker index in the group
+    const uint32_t mine = (j + 1u) << kGOwnShift;       // owner field of this walker
+    const uint64_t slot = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / W;
+    if (slot >= p.slots) return;                        // uniform over the group
+    const int32_t n = p.g.n;
+    const int32_t v = p.root;
+    const int2 *__restrict__ rowinfo = p.g.rowinfo;
+    const int32_t *__restrict__ col = p.g.col;
+    uint8_t *base = reinterpret_cast<uint8_t *>(p.ws) + slot * p.slot_bytes;
+    GroupCtl *ctl = reinterpret_cast<GroupCtl *>(base);
+    uint16_t *st = reinterpret_cast<uint16_t *>(base + 64);
+    const uint32_t cap = p.stack_cap;                   // entries per walker, a multiple of 4
+    uint32_t *stk = reinterpret_cast<uint32_t *>(base + 64 + 2ull * p.n_pad) + (uint64_t)j * cap;
+    const uint32_t nchunks = (uint32_t)((n + (int32_t)kChunk - 1) / (int32_t)kChunk);   // chunks holding nodes
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    const uint64_t limit = p.step_limit;
+    unsigned long long acc1 = 0, acc2 = 0;
+    unsigned int bad = 0;
+
+    for (;;) {
+        unsigned int q = 0;
+        if (j == 0) q = atomicAdd(&p.acc->claim, 1u);
+        q = __shfl_sync(gmask, q, (int)gbase);
+        if (q >= p.count) break;
+        const uint32_t i = p.first + q;
+
+        // Clear the slot's state and control block; the root starts in the tree.
+        {
+            uint4 *s4 = reinterpret_cast<uint4 *>(st);
+            const uint64_t n4 = 2ull * p.n_pad / 16u;
+            for (uint64_t x = j; x < n4; x += W) s4[x] = make_uint4(0u, 0u, 0u, 0u);
+            if (j == 0) {
+                uint4 *c4 = reinterpret_cast<uint4 *>(ctl);
+                for (int x = 0; x < 4; ++x) c4[x] = make_uint4(0u, 0u, 0u, 0u);
+            }
+            __threadfence();
+            __syncwarp(gmask);
+            if (j == 0) {
+                st[v] = (uint16_t)kGTree;
+                ctl->tree = 1u;
+            }
+            __threadfence();
+            __syncwarp(gmask);
+        }
+
+        uint32_t phase = G_SCAN;
+        uint32_t cbase = 0, cmask = 0;       // current scan chunk and its candidate starts
+        int32_t h = 0;                       // head of the walker's path
+        uint32_t hk = 0;                     // draws of the head
+        bool hpend = false;                  // the head's arrow is pending (taken without a draw)
+        uint64_t hrow = 0;                   // row record of the head
+        uint32_t sp = 0;                     // path length (stack entries 0 .. sp-2 in memory, the head in `top`)
+        uint32_t top = 0;
+        int32_t w = 0;                       // target of the head's arrow (G_MOVE)
+        uint32_t ew = 0;                     // expected word of w for the claim
+        uint64_t y1 = 0;
+        uint32_t iter = 0;
+        unsigned long long tprog = 0;        // last progress (set when a wait or an idle sweep begins)
+        bool waiting = false;
+        bool withdraw = false;
+
+        while (phase != G_DONE) {
+            if (phase == G_SCAN) {
+                if (cmask == 0u) {
+                    if (ld_u32(&ctl->tree) >= (unsigned)n || ld_u32(&ctl->status)) { phase = G_DONE; break; }
+                    const unsigned int c = atomicAdd(&ctl->cursor, 1u);
+                    const uint32_t ch = c % nchunks;
+                    cbase = ch * kChunk;
+                    const uint16_t *cp = st + cbase;
+                    const uint4 a = ld_chunk4(cp), b = ld_chunk4(cp + 8), cc = ld_chunk4(cp + 16), d = ld_chunk4(cp + 24);
+                    cmask = free_mask(a, b, cc, d);
+                    // The last chunk holds 1..31 nodes: cbase < n <= cbase + 32.
+                    if (cbase + kChunk > (uint32_t)n) cmask &= (1u << ((uint32_t)n - cbase)) - 1u;
+                    if (c >= nchunks && cmask == 0u) {
+                        // An idle sweep: the remaining nodes are on other walkers' paths.
+                        if (!waiting) { waiting = true; tprog = now_ns(); }
+                        else if (now_ns() - tprog > kStallNs) { withdraw = true; phase = G_DONE; break; }
+                        __nanosleep(200);
+                    }
+                    continue;
+                }
+                const int32_t s = (int32_t)(cbase + (uint32_t)__ffs(cmask) - 1u);
+                cmask &= cmask - 1u;
+                // Claim the start: most nodes are untouched (word 0) on the first pass.
+                uint32_t expect = 0u;
+                uint32_t old = cas_word(st + s, expect, mine);
+                const uint64_t row = ld_row(rowinfo, s);
+                for (int t = 0; t < 8 && old != expect && w_free(old); ++t) {
+                    expect = old;
+                    old = cas_word(st + s, expect, expect | mine);
+                }
+                if (old != expect) continue;           // in the tree, or taken by another walker
+                waiting = false;
+                h = s;
+                hk = old & kGK;
+                hpend = (old & kGPend) != 0u;
+                hrow = row;
+                sp = 1;
+                top = (uint32_t)s | (hk << kNodeBits);
+                phase = G_STEP;
+                continue;
+            }
+            if (phase == G_STEP) {
+                // Take the head's arrow: its pending one, or its next stack entry.
+                uint32_t kd;
+                if (hpend) {
+                    kd = hk - 1u;
+                    hpend = false;
+                } else {
+                    if (hk >= kGKMax) { withdraw = true; phase = G_DONE; break; }
+                    kd = hk;
+                    ++hk;
+                    ++y1;
+                    if (kd) atomicAdd(&p.rep1[h], 1ull);
+                    st_word(st + h, mine | hk);
+                    if (y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; withdraw = true; phase = G_DONE; break; }
+                }
+                top = (uint32_t)h | (hk << kNodeBits);
+                const uint32_t deg = (uint32_t)(hrow >> 32);
+                w = col[(int64_t)(int32_t)(uint32_t)hrow + (int64_t)lap::below(lap::philox_r64((uint32_t)h, kd, i, 0u, key0, key1), deg)];
+                ew = 0u;
+                phase = G_MOVE;
+                if (((++iter) & 255u) == 0u && ld_u32(&ctl->status)) { phase = G_DONE; break; }
+                // fall through to the claim in the same iteration
+            }
+            if (phase == G_MOVE) {
+                uint32_t old = cas_word(st + w, ew, ew | mine);
+                const uint64_t row = ld_row(rowinfo, w);
+                for (int t = 0; t < 8 && old != ew && w_free(old); ++t) {
+                    ew = old;
+                    old = cas_word(st + w, ew, ew | mine);
+                }
+                if (old == ew) {
+                    // w joins the path as its new head.
+                    if (sp >= cap) { withdraw = true; phase = G_DONE; break; }
+                    stk[sp - 1] = top;
+                    ++sp;
+                    h = w;
+                    hk = old & kGK;
+                    hpend = (old & kGPend) != 0u;
+                    hrow = row;
+                    top = (uint32_t)w | (hk << kNodeBits);
+                    waiting = false;
+                    phase = G_STEP;
+                    continue;
+                }
+                if (old & kGTree) {
+                    // The loop-erased path joins the tree (Alg. 2's retrace).
+                    st_word(st + (top & kGNode), kGTree | (top >> kNodeBits));
+                    for (uint32_t x = 0; x + 1u < sp; ++x) {
+                        const uint32_t e = stk[x];
+                        st_word(st + (e & kGNode), kGTree | (e >> kNodeBits));
+                    }
+                    __threadfence();
+                    atomicAdd(&ctl->tree, sp);
+                    sp = 0;
+                    waiting = false;
+                    phase = G_SCAN;
+                    continue;
+                }
+                const uint32_t o = w_owner(old);
+                if (o == j + 1u) {
+                    // A cycle of stack tops closed at w: pop it; w draws again.
+                    st_word(st + h, hk);
+                    uint32_t x = sp - 1u;            // entries 0 .. sp-2 are in memory
+                    uint32_t e = 0;
+                    for (;;) {
+                        if (x == 0u) { bad |= LAP_DEV_BAD_INDEX; withdraw = true; break; }
+                        e = stk[--x];
+                        if ((int32_t)(e & kGNode) == w) break;
+                        st_word(st + (e & kGNode), e >> kNodeBits);
+                    }
+                    if (withdraw) { phase = G_DONE; break; }
+                    sp = x + 1u;
+                    top = e;
+                    h = w;
+                    hk = e >> kNodeBits;
+                    hpend = false;
+                    hrow = row;
+                    waiting = false;
+                    phase = G_STEP;
+                    continue;
+                }
+                if (j + 1u > o) {
+                    // Abort: every node of the path keeps its arrow as pending.
+                    st_word(st + (top & kGNode), kGPend | (top >> kNodeBits));
+                    for (uint32_t x = 0; x + 1u < sp; ++x) {
+                        const uint32_t e = stk[x];
+                        st_word(st + (e & kGNode), kGPend | (e >> kNodeBits));
+                    }
+                    sp = 0;
+                    waiting = false;
+                    phase = G_SCAN;
+                    continue;
+                }
+                // Wait for the higher-numbered walker; try the same arrow again.
+                if (!waiting) { waiting = true; tprog = now_ns(); }
+                else if (now_ns() - tprog > kStallNs) { withdraw = true; phase = G_DONE; break; }
+                if (ld_u32(&ctl->status)) { phase = G_DONE; break; }
+                ew = 0u;
+                __nanosleep(100);
+                continue;
+            }
+        }
+
+        if (withdraw) atomicOr(&ctl->status, kWithdraw);
+        atomicAdd(&ctl->y1, (unsigned long long)y1);
+        __threadfence();
+        __syncwarp(gmask);
+        if (ld_u32(&ctl->status) & kWithdraw) {
+            // Withdraw the sample: subtract the repeat visits counted so far.
+            for (int32_t x = (int32_t)j; x < n; x += W) {
+                const uint32_t k = ld_word(st + x) & kGK;
+                if (k >= 2u) atomicAdd(&p.rep1[x], (unsigned long long)(-(long long)(k - 1u)));
+            }
+            if (j == 0) {
+                const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
+                if (ix < p.count) p.ovf_ids[ix] = i;
+            }
+        } else {
+            if (j == 0) {
+                // Alg. 2: the v-absorbed walk from a uniform start (or the fixed
+                // start of a single-source row), counting passes.
+                uint64_t t = 0;
+                int32_t u = p.ustart ? (int32_t)(p.ustart - 1u)
+                                     : (int32_t)lap::below(lap::philox_r64(0u, 0u, i, 1u, key0, key1), (uint64_t)n);
+                while (u != v) {
+                    atomicAdd(&p.cnt2[u], 1ull);
+                    if (++t > limit) { bad |= LAP_DEV_STEP_LIMIT; break; }
+                    const uint64_t r = ld_row(rowinfo, u);
+                    u = col[(int64_t)(int32_t)(uint32_t)r +
+                            (int64_t)lap::below(lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1), (uint32_t)(r >> 32))];
+                }
+                const unsigned long long sy1 = ld_u64(&ctl->y1);
+                acc1 += sy1;
+                if (p.y1_out) p.y1_out[i - p.first] = sy1;
+            }
+            if (j == 1u) {
+                // Alg. 4: the v-absorbed walk from s ~ pi (the head of a uniform arc); Y2 = its length.
+                uint64_t y2 = 0;
+                int32_t u = col[(int64_t)lap::below(lap::philox_r64(0u, 0u, i, 2u, key0, key1), (uint64_t)p.g.arcs)];
+                while (u != v) {
+                    if (++y2 > limit) { bad |= LAP_DEV_STEP_LIMIT; break; }
+                    const uint64_t r = ld_row(rowinfo, u);
+                    u = col[(int64_t)(int32_t)(uint32_t)r +
+                            (int64_t)lap::below(lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1), (uint32_t)(r >> 32))];
+                }
+                acc2 += y2;
+                if (p.y2_out) p.y2_out[i - p.first] = y2;
+            }
+        }
+        __syncwarp(gmask);
+    }
+    if (acc1) atomicAdd(&p.acc->sum_y1, acc1);
+    if (acc2) atomicAdd(&p.acc->sum_y2, acc2);
+    if (bad) atomicOr(&p.acc->status, bad);
+}
+
+}  // namespace
+
+cudaError_t lap_launch_sample_group(const LapSampleLaunch &p, int walkers, cudaStream_t st)
+{
+    if (p.count == 0 || p.slots == 0) return cudaSuccess;
+    const uint64_t lanes = p.slots * (uint64_t)walkers;
+    const int block = 256;
+    const uint64_t grid = (lanes + block - 1) / block;
+    if (walkers == 2) lewalk_group_kernel<2><<<(unsigned)grid, block, 0, st>>>(p);
+    else if (walkers == 4) lewalk_group_kernel<4><<<(unsigned)grid, block, 0, st>>>(p);
+    else if (walkers == 8) lewalk_group_kernel<8><<<(unsigned)grid, block, 0, st>>>(p);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}

@@ -28,6 +28,7 @@ STATUS = {
 LAP_OPT_STEP_LIMIT, LAP_OPT_SLOTS, LAP_OPT_BLOCK, LAP_OPT_CURSOR, LAP_OPT_KERNEL, LAP_OPT_STACK = 1, 2, 3, 4, 5, 6
 LAP_OPT_PATHS = 7
 LAP_OPT_PATH_START = 8
+LAP_OPT_WALKERS = 9
 LAP_STAT_SLOTS, LAP_STAT_KERNEL, LAP_STAT_FALLBACKS = 1, 2, 3
 LAP_MLP_PARAMS = 4866
 LAP_BOPT_LANES, LAP_BOPT_CLAIM, LAP_BOPT_ORDER, LAP_BOPT_BLOCK, LAP_BOPT_STACK, LAP_BOPT_PATHS = 1, 2, 3, 4, 5, 6
@@ -93,6 +94,7 @@ def library():
         "lap_cv_fit_betas": (i32, [vp, vp, vp, u64, u64, u64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]),
         "lap_cv_sums": (i32, [vp, vp, vp, vp, ctypes.c_int]),
+        "lap_cv_set_sums": (i32, [vp, vp, vp, vp, ctypes.c_int]),
         "lap_cv_estimates": (i32, [vp, ctypes.c_double, ctypes.c_double, vp, vp, ctypes.c_int, vp, vp]),
         "lap_sample_trace_cv": (i32, [vp, u64, u64, vp, vp, vp]),
         "lap_mlp_forward": (i32, [vp, vp, i64, vp, vp]),
@@ -371,8 +373,25 @@ def lap_cv_sums(h, n):
     return a1, a2, p2
 
 
-def lap_cv_estimates(h, n, beta1, beta2):
-    """Returns (ldiag, ecc, kemeny, m2_total) of the control-variate estimators."""
+def lap_cv_set_sums(h, a1, a2, p2):
+    """a1, a2, p2: int64 arrays (numpy: host; torch CUDA tensors: device)."""
+    if _is_torch(a1):
+        _check(library().lap_cv_set_sums(h, _dp(a1), _dp(a2), _dp(p2), 1), h)
+    else:
+        a = [np.ascontiguousarray(x, dtype=np.int64) for x in (a1, a2, p2)]
+        _check(library().lap_cv_set_sums(h, _host_ptr(a[0]), _host_ptr(a[1]), _host_ptr(a[2]), 0), h)
+
+
+def lap_cv_estimates(h, n, beta1, beta2, ecc_out=None):
+    """Returns (ldiag, ecc, kemeny, m2_total) of the control-variate estimators.
+    With a float64 CUDA tensor `ecc_out` the ECC goes there (device) and
+    ldiag is not read: returns (None, ecc_out, kemeny, m2_total)."""
+    if ecc_out is not None:
+        kc = np.zeros(1)
+        m2 = np.zeros(1)
+        _check(library().lap_cv_estimates(h, float(beta1), float(beta2), None, _dp(ecc_out), 1,
+                                          _host_ptr(kc), _host_ptr(m2)), h)
+        return None, ecc_out, float(kc[0]), float(m2[0])
     ld = np.zeros(n)
     ec = np.zeros(n)
     kc = np.zeros(1)
@@ -707,8 +726,11 @@ class LapGraph:
     def cv_sums(self):
         return lap_cv_sums(self.h, self.n)
 
-    def cv_estimates(self, beta1, beta2):
-        return lap_cv_estimates(self.h, self.n, beta1, beta2)
+    def cv_set_sums(self, a1, a2, p2):
+        lap_cv_set_sums(self.h, a1, a2, p2)
+
+    def cv_estimates(self, beta1, beta2, ecc_out=None):
+        return lap_cv_estimates(self.h, self.n, beta1, beta2, ecc_out)
 
     def sample_trace_cv(self, n_samples, seed):
         t = self._torch

@@ -293,3 +293,43 @@ def test_cv_fit_betas_match_oracle(kernel):
     assert b1 != 0.0 and b2 != 0.0
     c = oracle.sample(g.row_ptr, g.col, v, 3, 0, 20)
     assert int(s[0]) == 20 and np.array_equal(c1, c.cnt1)
+
+
+def test_cv_sums_merge_across_handles():
+    """Two handles draw disjoint sample-id ranges with the same potentials;
+    their integer counts and control-variate sums, added on the host and
+    loaded into a third handle (lap_set_counts, then lap_cv_set_sums), give
+    the control-variate estimates of one handle that drew every id, bit for
+    bit."""
+    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR
+    g = I.ba(2500, 3, seed=21)
+    rng = np.random.default_rng(22)
+    phi1 = torch.from_numpy(rng.uniform(0.0, 2.0, g.n)).cuda()
+    phi2 = torch.from_numpy(rng.uniform(0.0, 30.0, g.n)).cuda()
+
+    def run(first, count):
+        G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 26)
+        G.set_root()
+        G.set_option(LAP_OPT_CURSOR, first)
+        G.cv_set_potentials(phi1, phi2)
+        G.sample(count, 8)
+        return G
+
+    whole = run(0, 500)
+    a, b = run(0, 180), run(180, 320)
+    try:
+        ca, cb = a.counts(), b.counts()
+        sa, sb = a.cv_sums(), b.cv_sums()
+        m = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 22)
+        m.set_root()
+        m.cv_set_potentials(phi1, phi2)
+        m.set_counts(ca[0] + cb[0], ca[1] + cb[1], (ca[2] + cb[2])[:3])
+        m.cv_set_sums(*(x + y for x, y in zip(sa, sb)))
+        got = m.cv_estimates(0.7, 1.3)
+        want = whole.cv_estimates(0.7, 1.3)
+        m.close()
+    finally:
+        for G in (whole, a, b):
+            G.close()
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    assert got[2] == want[2] and got[3] == want[3]
