@@ -114,9 +114,32 @@ __device__ __forceinline__ uint32_t free_mask(uint4 a, uint4 b, uint4 c, uint4 d
     return m;
 }
 
-__device__ __forceinline__ uint64_t ld_row(const int2 *rowinfo, int32_t u)
+// The graph (row records, columns) should stay in L2 while the state words
+// stream through it.
+__device__ __forceinline__ uint64_t policy_evict_last()
 {
-    return *reinterpret_cast<const unsigned long long *>(rowinfo + u);
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t ld_row(const int2 *rowinfo, int32_t u, uint64_t pol)
+{
+    uint64_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(rowinfo + u), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int32_t ld_col(const int32_t *a, uint64_t pol)
+{
+    int32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+// Target of draw k at node u (row record r of u), sample i.
+__device__ __forceinline__ int32_t arrow_of(const int32_t *col, uint64_t r, uint32_t u, uint32_t k, uint32_t i,
+                                            uint32_t key0, uint32_t key1, uint64_t pol)
+{
+    return ld_col(col + (int64_t)(int32_t)(uint32_t)r + (int64_t)lap::below(lap::philox_r64(u, k, i, 0u, key0, key1),
+                                                                             (uint32_t)(r >> 32)), pol);
 }
 
 enum : uint32_t { G_SCAN = 0, G_STEP, G_MOVE, G_DONE };
@@ -144,6 +167,7 @@ __global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
     const uint32_t nchunks = (uint32_t)((n + (int32_t)kChunk - 1) / (int32_t)kChunk);   // chunks holding nodes
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
     const uint64_t limit = p.step_limit;
+    const uint64_t keep = policy_evict_last();
     unsigned long long acc1 = 0, acc2 = 0;
     unsigned int bad = 0;
 
@@ -182,7 +206,7 @@ __global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
         uint32_t sp = 0;                     // path length (stack entries 0 .. sp-2 in memory, the head in `top`)
         uint32_t top = 0;
         int32_t w = 0;                       // target of the head's arrow (G_MOVE)
-        uint32_t ew = 0;                     // expected word of w for the claim
+        uint32_t ew = 0;                     // expected word of w for the claim (all ones: read it first)
         uint64_t y1 = 0;
         uint32_t iter = 0;
         unsigned long long tprog = 0;        // last progress (set when a wait or an idle sweep begins)
@@ -214,7 +238,7 @@ __global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
                 // Claim the start: most nodes are untouched (word 0) on the first pass.
                 uint32_t expect = 0u;
                 uint32_t old = cas_word(st + s, expect, mine);
-                const uint64_t row = ld_row(rowinfo, s);
+                const uint64_t row = ld_row(rowinfo, s, keep);
                 for (int t = 0; t < 8 && old != expect && w_free(old); ++t) {
                     expect = old;
                     old = cas_word(st + s, expect, expect | mine);
@@ -246,21 +270,36 @@ __global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
                     if (y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; withdraw = true; phase = G_DONE; break; }
                 }
                 top = (uint32_t)h | (hk << kNodeBits);
-                const uint32_t deg = (uint32_t)(hrow >> 32);
-                w = col[(int64_t)(int32_t)(uint32_t)hrow + (int64_t)lap::below(lap::philox_r64((uint32_t)h, kd, i, 0u, key0, key1), deg)];
-                ew = 0u;
+                w = arrow_of(col, hrow, (uint32_t)h, kd, i, key0, key1, keep);
+                ew = 0xFFFFFFFFu;
                 phase = G_MOVE;
                 if (((++iter) & 255u) == 0u && ld_u32(&ctl->status)) { phase = G_DONE; break; }
                 // fall through to the claim in the same iteration
             }
             if (phase == G_MOVE) {
-                uint32_t old = cas_word(st + w, ew, ew | mine);
-                const uint64_t row = ld_row(rowinfo, w);
-                for (int t = 0; t < 8 && old != ew && w_free(old); ++t) {
+                // Read w's word; only a free node needs the compare-and-swap
+                // that claims it (InTree is final, so a plain read of it is
+                // conclusive; most steps end in the tree).
+                const uint64_t row = ld_row(rowinfo, w, keep);
+                uint32_t old;
+                bool claimed = false;
+                if (ew == 0xFFFFFFFFu) {
+                    old = ld_word(st + w);
+                    if (w_free(old)) {
+                        ew = old;
+                        old = cas_word(st + w, ew, ew | mine);
+                        claimed = old == ew;
+                    }
+                } else {
+                    old = cas_word(st + w, ew, ew | mine);
+                    claimed = old == ew;
+                }
+                for (int t = 0; t < 8 && !claimed && w_free(old); ++t) {
                     ew = old;
                     old = cas_word(st + w, ew, ew | mine);
+                    claimed = old == ew;
                 }
-                if (old == ew) {
+                if (claimed) {
                     // w joins the path as its new head.
                     if (sp >= cap) { withdraw = true; phase = G_DONE; break; }
                     stk[sp - 1] = top;
@@ -327,7 +366,7 @@ __global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
                 if (!waiting) { waiting = true; tprog = now_ns(); }
                 else if (now_ns() - tprog > kStallNs) { withdraw = true; phase = G_DONE; break; }
                 if (ld_u32(&ctl->status)) { phase = G_DONE; break; }
-                ew = 0u;
+                ew = 0xFFFFFFFFu;
                 __nanosleep(100);
                 continue;
             }
@@ -357,9 +396,9 @@ __global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
                 while (u != v) {
                     atomicAdd(&p.cnt2[u], 1ull);
                     if (++t > limit) { bad |= LAP_DEV_STEP_LIMIT; break; }
-                    const uint64_t r = ld_row(rowinfo, u);
-                    u = col[(int64_t)(int32_t)(uint32_t)r +
-                            (int64_t)lap::below(lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1), (uint32_t)(r >> 32))];
+                    const uint64_t r = ld_row(rowinfo, u, keep);
+                    u = ld_col(col + (int64_t)(int32_t)(uint32_t)r +
+                               (int64_t)lap::below(lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1), (uint32_t)(r >> 32)), keep);
                 }
                 const unsigned long long sy1 = ld_u64(&ctl->y1);
                 acc1 += sy1;
@@ -368,12 +407,12 @@ __global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
             if (j == 1u) {
                 // Alg. 4: the v-absorbed walk from s ~ pi (the head of a uniform arc); Y2 = its length.
                 uint64_t y2 = 0;
-                int32_t u = col[(int64_t)lap::below(lap::philox_r64(0u, 0u, i, 2u, key0, key1), (uint64_t)p.g.arcs)];
+                int32_t u = ld_col(col + (int64_t)lap::below(lap::philox_r64(0u, 0u, i, 2u, key0, key1), (uint64_t)p.g.arcs), keep);
                 while (u != v) {
                     if (++y2 > limit) { bad |= LAP_DEV_STEP_LIMIT; break; }
-                    const uint64_t r = ld_row(rowinfo, u);
-                    u = col[(int64_t)(int32_t)(uint32_t)r +
-                            (int64_t)lap::below(lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1), (uint32_t)(r >> 32))];
+                    const uint64_t r = ld_row(rowinfo, u, keep);
+                    u = ld_col(col + (int64_t)(int32_t)(uint32_t)r +
+                               (int64_t)lap::below(lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1), (uint32_t)(r >> 32)), keep);
                 }
                 acc2 += y2;
                 if (p.y2_out) p.y2_out[i - p.first] = y2;
