@@ -75,23 +75,25 @@ typedef enum {
     LAP_OPT_CURSOR = 4,        /* first sample id of the next lap_sample (default 0); only before the
                                   first sample after lap_set_root.  Lets several processes or GPUs
                                   draw disjoint sample-id ranges whose counts add up exactly. */
-    LAP_OPT_KERNEL = 5,        /* 0 = automatic, 1 = 8-byte state per node, 2 = 1-byte state per node
-                                  (default when n < 2^27).  Kernel 2 keeps draw counts above 30 (and,
-                                  with LAP_OPT_PATHS = 1, path departure counts above 14) in a
-                                  table per sample of 8-byte entries, as many as the next power
+    LAP_OPT_KERNEL = 5,        /* 0 = automatic: kernel 3 for calls of at most 320 samples per SM
+                                  when it applies, else kernel 2 when n < 2^27, else kernel 1.
+                                  1 = 8-byte state per node.
+                                  2 = 1-byte state per node.  Kernel 2 keeps draw counts above 30
+                                  (and, with LAP_OPT_PATHS = 1, path departure counts above 14) in
+                                  a table per sample of 8-byte entries, as many as the next power
                                   of two >= n, 256 to 8192.  A sample that does not fit kernel 2
                                   (more such nodes than the table holds, or a loop-erased path
-                                  longer than the stack) is withdrawn and re-run with kernel 1:
-                                  results are identical either way.  3 = several walkers per sample
-                                  (LAP_OPT_WALKERS lanes share one Wilson run; 2 bytes of state per
-                                  node): more samples' worth of independent memory chains when a
-                                  call has few samples.  Kernel 3 needs n < 2^22 and covers the
-                                  plain estimators only (LAP_OPT_PATHS = 0, no control variate;
-                                  otherwise kernel 2 runs).  Its samples that do not fit (a node
-                                  drawn 1023 times, a path longer than a walker's stack, a walker
-                                  without progress for 4 s) are withdrawn and re-run with kernel 1.
+                                  longer than the stack) is withdrawn and re-run with kernel 1.
+                                  3 = several walkers per sample (LAP_OPT_WALKERS lanes share one
+                                  Wilson run; 2 bytes of state per node): more independent memory
+                                  chains when a call has few samples, and each sample finishes
+                                  sooner.  Kernel 3 needs n < 2^22 and covers the plain estimators
+                                  only (LAP_OPT_PATHS = 0, no control variate; otherwise kernel 2
+                                  runs).  Its samples that do not fit (a node drawn 1023 times, a
+                                  path longer than a walker's stack, a walker without progress for
+                                  4 s) are withdrawn and re-run with kernel 1.
                                   Counts are identical with every kernel. */
-    LAP_OPT_STACK = 6,         /* loop-erased path capacity per sample of kernel 2; 0 = default
+    LAP_OPT_STACK = 6,         /* loop-erased path capacity per sample (kernel 2) or walker (kernel 3); 0 = default
                                   (16 sqrt(n) rounded up to a power of two, at least 1024) */
     LAP_OPT_PATHS = 7,         /* 0 (default): the uniform-start and pi-start v-absorbed walks take
                                   their own draws, as Alg. 2 and Alg. 4 print them.  1: they are the
@@ -121,10 +123,12 @@ typedef enum {
 
 /* Statistics for lap_get_stat. */
 typedef enum {
-    LAP_STAT_SLOTS = 1,        /* samples in flight per launch with the current workspace and kernel */
-    LAP_STAT_KERNEL = 2,       /* kernel the next lap_sample will use (1 or 2) */
-    LAP_STAT_FALLBACKS = 3     /* samples re-run with kernel 1 after kernel 2 withdrew them, since
+    LAP_STAT_SLOTS = 1,        /* samples in flight per launch of a large call (LAP_STAT_KERNEL) with
+                                  the current workspace (kernel 3: groups of walkers) */
+    LAP_STAT_KERNEL = 2,       /* kernel a large lap_sample call will use (1, 2 or 3) */
+    LAP_STAT_FALLBACKS = 3,    /* samples re-run with kernel 1 after kernel 2 or 3 withdrew them, since
                                   lap_set_root (synchronises) */
+    LAP_STAT_LAST_KERNEL = 4   /* kernel of the last lap_sample call (0 before any) */
 } lap_stat;
 
 /* Library version as major*10000 + minor*100 + patch. */
@@ -239,6 +243,24 @@ lap_status lap_kemeny(lap_graph *g, double *out1);
  * errors.
  */
 lap_status lap_lv_row(lap_graph *g, double *out, int out_on_device);
+
+/*
+ * Solves L_v x = b in FP64 (L_v: the Laplacian without row and column v,
+ * Section 3.1; symmetric positive definite for a connected graph) by
+ * conjugate gradients with the Jacobi preconditioner D^{-1}, until
+ * ||b - L_v x|| <= rtol ||b|| or maxiter iterations.  b[v] is ignored and
+ * x[v] = 0.  The sampled quantities that are linear in L_v^{-1} applied to a
+ * known vector come out exactly: b = 1 gives n y2(u) of Alg. 2 and the
+ * row-sum terms of (L^+)_uu (Section 3.1, element-wise Theorem 1); b = d
+ * gives the hitting times h(u, v) and E[Y2] = d^T x / 2m (Section 3.2,
+ * Alg. 4); b = e_s gives row s of L_v^{-1}.  b, x: n doubles, host or
+ * device (on_device); iterations and residual (may be NULL) receive the
+ * iterations run and the final relative residual.  Synchronises; allocates
+ * and frees 4 n + 2056 doubles of device scratch.  Errors: LAP_ERR_NO_ROOT,
+ * LAP_ERR_INVALID_ARG, LAP_ERR_OOM, LAP_ERR_CUDA.
+ */
+lap_status lap_lv_solve(lap_graph *g, const double *b, double *x, int on_device, double rtol, int32_t maxiter,
+                        int32_t *iterations, double *residual);
 
 /*
  * Two more quantities of the same diagonal (Section 5, "Discussions"):

@@ -115,10 +115,19 @@ bool group_ok(const lap_graph *g)
            (!g->ws || g->ws_bytes >= slot_bytes_of(g, LAP_KERNEL_GROUP));
 }
 
-int choose_kernel(const lap_graph *g)
+// Calls of at most this many samples per SM take kernel 3 automatically:
+// below it one lane per sample leaves the GPU short of independent memory
+// chains (measured on one GB300: kernel 3 ahead up to 32,768 samples on
+// Barabasi-Albert 10^6 and R-MAT scale 22, behind at 65,536 on the former).
+constexpr uint64_t kGroupAutoPerSm = 320;
+
+// n_samples: the size of the call (0: a call large enough for kernel 2).
+int choose_kernel(const lap_graph *g, uint64_t n_samples = 0)
 {
     if (g->kernel_opt == LAP_KERNEL_WIDE) return LAP_KERNEL_WIDE;
     if (g->kernel_opt == LAP_KERNEL_GROUP && group_ok(g)) return LAP_KERNEL_GROUP;
+    if (g->kernel_opt == 0 && n_samples > 0 && n_samples <= kGroupAutoPerSm * (uint64_t)g->num_sms && group_ok(g))
+        return LAP_KERNEL_GROUP;
     if (g->n >= (1 << 27) || g->compact_disabled) return LAP_KERNEL_WIDE;
     if (g->ws && g->ws_bytes < slot_bytes_of(g, LAP_KERNEL_COMPACT)) return LAP_KERNEL_WIDE;
     return LAP_KERNEL_COMPACT;
@@ -423,6 +432,7 @@ lap_status lap_get_stat(lap_graph *g, int32_t stat, int64_t *value)
     switch (stat) {
     case LAP_STAT_SLOTS: *value = (int64_t)slots_for(g, choose_kernel(g), 0); return LAP_OK;
     case LAP_STAT_KERNEL: *value = choose_kernel(g); return LAP_OK;
+    case LAP_STAT_LAST_KERNEL: *value = g->used_kernel; return LAP_OK;
     case LAP_STAT_FALLBACKS: {
         lap_status s = resolve_pending(g);
         if (s != LAP_OK) return s;
@@ -557,10 +567,11 @@ static lap_status sample_chunk(lap_graph *g, uint64_t n_samples, uint64_t seed, 
     if (g->cursor + n_samples > (1ull << 32)) return fail(g, LAP_ERR_TOO_LARGE, "sample ids are limited to 2^32");
     if (n_samples == 0) return LAP_OK;
     if ((s = resolve_pending(g)) != LAP_OK) return s;
-    const int kernel = choose_kernel(g);
+    const int kernel = choose_kernel(g, n_samples);
     if ((s = ensure_workspace(g, kernel)) != LAP_OK) return s;
     g->seed = seed;
     g->seed_set = true;
+    g->used_kernel = kernel;
 
     LapSampleLaunch p;
     memset(&p, 0, sizeof(p));
@@ -710,6 +721,45 @@ lap_status lap_lv_row(lap_graph *g, double *out, int out_on_device)
     }
     LAP_CUDA(g, lap_launch_lv_row(g->d_rowinfo, g->n, g->omega, g->d_cnt2, g->d_aux, g->stream));
     return copy_out(g, out, g->d_aux, sizeof(double) * (size_t)g->n, 0);
+}
+
+lap_status lap_lv_solve(lap_graph *g, const double *b, double *x, int on_device, double rtol, int32_t maxiter,
+                        int32_t *iterations, double *residual)
+{
+    lap_status s = check_sticky(g);
+    if (s != LAP_OK) return s;
+    if (!b || !x) return fail(g, LAP_ERR_INVALID_ARG, "b and x must be set");
+    if (g->root < 0) return fail(g, LAP_ERR_NO_ROOT, "lap_set_root has not been called");
+    if (!(rtol > 0.0) || maxiter < 1) return fail(g, LAP_ERR_INVALID_ARG, "rtol must be > 0 and maxiter >= 1");
+    const size_t n = (size_t)g->n;
+    double *scratch = nullptr, *db = nullptr, *dx = nullptr;
+    auto release = [&]() {
+        cudaStreamSynchronize(g->stream);
+        cudaFree(scratch);
+        cudaFree(db);
+        cudaFree(dx);
+    };
+    bool ok = dalloc(&scratch, 4 * n + 2 * 1024 + 8) == cudaSuccess;
+    if (ok && !on_device) ok = dalloc(&db, n) == cudaSuccess && dalloc(&dx, n) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        release();
+        return fail(g, LAP_ERR_OOM, "solver scratch: device allocation failed");
+    }
+    cudaError_t e = cudaSuccess;
+    if (!on_device) e = cudaMemcpyAsync(db, b, sizeof(double) * n, cudaMemcpyHostToDevice, g->stream);
+    int32_t it = 0;
+    double res = 0.0;
+    if (e == cudaSuccess)
+        e = lap_run_lv_solve(g->d_rowinfo, g->d_col, g->n, g->root, on_device ? b : db, on_device ? x : dx, scratch,
+                             rtol, maxiter, &it, &res, g->stream);
+    if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(x, dx, sizeof(double) * n, cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    release();
+    if (e != cudaSuccess) return cuda_fail(g, e, "lap_lv_solve");
+    if (iterations) *iterations = it;
+    if (residual) *residual = res;
+    return LAP_OK;
 }
 
 lap_status lap_kemeny(lap_graph *g, double *out1)

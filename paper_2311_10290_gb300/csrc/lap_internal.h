@@ -156,6 +156,11 @@ struct LapBatchLaunch {
 cudaError_t lap_launch_batch(const LapBatchLaunch &p, bool probe, cudaStream_t st);
 int lap_batch_block(const LapBatchLaunch &p);
 uint64_t lap_batch_resident_lanes(int block, int num_sms);
+// solve.cu: conjugate gradients for L_v x = b; scratch: 4 n + 2 * 1024 + 8 doubles
+cudaError_t lap_run_lv_solve(const int2 *rowinfo, const int32_t *col, int32_t n, int32_t v, const double *b, double *x,
+                             double *scratch, double rtol, int32_t maxiter, int32_t *iterations, double *residual,
+                             cudaStream_t st);
+
 // finalize.cu: finalize of every graph of a batch, bit-identical per graph to
 // lap_launch_finalize; red holds graphs * (1024 + 2) doubles.
 cudaError_t lap_launch_finalize_batch(const LapBatchGraph *graphs, int32_t n_graphs, int32_t max_n, uint64_t omega,
@@ -291,6 +296,7 @@ struct lap_graph {
     int32_t path_start = -1;                // LAP_OPT_PATH_START (-1: uniform start)
     uint32_t stack_cap = 0;                 // 0: default, about 16 sqrt(n)
     int last_kernel = 0;                    // layout the workspace currently holds
+    int used_kernel = 0;                    // kernel of the last lap_sample call (LAP_STAT_LAST_KERNEL)
     bool compact_disabled = false;          // set after a compact launch overflowed
     int64_t fallbacks = 0;
 

@@ -29,7 +29,7 @@ LAP_OPT_STEP_LIMIT, LAP_OPT_SLOTS, LAP_OPT_BLOCK, LAP_OPT_CURSOR, LAP_OPT_KERNEL
 LAP_OPT_PATHS = 7
 LAP_OPT_PATH_START = 8
 LAP_OPT_WALKERS = 9
-LAP_STAT_SLOTS, LAP_STAT_KERNEL, LAP_STAT_FALLBACKS = 1, 2, 3
+LAP_STAT_SLOTS, LAP_STAT_KERNEL, LAP_STAT_FALLBACKS, LAP_STAT_LAST_KERNEL = 1, 2, 3, 4
 LAP_MLP_PARAMS = 4866
 LAP_BOPT_LANES, LAP_BOPT_CLAIM, LAP_BOPT_ORDER, LAP_BOPT_BLOCK, LAP_BOPT_STACK, LAP_BOPT_PATHS = 1, 2, 3, 4, 5, 6
 LAP_BSTAT_LANES, LAP_BSTAT_CLAIM, LAP_BSTAT_UNITS, LAP_BSTAT_RERUNS, LAP_BSTAT_GRAPH_CAPTURES = 1, 2, 3, 4, 5
@@ -71,6 +71,8 @@ def library():
         "lap_ldiag": (i32, [vp, vp, ctypes.c_int]),
         "lap_kemeny": (i32, [vp, vp]),
         "lap_lv_row": (i32, [vp, vp, ctypes.c_int]),
+        "lap_lv_solve": (i32, [vp, vp, vp, ctypes.c_int, ctypes.c_double, i32, ctypes.POINTER(i32),
+                               ctypes.POINTER(ctypes.c_double)]),
         "lap_batch_set_path_start": (i32, [vp, i32, i32]),
         "lap_batch_lv_row": (i32, [vp, i32, vp, ctypes.c_int]),
         "lap_counts": (i32, [vp, vp, vp, vp, ctypes.c_int]),
@@ -232,6 +234,22 @@ def lap_ldiag(h, n, out=None):
 
 def lap_lv_row(h, n, out=None):
     return _out(h, library().lap_lv_row, n, np.float64, out)
+
+
+def lap_lv_solve(h, n, b, rtol=1e-12, maxiter=100000, out=None):
+    """x = L_v^{-1} b; b a float64 numpy array (host) or CUDA tensor (device);
+    returns (x, iterations, residual)."""
+    it, res = ctypes.c_int32(0), ctypes.c_double(0.0)
+    if _is_torch(b):
+        x = out if out is not None else b.new_empty(n)
+        _check(library().lap_lv_solve(h, _dp(b), _dp(x), 1, float(rtol), int(maxiter), ctypes.byref(it),
+                                      ctypes.byref(res)), h)
+    else:
+        bb = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(n) if out is None else out
+        _check(library().lap_lv_solve(h, _host_ptr(bb), _host_ptr(x), 0, float(rtol), int(maxiter),
+                                      ctypes.byref(it), ctypes.byref(res)), h)
+    return x, it.value, res.value
 
 
 def lap_hops(h, n, out=None):
@@ -670,6 +688,9 @@ class LapGraph:
 
     def lv_row(self, out=None):
         return lap_lv_row(self.h, self.n, out)
+
+    def lv_solve(self, b, rtol=1e-12, maxiter=100000, out=None):
+        return lap_lv_solve(self.h, self.n, b, rtol, maxiter, out)
 
     def counts(self, per_node=True):
         return lap_counts(self.h, self.n, per_node)

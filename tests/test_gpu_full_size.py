@@ -7,9 +7,9 @@ the benchmark uses.
   and count-table tags separate consecutive samples of one lane).
 * R-MAT scale 22, edge factor 16, largest component (2.4M nodes, 1.28e8
   arcs, a 162,713-degree hub as the root): complete counts bit-exact for 48
-  samples on both kernels, and the benchmark's own launch (16,384 samples,
-  the default workspace) checked on sampled ids one by one plus invariants
-  that hold at any size.
+  samples on the 8-byte and 1-byte kernels, and the benchmark's own launch
+  (16,384 samples, the default workspace: the several-walkers kernel)
+  checked on sampled ids one by one plus invariants that hold at any size.
 
 Counts are integers: compared bit for bit."""
 import os
@@ -24,7 +24,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 from paper_2311_10290_gb300.lap import (LAP_OPT_KERNEL, LAP_OPT_SLOTS, LAP_STAT_FALLBACKS,  # noqa: E402
-                                        LAP_STAT_KERNEL, LapGraph)
+                                        LAP_STAT_KERNEL, LAP_STAT_LAST_KERNEL, LapGraph)
 
 THREADS = max(1, min(16, os.cpu_count() or 1))
 
@@ -86,6 +86,7 @@ def test_full_size_rmat22_bench_launch_sampled(rmat22):
         y1, y2 = G.sample_trace(omega, seed)
         c1, c2, s = G.counts()
         assert G.stat(LAP_STAT_FALLBACKS) == 0
+        assert G.stat(LAP_STAT_LAST_KERNEL) == 3             # several walkers per sample at this size
         y1 = y1.cpu().numpy().astype(np.uint64)
         y2 = y2.cpu().numpy().astype(np.uint64)
     finally:

@@ -97,13 +97,24 @@ def test_counts_and_estimates_match_oracle(name, maker, root, omega, kernel):
     assert_parity(g, r, c, omega)
 
 
-def test_compact_kernel_is_the_default_and_does_not_fall_back_on_social_graphs():
+def test_default_kernels_do_not_fall_back_on_social_graphs():
+    """Large calls take the 1-byte kernel (LAP_STAT_KERNEL), a call of a few
+    thousand samples the several-walkers kernel (LAP_STAT_LAST_KERNEL); neither
+    withdraws a sample on a Barabasi-Albert graph."""
+    from paper_2311_10290_gb300.lap import LAP_STAT_LAST_KERNEL
     g = I.ba(20000, 4, seed=1)
-    st = {}
-    r = gpu_run(g, 5, 2000, stats=st)
-    assert st == {"kernel": 2, "fallbacks": 0}
-    c = oracle_run(g, r["v"], 5, 2000, threads=4)
-    assert_parity(g, r, c, 2000)
+    G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 30)
+    try:
+        v = G.set_root()
+        assert G.stat(LAP_STAT_KERNEL) == 2 and G.stat(LAP_STAT_LAST_KERNEL) == 0
+        G.sample(2000, 5)
+        assert G.stat(LAP_STAT_LAST_KERNEL) == 3 and G.stat(LAP_STAT_FALLBACKS) == 0
+        c1, c2, s = G.counts()
+    finally:
+        G.close()
+    c = oracle_run(g, v, 5, 2000, threads=4)
+    assert np.array_equal(c1, c.cnt1) and np.array_equal(c2, c.cnt2)
+    assert int(s[1]) == c.sum_y1 and int(s[2]) == c.sum_y2
 
 
 PATH_CASES = [
