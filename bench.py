@@ -87,6 +87,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ws-frac", type=float, default=0.6, help="fraction of free HBM lent as Wilson state")
     ap.add_argument("--ws-gb", type=float, default=0.0, help="cap on the Wilson-state workspace in GB (profiler runs)")
+    ap.add_argument("--tta-large", default="ba_1m:16384,rmat_22:65536",
+                    help="time to accuracy on large graphs: workload:largest omega of the grid, comma separated")
+    ap.add_argument("--tta-forms", default="plain,paths,cv", help="estimator forms of the large-graph runs")
+    ap.add_argument("--tta-seeds", type=int, default=10, help="seeds (disjoint id ranges) per form")
     ap.add_argument("--kernel", type=int, default=0, help="LAP_OPT_KERNEL for the timed steps (0: the library's choice)")
     ap.add_argument("--walkers", type=int, default=8, help="LAP_OPT_WALKERS (kernel 3)")
     ap.add_argument("--cv-graphs", type=int, default=200, help="training graphs for the learned control variate (0: skip)")
@@ -240,6 +244,20 @@ def cpu_time_to_accuracy(omega, seed=7):
             "ecc_max_rel_err": float(np.max(np.abs(ec - ecc_t) / ecc_t)), "kc_rel_err": abs(kc - kc_t) / kc_t}
 
 
+def cpu_oracle_extrapolated(g, v, seed, omega, sample=256, first_id=1 << 29):
+    """The oracle on all host cores for a bounded sample of `sample` ids,
+    extrapolated linearly to omega samples (the samples are independent and
+    identically distributed, so the time grows in proportion)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.sample_threads(g.row_ptr, g.col, v, seed, first_id, sample, cores)
+    dt = time.perf_counter() - t0
+    return {"omega": int(omega), "sample": sample, "sample_seconds": round(dt, 2), "cores": cores, "kind": "oracle",
+            "seconds_extrapolated": dt * omega / sample,
+            "note": "measured on %d sample ids, extrapolated linearly to omega" % sample}
+
+
 # ------------------------------------------------------------ accuracy
 
 def read_truth():
@@ -348,120 +366,142 @@ def time_to_accuracy(torch, LapGraph, seeds=10, target=1e-2, params=None, paths=
     return res
 
 
-def large_truth(torch, LapGraph, g, v, seeds, omega_max):
-    """Plain runs of `seeds` disjoint id ranges of omega_max samples each (ids
-    [s * omega_max, (s + 1) * omega_max), Philox seed 1): their pooled
-    integer counts, the statistical part of the ground truth.  Returns
-    (pooled cnt1 as int64, pooled sum Y1, samples, GPU seconds)."""
-    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR
-    cnt = np.zeros(g.n, dtype=np.int64)
-    sy1, secs = 0, 0.0
-    H = LapGraph(g.row_ptr, g.col, workspace_bytes=int(torch.cuda.mem_get_info()[0] * 0.45))
+def omega_grid(omega_max, lo=256):
+    """round(lo * 2^(k/2)) up to omega_max (the last point is omega_max)."""
+    out, k = [], 0
+    while True:
+        w = int(round(lo * 2.0 ** (k / 2.0)))
+        if w >= omega_max:
+            out.append(int(omega_max))
+            return out
+        out.append(w)
+        k += 1
+
+
+class CheckpointBlocks:
+    """One handle per block of the omega grid, each on its own CUDA stream, so
+    that every block of a seed samples at once: the estimate at grid point k
+    is the sum of blocks 0..k, i.e. the sample ids [first, first + grid[k]).
+    A further handle (which never samples) finalizes the running sums with
+    the library (lap_set_counts, lap_cv_set_sums, lap_ecc / lap_cv_estimates)."""
+
+    def __init__(self, torch, LapGraph, g, v, grid, form, ws_total, phi=None):
+        from paper_2311_10290_gb300.lap import LAP_OPT_PATHS
+        self.torch, self.g, self.v, self.grid, self.form, self.phi = torch, g, v, grid, form, phi
+        self.bounds = [0] + list(grid)
+        sizes = [self.bounds[k + 1] - self.bounds[k] for k in range(len(grid))]
+        self.streams = [torch.cuda.Stream() for _ in sizes]
+        self.handles = []
+        # Lanes are shared out in proportion to the block sizes, so that the
+        # blocks' kernels fit on the GPU together and run side by side.
+        from paper_2311_10290_gb300.lap import LAP_OPT_SLOTS
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        lanes = sms * 1024
+        walkers = 8 if form == "plain" else 1          # kernel 3 counts groups of 8 lanes as one slot
+        for k, sz in enumerate(sizes):
+            ws = max(8 * g.n * 4, int(ws_total * sz / grid[-1]))
+            H = LapGraph(g.row_ptr, g.col, workspace_bytes=ws, stream=self.streams[k])
+            H.set_option(LAP_OPT_PATHS, 1 if form == "paths" else 0)
+            H.set_option(LAP_OPT_SLOTS, max(1, int(lanes / walkers * sz / grid[-1])))
+            self.handles.append(H)
+        self.F = LapGraph(g.row_ptr, g.col, workspace_bytes=8 * g.n)
+        self.F.set_root(v)
+        if phi is not None:
+            self.F.cv_set_potentials(*phi)
+
+    def close(self):
+        for H in self.handles + [self.F]:
+            H.close()
+
+    def run(self, first, seed, betas=None):
+        """All blocks of one seed; returns (list of (ECC tensor float32 on the
+        device, Kemeny) per grid point, final (cnt1 int64, sum Y1))."""
+        from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR
+        torch, g = self.torch, self.g
+        for k, H in enumerate(self.handles):
+            H.set_root(self.v)
+            H.set_option(LAP_OPT_CURSOR, first + self.bounds[k])
+            if self.phi is not None:
+                H.cv_set_potentials(*self.phi)
+            H.sample(self.bounds[k + 1] - self.bounds[k], seed)
+        c1 = np.zeros(g.n, dtype=np.uint64)
+        c2 = np.zeros(g.n, dtype=np.uint64)
+        sums = np.zeros(3, dtype=np.uint64)
+        a = [np.zeros(g.n, dtype=np.int64) for _ in range(3)] if self.phi is not None else None
+        est = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        out = []
+        for k, H in enumerate(self.handles):
+            b1, b2, bs = H.counts()
+            c1 += b1
+            c2 += b2
+            sums += bs[:3]
+            self.F.set_counts(c1, c2, sums)
+            if a is None:
+                self.F.ecc(est)
+                kc = self.F.kemeny()
+            else:
+                for x, y in zip(a, H.cv_sums()):
+                    x += y
+                self.F.cv_set_sums(*a)
+                _, _, kc, _ = self.F.cv_estimates(*betas, ecc_out=est)
+            out.append((est.float().clone(), kc))
+        return out, (c1.astype(np.int64), int(sums[1]))
+
+
+def exact_parts(torch, LapGraph, g, v, rtol=1e-12):
+    """The parts of the large-graph ground truth that one FP64 solve each
+    fixes, by the library's conjugate-gradient solver (lap_lv_solve):
+    y2(u) = (L_v^{-1} 1)_u / n, lvv = (L^+)_vv = (1/n) sum_u y2(u), and
+    E[Y2] = d^T L_v^{-1} d / 2m."""
+    H = LapGraph(g.row_ptr, g.col, workspace_bytes=8 * g.n)
     try:
-        for s in range(seeds):
-            H.set_root(v)
-            H.set_option(LAP_OPT_CURSOR, s * omega_max)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            H.sample(omega_max, 1)
-            b.record()
-            c1, _, sums = H.counts()
-            secs += a.elapsed_time(b) / 1e3
-            cnt += c1.astype(np.int64)
-            sy1 += int(sums[1])
+        H.set_root(v)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d = torch.from_numpy(np.diff(g.row_ptr.astype(np.int64)).astype(np.float64)).cuda()
+        r1, it1, res1 = H.lv_solve(torch.ones(g.n, dtype=torch.float64, device="cuda"), rtol=rtol)
+        hv, it2, res2 = H.lv_solve(d, rtol=rtol)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
     finally:
         H.close()
-    return cnt, sy1, seeds * omega_max, secs
+    y2 = r1 / g.n
+    return {"y2": y2, "lvv": float(y2.sum().item()) / g.n, "ey2": float((d * hv).sum().item()) / float(g.arcs),
+            "info": {"iterations": [it1, it2], "residuals": [res1, res2], "seconds": round(secs, 3), "rtol": rtol}}
 
 
-def large_ecc_truth(torch, g, v, cnt1, omega_pool, sum_y1, exact):
+def ecc_truth(torch, g, v, cnt1, omega_pool, sum_y1, exact):
     """ECC and Kemeny ground truth from pooled plain counts plus the exact
     parts of the sparse solves: (L^+)_uu = cnt1_pool(u) / (omega_pool d_u)
     - 2 y2(u) + lvv (u != v), (L^+)_vv = lvv (Section 3.1, element-wise
     Theorem 1), c(u) = (n-1) / (n (L^+)_uu + Tr L^+) (Section 2), and
     kappa = sum Y1 / omega_pool - E[Y2] (Alg. 4)."""
     d = torch.from_numpy(np.diff(g.row_ptr.astype(np.int64)).astype(np.float64)).cuda()
-    y2 = torch.from_numpy(exact["y2"]).cuda()
-    ld = torch.from_numpy(cnt1).cuda().double() / (float(omega_pool) * d) - 2.0 * y2 + exact["lvv"]
+    ld = torch.from_numpy(cnt1).cuda().double() / (float(omega_pool) * d) - 2.0 * exact["y2"] + exact["lvv"]
     ld[v] = exact["lvv"]
-    tr = ld.sum()
-    ecc = (g.n - 1) / (g.n * ld + tr)
+    ecc = (g.n - 1) / (g.n * ld + ld.sum())
     kc = float(sum_y1) / float(omega_pool) - exact["ey2"]
-    return ecc, kc
+    return ecc.float(), kc
 
 
-def time_to_accuracy_large(torch, LapGraph, g, v, truth, omega_max, form, params=None, seeds=10, target=1e-2):
-    """Time to relative error 1e-2 on a large graph (Section 6 protocol: error
-    metrics of ECC (max over nodes) and Kemeny; mean over seeds).  Each seed
-    draws its own id range, disjoint from the truth pool's, on the grid
-    omega = round(256 * 2^(k/2)) up to omega_max; the errors are taken
-    against the ground truth of `pool` (plain counts of other ids) with the
-    exact sparse-solve parts; the smallest omega whose mean errors are both
-    <= target is then timed in one fresh run (sampling plus finalize)."""
-    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, LAP_OPT_PATHS
-    grid = []
-    k = 0
-    while True:
-        w = int(round(256 * 2.0 ** (k / 2.0)))
-        if w > omega_max:
-            break
-        grid.append(w)
-        k += 1
-    ecc_t, kc_t, truth_samples = truth
-    ws = int(torch.cuda.mem_get_info()[0] * 0.45)
-    H = LapGraph(g.row_ptr, g.col, workspace_bytes=ws)
-    base = 1 << 30                              # ids far after the truth pool's
-    errs = np.zeros((seeds, len(grid), 2))
-    betas = (0.0, 0.0)
-    prep = 0.0
+def timed_run(torch, LapGraph, g, v, omega, first, seed, form, phi=None, betas=None):
+    """One fresh call of omega samples (the library's kernel choice) plus the
+    finalize, timed with CUDA events on the handle's stream; with its
+    algorithmic bytes and roofline fraction."""
+    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, LAP_OPT_PATHS, LAP_STAT_LAST_KERNEL
+    H = LapGraph(g.row_ptr, g.col, workspace_bytes=int(torch.cuda.mem_get_info()[0] * 0.5))
     try:
         H.set_option(LAP_OPT_PATHS, 1 if form == "paths" else 0)
         H.set_root(v)
-        if params is not None:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            _, _, b1, b2 = cv_prepare(H, params, 4242, pilot=8192, batches=8)
-            torch.cuda.synchronize()
-            prep = time.perf_counter() - t0
-            betas = (b1, b2)
+        H.set_option(LAP_OPT_CURSOR, first)
+        if phi is not None:
+            H.cv_set_potentials(*phi)
         est = torch.empty(g.n, dtype=torch.float64, device="cuda")
-        for s in range(seeds):
-            H.set_root(v)
-            H.set_option(LAP_OPT_CURSOR, base + s * omega_max)
-            done = 0
-            for j, w in enumerate(grid):
-                H.sample(w - done, 1)
-                done = w
-                if params is None:
-                    H.ecc(est)
-                    kc = H.kemeny()
-                else:
-                    _, _, kc, _ = H.cv_estimates(*betas, ecc_out=est)
-                errs[s, j, 0] = float(torch.max(torch.abs(est - ecc_t) / ecc_t))
-                errs[s, j, 1] = abs(kc - kc_t) / abs(kc_t)
-        mean = errs.mean(axis=0)
-        found = None
-        for j, w in enumerate(grid):
-            if mean[j, 0] <= target and mean[j, 1] <= target:
-                found = w
-                break
-        res = {"form": form, "seeds": seeds, "grid_max": omega_max, "truth_samples": truth_samples,
-               "curve": [{"omega": w, "ecc_max_rel": round(float(mean[j, 0]), 5), "kc_rel": round(float(mean[j, 1]), 7)}
-                         for j, w in enumerate(grid)]}
-        if params is not None:
-            res["betas"] = list(betas)
-            res["prepare_seconds"] = round(prep, 2)
-        if found is None:
-            res["reached"] = False
-            return res
-        # One fresh run to the found omega (ids of the first seed), timed on the device.
-        H.set_root(v)
-        H.set_option(LAP_OPT_CURSOR, base)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        H.sample(found, 1)
-        if params is None:
+        H.sample(omega, seed)
+        if phi is None:
             H.ecc(est)
             H.kemeny()
         else:
@@ -470,18 +510,104 @@ def time_to_accuracy_large(torch, LapGraph, g, v, truth, omega_max, form, params
         torch.cuda.synchronize()
         secs = a.elapsed_time(b) / 1e3
         _, c2, sums = H.counts()
-        alg = (BYTES_WILSON_STEP * int(sums[1]) + BYTES_TREE_INSERT * (g.n - 1) * found +
-               BYTES_WALK_STEP * (int(c2.sum()) + int(sums[2])))
-        pk = peaks()[0]
-        j = grid.index(found)
-        res.update({"reached": True, "omega": found, "gpu_seconds": secs,
-                    "ecc_max_rel_err_mean": float(mean[j, 0]), "kc_rel_err_mean": float(mean[j, 1]),
-                    "roofline": {"bound": "hbm", "achieved": alg / secs / 1e9, "peak": pk, "unit": "GB/s",
-                                 "frac": alg / secs / 1e9 / pk,
-                                 "note": "algorithmic bytes of the timed run (sampling plus finalize) over its time"}})
-        return res
+        kernel = H.stat(LAP_STAT_LAST_KERNEL)
     finally:
         H.close()
+    alg = (BYTES_WILSON_STEP * int(sums[1]) + BYTES_TREE_INSERT * (g.n - 1) * omega +
+           BYTES_WALK_STEP * (int(c2.sum()) + int(sums[2])))
+    pk = peaks()[0]
+    return {"gpu_seconds": secs, "kernel": kernel, "walk_steps": int(sums[1]) + int(c2.sum()) + int(sums[2]),
+            "roofline": {"bound": "hbm", "achieved": alg / secs / 1e9, "peak": pk, "unit": "GB/s",
+                         "frac": alg / secs / 1e9 / pk,
+                         "note": "algorithmic bytes of the timed call (sampling plus finalize) over its time"}}
+
+
+def time_to_accuracy_large(torch, LapGraph, g, v, exact, omega_max, forms=("plain", "paths", "cv"), params=None,
+                           seeds=10, target=1e-2, ws_frac=0.5):
+    """Time to relative error 1e-2 on a large graph, Section 6's protocol:
+    ECC max relative error over all nodes and Kemeny relative error, each the
+    mean over `seeds` seeds (disjoint sample-id ranges), on the grid
+    round(256 * 2^(k/2)) up to omega_max; the smallest grid point where both
+    means are <= target, then one fresh timed call to it.
+
+    Ground truth: the plain estimates pooled over the plain seeds (all of
+    them for the other forms, whose ids are disjoint; all but the seed itself
+    for a plain seed), with the parts the sparse solves fix exactly (y2,
+    L^+_vv, E[Y2]).  The pool holds at least (seeds - 1) * omega_max samples."""
+    res = {"seeds": seeds, "grid_max": omega_max, "target": target}
+    grid = omega_grid(omega_max)
+    ws_total = int(torch.cuda.mem_get_info()[0] * ws_frac)
+    stored, finals = [], []
+    base = {"plain": 0, "paths": 1 << 30, "cv": (1 << 30) + (1 << 29)}
+    for form in forms:
+        if form == "cv" and params is None:
+            continue
+        t0 = time.perf_counter()
+        phi = betas = None
+        prep = 0.0
+        if form == "cv":
+            from paper_2311_10290_gb300.lap import LapGraph as LG
+            P = LG(g.row_ptr, g.col, workspace_bytes=int(torch.cuda.mem_get_info()[0] * 0.3))
+            try:
+                P.set_root(v)
+                torch.cuda.synchronize()
+                tp = time.perf_counter()
+                phi1, phi2, b1, b2 = cv_prepare(P, params, 4242, pilot=8192, batches=8)
+                torch.cuda.synchronize()
+                prep = time.perf_counter() - tp
+            finally:
+                P.close()
+            phi, betas = (phi1, phi2), (b1, b2)
+        blocks = CheckpointBlocks(torch, LapGraph, g, v, grid, form, ws_total, phi=phi)
+        per_seed = []
+        try:
+            for s in range(seeds):
+                curve, fin = blocks.run(base[form] + s * omega_max, 1, betas)
+                per_seed.append(curve)
+                if form == "plain":
+                    finals.append(fin)
+        finally:
+            blocks.close()
+        stored.append((form, per_seed, phi, betas, prep, time.perf_counter() - t0))
+    if not finals:
+        return {"error": "the plain form is needed for the ground truth"}
+    pool_c = sum(c for c, _ in finals)
+    pool_y = sum(y for _, y in finals)
+    for form, per_seed, phi, betas, prep, wall in stored:
+        errs = np.zeros((seeds, len(grid), 2))
+        for s, curve in enumerate(per_seed):
+            if form == "plain":
+                c, y = pool_c - finals[s][0], pool_y - finals[s][1]
+                ecc_t, kc_t = ecc_truth(torch, g, v, c, (seeds - 1) * omega_max, y, exact)
+            elif s == 0:
+                ecc_t, kc_t = ecc_truth(torch, g, v, pool_c, seeds * omega_max, pool_y, exact)
+            for j, (est, kc) in enumerate(curve):
+                errs[s, j, 0] = float(torch.max(torch.abs(est - ecc_t) / ecc_t))
+                errs[s, j, 1] = abs(kc - kc_t) / abs(kc_t)
+        mean = errs.mean(axis=0)
+        found = next((w for j, w in enumerate(grid) if mean[j, 0] <= target and mean[j, 1] <= target), None)
+        r = {"curve": [{"omega": w, "ecc_max_rel": round(float(mean[j, 0]), 5), "kc_rel": round(float(mean[j, 1]), 7)}
+                       for j, w in enumerate(grid)],
+             "truth_samples": (seeds - 1 if form == "plain" else seeds) * omega_max, "wall_seconds": round(wall, 1)}
+        if form == "cv":
+            r["betas"] = list(betas)
+            r["prepare_seconds"] = round(prep, 2)
+        if found is None:
+            # Beyond the grid: the errors fall like omega^(-1/2); the fit over
+            # the last four grid points gives the omega the target needs.
+            ws = np.array(grid[-4:], dtype=np.float64)
+            e = np.maximum(mean[-4:, 0], mean[-4:, 1])
+            c = float(np.exp(np.mean(np.log(e) + 0.5 * np.log(ws))))
+            r.update({"reached": False, "omega_extrapolated": int(math.ceil((c / target) ** 2)),
+                      "note": "not reached on the grid; omega_extrapolated = (c / target)^2 from err = c / sqrt(omega) "
+                              "fitted to the last four grid points"})
+        else:
+            j = grid.index(found)
+            r.update({"reached": True, "omega": found, "ecc_max_rel_err_mean": float(mean[j, 0]),
+                      "kc_rel_err_mean": float(mean[j, 1])})
+            r.update(timed_run(torch, LapGraph, g, v, found, base[form] + (1 << 28), 1, form, phi=phi, betas=betas))
+        res[form] = r
+    return res
 
 
 def note(msg):
@@ -531,6 +657,68 @@ def cv_train(torch, LapGraph, count):
                                 "targets from the sampler: 512 Wilson samples and 16 v-absorbed walks per node",
                     "data_seconds": round(t1 - t0, 2), "train_seconds": round(t2 - t1, 2),
                     "loss_first_last_epoch": [round(hist[0], 5), round(hist[-1], 5)]}
+
+
+def cv_diagnostics(torch, LapGraph, params, graphs=None, omega=1 << 18, samples=8192):
+    """What the trained network learned, on held-out graphs small enough for
+    near-exact targets: R^2 of head 0 against the mean Wilson visits of
+    `omega` samples (d_u (L_v^{-1})_uu, standard error about 1e-3), R^2 of
+    head 1 against the exact h(u, v) / E[Y2] of the library's FP64 solve; and
+    the per-sample variance of the Kemeny estimator Y1 - Y2 + beta2 M2
+    relative to plain with (a) the network's potential, (b) the exact
+    hitting-time potential (the best any potential can do for the pi-walk
+    term: Y2 - M2 is then the start's hitting time), each also on the
+    loop-included paths."""
+    from paper_2311_10290_gb300 import cv as CVG
+    from paper_2311_10290_gb300 import inputs
+    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, LAP_OPT_PATHS
+    graphs = graphs or [inputs.ba(3000, 4, seed=9001), inputs.rmat(11, 8, seed=9002)]
+    out = []
+    for g in graphs:
+        G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 30)
+        try:
+            v = G.set_root()
+            d = torch.from_numpy(np.diff(g.row_ptr.astype(np.int64)).astype(np.float64)).cuda()
+            G.sample(omega, 1)
+            c1, _, sums = G.counts()
+            ey2 = float(sums[2]) / omega
+            hv, _, _ = G.lv_solve(d)
+            ey2_exact = float((d * hv).sum().item()) / float(g.arcs)
+            y = CVG.predict(G, params).double()
+            keep = torch.ones(g.n, dtype=torch.bool, device="cuda")
+            keep[v] = False
+            t0 = torch.from_numpy(c1.astype(np.float64) / omega).cuda()
+            t1 = hv / ey2_exact
+
+            def r2(pred, t):
+                return float(1.0 - ((pred - t) ** 2).sum() / ((t - t.mean()) ** 2).sum())
+
+            row = {"graph": g.name, "n": g.n, "r2_visits_head": r2(y[keep, 0], t0[keep]),
+                   "r2_hitting_head": r2(y[keep, 1], t1[keep]), "mean_y2_sampled": ey2, "mean_y2_exact": ey2_exact}
+            exact_phi2 = hv.clone()
+            exact_phi2[v] = 0.0
+            for paths in (0, 1):
+                for name, phi2 in (("network", None), ("exact_hitting_time", exact_phi2)):
+                    G.set_option(LAP_OPT_PATHS, paths)
+                    G.set_root(v)
+                    if phi2 is None:
+                        p1, p2 = CVG.pilot_potentials(G, params, seed=3, samples=2048)
+                    else:
+                        p1, p2 = None, phi2
+                    _, b2 = CVG.fit_betas(G, p1, p2, seed=4, pilot=8192)
+                    G.set_root(v)
+                    G.set_option(LAP_OPT_CURSOR, 1 << 24)
+                    G.cv_set_potentials(p1, p2)
+                    a, b, m = G.sample_trace_cv(samples, 5)
+                    est = (a - b).double()
+                    cvv = est + b2 * m
+                    row["kemeny_var_ratio_%s%s" % (name, "_paths" if paths else "")] = float(cvv.var() / est.var())
+                    row["kemeny_var_plain%s" % ("_paths" if paths else "")] = float(est.var())
+            G.set_option(LAP_OPT_PATHS, 0)
+        finally:
+            G.close()
+        out.append(row)
+    return out
 
 
 def cv_prepare(G, params, seed, pilot, batches):
@@ -1143,12 +1331,34 @@ def run_ours(args, rank, world):
     if rank == 0 and args.cv_graphs > 0:
         note("control variate: training data and training")
         params, info = cv_train(torch, LapGraph, args.cv_graphs)
+        note("control variate: what the network learned (held-out graphs)")
+        info["diagnostics"] = cv_diagnostics(torch, LapGraph, params)
         note("control variate: CV vs plain on %s" % g.name)
         info["graphs"] = [cv_measurement(torch, LapGraph, g, v, params, args.cv_batch, 4)]
         if not args.no_tta:
             note("time to accuracy (CV)")
             info["time_to_accuracy_cv"] = time_to_accuracy(torch, LapGraph, params=params)
         res["cv_vs_plain"] = info
+    if rank == 0 and args.tta_large and not args.no_tta:
+        out = []
+        for spec in [x for x in args.tta_large.split(",") if x.strip()]:
+            name, om = spec.split(":")
+            note("time to accuracy on %s (grid to %s samples)" % (name, om))
+            g2 = g if name == args.workload else load_graph(name)
+            v2 = int(np.argmax(np.diff(g2.row_ptr)))          # the library's root: max degree, smallest id
+            exact = exact_parts(torch, LapGraph, g2, v2)
+            forms = [f for f in args.tta_forms.split(",") if f.strip()]
+            r = time_to_accuracy_large(torch, LapGraph, g2, v2, exact, int(om), forms=forms, params=params,
+                                       seeds=args.tta_seeds)
+            r = {"workload": g2.name, "n": g2.n, "arcs": g2.arcs, "root": v2, "exact_solve": exact["info"], **r}
+            if not args.no_cpu and world == 1:
+                om_star = max([r[f].get("omega", r[f].get("omega_extrapolated", 0)) for f in forms if f in r] or [0])
+                if om_star:
+                    r["cpu_oracle"] = cpu_oracle_extrapolated(g2, v2, args.seed, om_star)
+            out.append(r)
+            del exact
+            torch.cuda.empty_cache()
+        res["time_to_accuracy_large"] = out
     if rank == 0 and args.paths > 0:
         note("loop-included paths against own draws")
         res["paths_vs_own_draws"] = paths_measurement(torch, LapGraph, g, v, args)

@@ -117,16 +117,21 @@ bool group_ok(const lap_graph *g)
 
 // Calls of at most this many samples per SM take kernel 3 automatically:
 // below it one lane per sample leaves the GPU short of independent memory
-// chains (measured on one GB300: kernel 3 ahead up to 32,768 samples on
-// Barabasi-Albert 10^6 and R-MAT scale 22, behind at 65,536 on the former).
+// chains.  Measured on one GB300: on Barabasi-Albert 10^6, whose graph stays
+// in L2, kernel 3 is ahead up to 32,768 samples and level at 65,536; on R-MAT
+// scale 22, whose column array misses L2, it is ahead at 65,536 too.
 constexpr uint64_t kGroupAutoPerSm = 320;
+constexpr uint64_t kGroupAutoPerSmLarge = 1024;     // graphs whose arrays exceed kL2Graph
+constexpr uint64_t kL2Graph = 96ull << 20;
 
 // n_samples: the size of the call (0: a call large enough for kernel 2).
 int choose_kernel(const lap_graph *g, uint64_t n_samples = 0)
 {
     if (g->kernel_opt == LAP_KERNEL_WIDE) return LAP_KERNEL_WIDE;
     if (g->kernel_opt == LAP_KERNEL_GROUP && group_ok(g)) return LAP_KERNEL_GROUP;
-    if (g->kernel_opt == 0 && n_samples > 0 && n_samples <= kGroupAutoPerSm * (uint64_t)g->num_sms && group_ok(g))
+    const bool large_graph = 4ull * (uint64_t)g->arcs + 8ull * (uint64_t)g->n > kL2Graph;
+    const uint64_t per_sm = large_graph ? kGroupAutoPerSmLarge : kGroupAutoPerSm;
+    if (g->kernel_opt == 0 && n_samples > 0 && n_samples <= per_sm * (uint64_t)g->num_sms && group_ok(g))
         return LAP_KERNEL_GROUP;
     if (g->n >= (1 << 27) || g->compact_disabled) return LAP_KERNEL_WIDE;
     if (g->ws && g->ws_bytes < slot_bytes_of(g, LAP_KERNEL_COMPACT)) return LAP_KERNEL_WIDE;

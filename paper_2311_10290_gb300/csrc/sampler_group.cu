@@ -145,7 +145,7 @@ __device__ __forceinline__ int32_t arrow_of(const int32_t *col, uint64_t r, uint
 enum : uint32_t { G_SCAN = 0, G_STEP, G_MOVE, G_DONE };
 
 template <int W>
-__global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
+__global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
 {
     static_assert(W == 2 || W == 4 || W == 8, "walkers per sample");
     const uint32_t lane = threadIdx.x & 31u;
@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
         int32_t w = 0;                       // target of the head's arrow (G_MOVE)
         uint32_t ew = 0;                     // expected word of w for the claim (all ones: read it first)
         uint64_t y1 = 0;
+        uint32_t committed = 0;              // nodes this walker added to the tree, not yet in ctl->tree
         uint32_t iter = 0;
         unsigned long long tprog = 0;        // last progress (set when a wait or an idle sweep begins)
         bool waiting = false;
@@ -216,6 +217,13 @@ __global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
         while (phase != G_DONE) {
             if (phase == G_SCAN) {
                 if (cmask == 0u) {
+                    // The tree count is published once per chunk: the sample ends
+                    // when every walker's additions are in (no walker that still
+                    // holds a path or unpublished nodes can see the full count).
+                    if (committed) {
+                        atomicAdd(&ctl->tree, committed);
+                        committed = 0;
+                    }
                     if (ld_u32(&ctl->tree) >= (unsigned)n || ld_u32(&ctl->status)) { phase = G_DONE; break; }
                     const unsigned int c = atomicAdd(&ctl->cursor, 1u);
                     const uint32_t ch = c % nchunks;
@@ -261,12 +269,15 @@ __global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
                     kd = hk - 1u;
                     hpend = false;
                 } else {
-                    if (hk >= kGKMax) { withdraw = true; phase = G_DONE; break; }
+                    if (hk >= kGKMax) { withdraw = true; phase = G_DONE; break; }   // top holds hk
                     kd = hk;
                     ++hk;
                     ++y1;
                     if (kd) atomicAdd(&p.rep1[h], 1ull);
-                    st_word(st + h, mine | hk);
+                    // The head's word is written when the path commits, aborts or
+                    // pops (or the sample is withdrawn): until then only its owner
+                    // reads its draw count, from the path entry.
+                    top = (uint32_t)h | (hk << kNodeBits);
                     if (y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; withdraw = true; phase = G_DONE; break; }
                 }
                 top = (uint32_t)h | (hk << kNodeBits);
@@ -320,8 +331,9 @@ __global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
                         const uint32_t e = stk[x];
                         st_word(st + (e & kGNode), kGTree | (e >> kNodeBits));
                     }
-                    __threadfence();
-                    atomicAdd(&ctl->tree, sp);
+                    // No fence: another walker that still reads such a node as
+                    // owned waits or aborts, both exact.
+                    committed += sp;
                     sp = 0;
                     waiting = false;
                     phase = G_SCAN;
@@ -373,6 +385,15 @@ __global__ void __launch_bounds__(256, 4) lewalk_group_kernel(LapSampleLaunch p)
         }
 
         if (withdraw) atomicOr(&ctl->status, kWithdraw);
+        // A walker stopped with a path (the sample is being withdrawn) writes
+        // its nodes' draw counts, so that the subtraction below sees them.
+        if (sp > 0) {
+            st_word(st + (top & kGNode), top >> kNodeBits);
+            for (uint32_t x = 0; x + 1u < sp; ++x) {
+                const uint32_t e = stk[x];
+                st_word(st + (e & kGNode), e >> kNodeBits);
+            }
+        }
         atomicAdd(&ctl->y1, (unsigned long long)y1);
         __threadfence();
         __syncwarp(gmask);
