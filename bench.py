@@ -44,29 +44,37 @@ BYTES_WILSON_STEP = 5 * SECTOR
 BYTES_TREE_INSERT = 2 * SECTOR
 BYTES_WALK_STEP = 3 * SECTOR
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one sampler
-# launch of the default workload (65,536 samples, BA n=1e6, m=5, default
-# workspace), from a single-pass ncu capture of that exact launch; valid only
-# for the sampler sources it was measured on (SHA-1 over the files below).
-TRAFFIC_PER_LAUNCH = {"ba_1m/65536": 11.908e12 + 1.314e12}
-TRAFFIC_SOURCES = ("sampler_compact.cu", "compact_state.cuh", "philox.cuh")
-TRAFFIC_SOURCES_SHA1 = "4af5c31933f7cbb7c6ab1236ebb591c2c49755f1"
+# DRAM traffic per Wilson step (dram__bytes_read.sum + dram__bytes_write.sum of
+# one sampler launch over the launch's Wilson steps, absorbed-walk steps and
+# tree insertions included), from ncu captures of small cases of the same
+# kernel and graph family (a 4 GB workspace, one launch; profiles/): the
+# bench scales it by the Wilson steps of its own launch.  Valid only for the
+# sources it was measured on (SHA-1 over the files listed).
+TRAFFIC_PER_WILSON_STEP = {
+    # 1-byte kernel, BA 10^6, 4096 samples in 3,535 lanes: 671.4 GB / 4.582e9 steps
+    "lewalk_compact_kernel": (146.53, ("sampler_compact.cu", "compact_state.cuh", "philox.cuh"),
+                              "98cf00da0b50c4c76b0ab9ce347f4a03af608187"),
+    # several walkers, R-MAT scale 22, 2048 samples in 682 groups of 8: 621.1 GB / 4.986e9 steps
+    "lewalk_group_kernel": (124.57, ("sampler_group.cu", "philox.cuh"), "0e7efd45423163089e7040dfe8865af6fec3bea9"),
+}
 
 
-def sampler_sources_sha1():
+def sources_sha1(files):
     import hashlib
     h = hashlib.sha1()
-    for f in TRAFFIC_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2311_10290_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def measured_traffic(workload, batch):
-    t = TRAFFIC_PER_LAUNCH.get("%s/%d" % (workload, batch))
-    if t is None or sampler_sources_sha1() != TRAFFIC_SOURCES_SHA1:
+def measured_traffic(kernel_name, wilson_steps):
+    """Bytes per launch scaled from the small-case capture, or None when the
+    kernel's sources changed since (or no capture exists for it)."""
+    t = TRAFFIC_PER_WILSON_STEP.get(kernel_name.split()[0])
+    if t is None or sources_sha1(t[1]) != t[2]:
         return None
-    return t
+    return t[0] * float(wilson_steps)
 
 
 HEADLINE_METRIC = ("time to rel.err 1e-2 for all-node ECC+Kemeny; walk steps/s; CV vs plain, 1 GB300")
@@ -87,27 +95,28 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ws-frac", type=float, default=0.6, help="fraction of free HBM lent as Wilson state")
     ap.add_argument("--ws-gb", type=float, default=0.0, help="cap on the Wilson-state workspace in GB (profiler runs)")
-    ap.add_argument("--tta-large", default="ba_1m:16384,rmat_22:65536",
-                    help="time to accuracy on large graphs: workload:largest omega of the grid, comma separated")
+    ap.add_argument("--tta-large", default="ba_1m:16384:plain+paths+cv,rmat_22:65536:plain",
+                    help="time to accuracy on large graphs: workload:largest omega of the grid[:forms joined by +], "
+                         "comma separated (forms default to --tta-forms)")
     ap.add_argument("--tta-forms", default="plain,paths,cv", help="estimator forms of the large-graph runs")
     ap.add_argument("--tta-seeds", type=int, default=10, help="seeds (disjoint id ranges) per form")
     ap.add_argument("--kernel", type=int, default=0, help="LAP_OPT_KERNEL for the timed steps (0: the library's choice)")
     ap.add_argument("--walkers", type=int, default=8, help="LAP_OPT_WALKERS (kernel 3)")
     ap.add_argument("--cv-graphs", type=int, default=200, help="training graphs for the learned control variate (0: skip)")
-    ap.add_argument("--cv-batch", type=int, default=16384, help="samples per batch in the CV-vs-plain measurement")
+    ap.add_argument("--cv-batch", type=int, default=8192, help="samples per batch in the CV-vs-plain measurement")
     ap.add_argument("--batched-graphs", type=int, default=512, help="graphs of the uneven batch (0: skip)")
     ap.add_argument("--batched-samples", type=int, default=4096, help="samples per graph of the uneven batch")
     ap.add_argument("--batched-nmax", type=int, default=1_000_000, help="largest n of the uneven batch recipe")
     ap.add_argument("--batched-ws-gb", type=float, default=0.0, help="cap on the batch workspace in GB (profiler runs)")
     ap.add_argument("--batched-orders", default="0",
                     help="unit orders to time on the uneven batch: 0 largest first, 1 smallest first")
-    ap.add_argument("--landmark-roots", type=int, default=12,
+    ap.add_argument("--landmark-roots", type=int, default=6,
                     help="roots of the landmark study on the BA 1e6 graph (0: skip)")
     ap.add_argument("--kemeny-sweep", type=int, default=1, help="kappa/n of 1e6-node BA and ER graphs (0: skip)")
     ap.add_argument("--study-samples", type=int, default=256, help="samples per root / graph of the two studies")
     ap.add_argument("--paths", type=int, default=1,
                     help="measure the loop-included-path form (LAP_OPT_PATHS) against own draws (0: skip)")
-    ap.add_argument("--spantree-trees", type=int, default=16384,
+    ap.add_argument("--spantree-trees", type=int, default=4096,
                     help="SpanTree (Alg. 1/3) trees timed on the main workload (0: skip the SpanTree section)")
     ap.add_argument("--extra-workloads", default="rmat_22",
                     help="comma-separated extra single-graph workloads (plain throughput, CV vs plain)")
@@ -747,9 +756,11 @@ def cv_measurement(torch, LapGraph, g, v, params, samples_per_batch, batches):
     estimator between `batches` independent batches.  The coefficients come
     from separate pilot samples, so both estimators stay unbiased."""
     from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, lap_counts
+    from paper_2311_10290_gb300.lap import LAP_OPT_KERNEL
     free, _ = torch.cuda.mem_get_info()
     G = LapGraph(g.row_ptr, g.col, workspace_bytes=int(free * 0.5))
     try:
+        G.set_option(LAP_OPT_KERNEL, 2)           # plain and CV timed on the same kernel
         G.set_root(v)
         t0 = time.perf_counter()
         phi1, phi2, beta1, beta2 = cv_prepare(G, params, 4242, pilot=2 * samples_per_batch, batches=4)
@@ -811,13 +822,14 @@ def cv_measurement(torch, LapGraph, g, v, params, samples_per_batch, batches):
 
 # ------------------------------------------------------------ loop-included paths
 
-def paths_measurement(torch, LapGraph, g, v, args, samples=16384, batches=4):
+def paths_measurement(torch, LapGraph, g, v, args, samples=8192, batches=4):
     """LAP_OPT_PATHS = 1 against own draws on one graph: per-sample variance
     of Y1 - Y2 (Kemeny), per-node variance of the L^+_uu numerator
     (cnt1 - 2 cnt2) / d between batches (ECC), and sampler time."""
-    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, LAP_OPT_PATHS, lap_counts
+    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, LAP_OPT_KERNEL, LAP_OPT_PATHS, lap_counts
     free, _ = torch.cuda.mem_get_info()
-    out = {"workload": g.name, "samples": samples, "batches": batches}
+    out = {"workload": g.name, "samples": samples, "batches": batches,
+           "kernel": "the 1-byte kernel in both modes (the several-walkers kernel has no path mode)"}
     d = np.diff(g.row_ptr.astype(np.int64)).astype(np.float64)
     keep = np.ones(g.n, bool)
     keep[v] = False
@@ -825,6 +837,7 @@ def paths_measurement(torch, LapGraph, g, v, args, samples=16384, batches=4):
     for mode in (0, 1):
         G = LapGraph(g.row_ptr, g.col, workspace_bytes=int(free * 0.5))
         try:
+            G.set_option(LAP_OPT_KERNEL, 2)
             G.set_option(LAP_OPT_PATHS, mode)
             G.set_root(v)
             torch.cuda.synchronize()
@@ -1048,7 +1061,7 @@ def extra_workload(torch, LapGraph, name, args, params):
     """Plain throughput (1 warm-up and 1 timed launch of `extra_samples`
     samples) on another single-graph workload, then the control variate
     against plain on it when a trained network is given."""
-    from paper_2311_10290_gb300.lap import LAP_STAT_FALLBACKS, LAP_STAT_KERNEL, lap_counts
+    from paper_2311_10290_gb300.lap import LAP_STAT_FALLBACKS, LAP_STAT_LAST_KERNEL, lap_counts
     t0 = time.perf_counter()
     g = load_graph(name)
     t_gen = time.perf_counter() - t0
@@ -1083,8 +1096,10 @@ def extra_workload(torch, LapGraph, name, args, params):
                "walk_steps": {"wilson": wilson, "uniform_walk": uwalk, "pi_walk": piwalk,
                               "wilson_steps_per_node_per_sample": wilson / B / g.n},
                "roofline": {"bound": "hbm", "achieved": alg / t_kernel / 1e9, "peak": peak, "unit": "GB/s",
-                            "frac": alg / t_kernel / 1e9 / peak},
-               "kernel": G.stat(LAP_STAT_KERNEL), "fallbacks": G.stat(LAP_STAT_FALLBACKS),
+                            "frac": alg / t_kernel / 1e9 / peak,
+                            "traffic": measured_traffic(KERNEL_NAMES[G.stat(LAP_STAT_LAST_KERNEL)], wilson),
+                            "traffic_note": "per launch, scaled from a small-case ncu capture by Wilson steps"},
+               "kernel": KERNEL_NAMES[G.stat(LAP_STAT_LAST_KERNEL)], "fallbacks": G.stat(LAP_STAT_FALLBACKS),
                "kemeny_estimate": kc, "slots": G.slots, "generate_seconds": round(t_gen, 1)}
     finally:
         G.close()
@@ -1224,6 +1239,8 @@ def run_ours(args, rank, world):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    from paper_2311_10290_gb300.lap import LAP_STAT_LAST_KERNEL
+    kernel_name = KERNEL_NAMES[G.stat(LAP_STAT_LAST_KERNEL)]
     c1a, c2a, sa = lap_counts(G.h, g.n)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -1277,7 +1294,7 @@ def run_ours(args, rank, world):
                  BYTES_WALK_STEP * (uwalk + piwalk)) / args.steps
     peak, peak_kind = peaks()
     achieved = alg_bytes / kernel_s / 1e9
-    traffic = measured_traffic(args.workload, B)
+    traffic = measured_traffic(kernel_name, wilson / args.steps)
     res = {
         "metric": HEADLINE_METRIC, "value": value, "unit": "walk steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -1296,6 +1313,7 @@ def run_ours(args, rank, world):
                        "wilson_steps_per_node_per_sample": wilson / max(1, samples) / g.n},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": float(traffic) if traffic else None,
+                     "traffic_note": "per launch, scaled from a small-case ncu capture by Wilson steps (profiles/)",
                      "kernel": kernel_name.split()[0], "kernel_ms": kernel_s * 1e3,
                      "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind},
         "gpu_launches": args.steps * 7,
@@ -1342,12 +1360,13 @@ def run_ours(args, rank, world):
     if rank == 0 and args.tta_large and not args.no_tta:
         out = []
         for spec in [x for x in args.tta_large.split(",") if x.strip()]:
-            name, om = spec.split(":")
+            parts = spec.split(":")
+            name, om = parts[0], parts[1]
+            forms = parts[2].split("+") if len(parts) > 2 else [f for f in args.tta_forms.split(",") if f.strip()]
             note("time to accuracy on %s (grid to %s samples)" % (name, om))
             g2 = g if name == args.workload else load_graph(name)
             v2 = int(np.argmax(np.diff(g2.row_ptr)))          # the library's root: max degree, smallest id
             exact = exact_parts(torch, LapGraph, g2, v2)
-            forms = [f for f in args.tta_forms.split(",") if f.strip()]
             r = time_to_accuracy_large(torch, LapGraph, g2, v2, exact, int(om), forms=forms, params=params,
                                        seeds=args.tta_seeds)
             r = {"workload": g2.name, "n": g2.n, "arcs": g2.arcs, "root": v2, "exact_solve": exact["info"], **r}
