@@ -403,7 +403,7 @@ class CheckpointBlocks:
         self.handles = []
         # Lanes are shared out in proportion to the block sizes, so that the
         # blocks' kernels fit on the GPU together and run side by side.
-        from paper_2311_10290_gb300.lap import LAP_OPT_SLOTS
+        from paper_2311_10290_gb300.lap import LAP_OPT_SLOTS, LAP_OPT_WALKERS
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         lanes = sms * 1024
         walkers = 8 if form == "plain" else 1          # kernel 3 counts groups of 8 lanes as one slot
@@ -411,6 +411,7 @@ class CheckpointBlocks:
             ws = max(8 * g.n * 4, int(ws_total * sz / grid[-1]))
             H = LapGraph(g.row_ptr, g.col, workspace_bytes=ws, stream=self.streams[k])
             H.set_option(LAP_OPT_PATHS, 1 if form == "paths" else 0)
+            H.set_option(LAP_OPT_WALKERS, 8)
             H.set_option(LAP_OPT_SLOTS, max(1, int(lanes / walkers * sz / grid[-1])))
             self.handles.append(H)
         self.F = LapGraph(g.row_ptr, g.col, workspace_bytes=8 * g.n)
@@ -708,8 +709,8 @@ def cv_diagnostics(torch, LapGraph, params, graphs=None, omega=1 << 18, samples=
             exact_phi2[v] = 0.0
             for paths in (0, 1):
                 for name, phi2 in (("network", None), ("exact_hitting_time", exact_phi2)):
-                    G.set_option(LAP_OPT_PATHS, paths)
                     G.set_root(v)
+                    G.set_option(LAP_OPT_PATHS, paths)
                     if phi2 is None:
                         p1, p2 = CVG.pilot_potentials(G, params, seed=3, samples=2048)
                     else:
@@ -723,7 +724,6 @@ def cv_diagnostics(torch, LapGraph, params, graphs=None, omega=1 << 18, samples=
                     cvv = est + b2 * m
                     row["kemeny_var_ratio_%s%s" % (name, "_paths" if paths else "")] = float(cvv.var() / est.var())
                     row["kemeny_var_plain%s" % ("_paths" if paths else "")] = float(est.var())
-            G.set_option(LAP_OPT_PATHS, 0)
         finally:
             G.close()
         out.append(row)

@@ -105,7 +105,11 @@ typedef enum {
                                   expectations (so the same estimands), correlated with the Wilson
                                   counts, which lowers the variance of y1 - 2 y2 and of Y1 - Y2.
                                   Only before the first sample after lap_set_root. */
-    LAP_OPT_WALKERS = 9,       /* lanes per sample of kernel 3: 2, 4 or 8 (default 8).  They run the
+    LAP_OPT_WALKERS = 9,       /* lanes per sample of kernel 3: 2, 4, 8 or 16; 0 (default) = 16 when
+                                  the call's samples times 16 lanes fit on the GPU at once (1280
+                                  lanes per SM), else 8.  The path stacks of a sample hold 8 x
+                                  LAP_OPT_STACK entries in all, shared out among its walkers;
+                                  with 16 walkers a node drawn 511 times withdraws the sample.  They run the
                                   sample's Wilson run together (Section 3.4, stack representation:
                                   the popped cycles, so every node's draws and the tree, do not
                                   depend on the order in which walkers find them), then one runs

@@ -100,8 +100,9 @@ uint64_t slot_bytes_of(const lap_graph *g, int kernel)
 {
     if (kernel == LAP_KERNEL_WIDE) return 8ull * (uint64_t)g->n;
     if (kernel == LAP_KERNEL_GROUP)
-        // Control block, 16-bit words, one path stack per walker.
-        return (64ull + 2ull * n_pad_of(g) + 4ull * stack_cap_of(g) * (uint64_t)g->walkers + 255ull) & ~255ull;
+        // Control block, 16-bit words, path stacks: 8 stacks' worth of entries
+        // shared out among the sample's walkers.
+        return (64ull + 2ull * n_pad_of(g) + 4ull * stack_cap_of(g) * 8ull + 255ull) & ~255ull;
     // State bytes, path-count bytes (loop-included paths only), stack, count table.
     return ((g->paths_opt ? 2ull : 1ull) * n_pad_of(g) + 4ull * stack_cap_of(g) + (8ull << lap_table_log2(g->n)) +
             255ull) & ~255ull;
@@ -123,6 +124,15 @@ bool group_ok(const lap_graph *g)
 constexpr uint64_t kGroupAutoPerSm = 320;
 constexpr uint64_t kGroupAutoPerSmLarge = 1024;     // graphs whose arrays exceed kL2Graph
 constexpr uint64_t kL2Graph = 96ull << 20;
+
+// Walkers per sample of kernel 3 for a call of n_samples: the option, or
+// 16 when the call's 16 lanes per sample fit on the GPU at once (1280 lanes
+// per SM: 5 blocks of 256), which halves a sample's time; else 8.
+int walkers_for(const lap_graph *g, uint64_t n_samples)
+{
+    if (g->walkers) return g->walkers;
+    return n_samples > 0 && n_samples * 16ull <= 1280ull * (uint64_t)g->num_sms ? 16 : 8;
+}
 
 // n_samples: the size of the call (0: a call large enough for kernel 2).
 int choose_kernel(const lap_graph *g, uint64_t n_samples = 0)
@@ -201,11 +211,11 @@ lap_status launch(lap_graph *g, LapSampleLaunch &p, int kernel)
     p.stack_cap = kernel == LAP_KERNEL_COMPACT
                       ? (uint32_t)((p.slot_bytes - (p.paths ? 2ull : 1ull) * p.n_pad - (8ull << p.tbl_log2)) / 4ull)
                   : kernel == LAP_KERNEL_GROUP
-                      ? (uint32_t)(((p.slot_bytes - 64ull - 2ull * p.n_pad) / 4ull / (uint64_t)g->walkers) & ~3ull)
+                      ? (uint32_t)(((p.slot_bytes - 64ull - 2ull * p.n_pad) / 4ull / (uint64_t)walkers_for(g, p.count)) & ~3ull)
                       : 0u;
     LAP_CUDA(g, cudaMemsetAsync(&g->d_acc->claim, 0, sizeof(unsigned int), g->stream));
     const cudaError_t e = kernel == LAP_KERNEL_WIDE    ? lap_launch_sample(p, g->stream)
-                          : kernel == LAP_KERNEL_GROUP ? lap_launch_sample_group(p, g->walkers, g->stream)
+                          : kernel == LAP_KERNEL_GROUP ? lap_launch_sample_group(p, walkers_for(g, p.count), g->stream)
                                                        : lap_launch_sample_compact(p, g->stream);
     if (e != cudaSuccess) {
         char buf[256];
@@ -389,8 +399,8 @@ lap_status lap_set_option(lap_graph *g, int32_t option, int64_t value)
         g->cursor = (uint64_t)value;
         return LAP_OK;
     case LAP_OPT_WALKERS:
-        if (value != 2 && value != 4 && value != 8) return fail(g, LAP_ERR_INVALID_ARG, "walkers must be 2, 4 or 8");
-        if (g->walkers != (int)value) g->last_kernel = 0;     // the slot layout changes
+        if (value != 0 && value != 2 && value != 4 && value != 8 && value != 16)
+            return fail(g, LAP_ERR_INVALID_ARG, "walkers must be 0 (automatic), 2, 4, 8 or 16");
         g->walkers = (int)value;
         return LAP_OK;
     case LAP_OPT_KERNEL:

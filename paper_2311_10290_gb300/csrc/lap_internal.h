@@ -97,7 +97,8 @@ enum : uint32_t {
 cudaError_t lap_launch_sample(const LapSampleLaunch &p, cudaStream_t st);
 // sampler_compact.cu
 cudaError_t lap_launch_sample_compact(const LapSampleLaunch &p, cudaStream_t st);
-// sampler_group.cu: `walkers` lanes per sample (2, 4 or 8); p.slots counts groups
+// sampler_group.cu: `walkers` lanes per sample (2, 4, 8 or 16); p.slots counts groups;
+// p.stack_cap is the stack capacity of each walker
 cudaError_t lap_launch_sample_group(const LapSampleLaunch &p, int walkers, cudaStream_t st);
 
 // ------------------------------------------------------------ batches
@@ -291,7 +292,7 @@ struct lap_graph {
     uint64_t slots_opt = 0;
     int block_opt = 0;
     int kernel_opt = 0;                     // 0 auto, LAP_KERNEL_WIDE, LAP_KERNEL_COMPACT, LAP_KERNEL_GROUP
-    int walkers = 8;                        // LAP_OPT_WALKERS (kernel 3)
+    int walkers = 0;                        // LAP_OPT_WALKERS (kernel 3; 0 = automatic)
     uint32_t paths_opt = 0;                 // LAP_OPT_PATHS
     int32_t path_start = -1;                // LAP_OPT_PATH_START (-1: uniform start)
     uint32_t stack_cap = 0;                 // 0: default, about 16 sqrt(n)

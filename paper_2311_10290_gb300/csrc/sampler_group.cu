@@ -23,15 +23,15 @@
 // cycle; the highest-numbered active walker always progresses.
 //
 // State per node and sample in flight, 16 bits, cleared at each sample start:
-//   bit 15 InTree | bit 14 pending | bits 10..13 owner (walker + 1, 0 = free) |
-//   bits 0..9 draws k
+//   bit 15 InTree | bit 14 pending | owner (walker + 1, 0 = free; 4 bits for up
+//   to 8 walkers, 5 for 16) | draws k (the remaining 10 or 9 bits)
 // A path node's arrow is never stored: it is draw k - 1.  A walker keeps its
 // path on a private stack (entries node | k << 22), the head in a register.
 // Start nodes come from a per-sample chunk cursor (32 nodes per chunk); past
 // the last chunk the cursor wraps around (sweeps pick up nodes released by
 // aborts and popped cycles behind it) until every node is in the tree.
 //
-// A sample that does not fit (a node drawn 1023 times, a path longer than the
+// A sample that does not fit (a node drawn 1023 (511) times, a path longer than the
 // walker's stack, or a walker without progress for kStallNs) is withdrawn
 // exactly as in the 1-byte kernel: the group subtracts k - 1 for every node
 // and lists the id for a re-run with the 8-byte kernel.
@@ -40,8 +40,18 @@
 
 namespace {
 
-constexpr uint32_t kGTree = 0x8000u, kGPend = 0x4000u, kGOwnShift = 10u, kGOwn = 0xFu << 10, kGK = 0x3FFu;
-constexpr uint32_t kGKMax = 0x3FFu;
+constexpr uint32_t kGTree = 0x8000u, kGPend = 0x4000u;
+
+// Owner and draw-count fields of the 16-bit word: 4 owner bits and 10 count
+// bits for up to 8 walkers, 5 and 9 for 16.
+template <int W>
+struct GWord {
+    static constexpr uint32_t own_bits = W <= 8 ? 4u : 5u;
+    static constexpr uint32_t shift = 14u - own_bits;
+    static constexpr uint32_t own = ((1u << own_bits) - 1u) << shift;
+    static constexpr uint32_t k = (1u << shift) - 1u;
+    static constexpr uint32_t kmax = k;                 // a node drawn this often withdraws the sample
+};
 constexpr int kNodeBits = 22;
 constexpr uint32_t kGNode = (1u << kNodeBits) - 1u;
 constexpr uint32_t kChunk = 32;                                   // nodes per scan chunk (64 bytes)
@@ -95,22 +105,26 @@ __device__ __forceinline__ uint32_t cas_word(uint16_t *a, uint32_t expect, uint3
 {
     return atomicCAS(reinterpret_cast<unsigned short int *>(a), (unsigned short int)expect, (unsigned short int)val);
 }
-__device__ __forceinline__ bool w_free(uint32_t w) { return (w & (kGTree | kGOwn)) == 0u; }
-__device__ __forceinline__ uint32_t w_owner(uint32_t w) { return (w & kGOwn) >> kGOwnShift; }
+template <int W>
+__device__ __forceinline__ bool w_free(uint32_t w) { return (w & (kGTree | GWord<W>::own)) == 0u; }
+template <int W>
+__device__ __forceinline__ uint32_t w_owner(uint32_t w) { return (w & GWord<W>::own) >> GWord<W>::shift; }
 
 // Bit b set when word b of the 32 words (two per 32-bit lane of the four
 // vectors) is neither in the tree nor owned.
+template <int W>
 __device__ __forceinline__ uint32_t free_mask2(uint32_t x)
 {
-    const uint32_t e = __vcmpeq2(x & ((kGTree | kGOwn) * 0x00010001u), 0u);   // 0xFFFF per free half
+    const uint32_t e = __vcmpeq2(x & ((kGTree | GWord<W>::own) * 0x00010001u), 0u);   // 0xFFFF per free half
     return (e & 1u) | ((e >> 15) & 2u);
 }
+template <int W>
 __device__ __forceinline__ uint32_t free_mask(uint4 a, uint4 b, uint4 c, uint4 d)
 {
     const uint32_t q[16] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w, d.x, d.y, d.z, d.w};
     uint32_t m = 0;
 #pragma unroll
-    for (int t = 0; t < 16; ++t) m |= free_mask2(q[t]) << (2 * t);
+    for (int t = 0; t < 16; ++t) m |= free_mask2<W>(q[t]) << (2 * t);
     return m;
 }
 
@@ -147,12 +161,13 @@ enum : uint32_t { G_SCAN = 0, G_STEP, G_MOVE, G_DONE };
 template <int W>
 __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
 {
-    static_assert(W == 2 || W == 4 || W == 8, "walkers per sample");
+    static_assert(W == 2 || W == 4 || W == 8 || W == 16, "walkers per sample");
+    using L = GWord<W>;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t gbase = lane & ~(uint32_t)(W - 1);
     const unsigned gmask = ((1u << W) - 1u) << gbase;
     const uint32_t j = lane - gbase;                    // walker index in the group
-    const uint32_t mine = (j + 1u) << kGOwnShift;       // owner field of this walker
+    const uint32_t mine = (j + 1u) << L::shift;         // owner field of this walker
     const uint64_t slot = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) / W;
     if (slot >= p.slots) return;                        // uniform over the group
     const int32_t n = p.g.n;
@@ -230,7 +245,7 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
                     cbase = ch * kChunk;
                     const uint16_t *cp = st + cbase;
                     const uint4 a = ld_chunk4(cp), b = ld_chunk4(cp + 8), cc = ld_chunk4(cp + 16), d = ld_chunk4(cp + 24);
-                    cmask = free_mask(a, b, cc, d);
+                    cmask = free_mask<W>(a, b, cc, d);
                     // The last chunk holds 1..31 nodes: cbase < n <= cbase + 32.
                     if (cbase + kChunk > (uint32_t)n) cmask &= (1u << ((uint32_t)n - cbase)) - 1u;
                     if (c >= nchunks && cmask == 0u) {
@@ -247,14 +262,14 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
                 uint32_t expect = 0u;
                 uint32_t old = cas_word(st + s, expect, mine);
                 const uint64_t row = ld_row(rowinfo, s, keep);
-                for (int t = 0; t < 8 && old != expect && w_free(old); ++t) {
+                for (int t = 0; t < 8 && old != expect && w_free<W>(old); ++t) {
                     expect = old;
                     old = cas_word(st + s, expect, expect | mine);
                 }
                 if (old != expect) continue;           // in the tree, or taken by another walker
                 waiting = false;
                 h = s;
-                hk = old & kGK;
+                hk = old & L::k;
                 hpend = (old & kGPend) != 0u;
                 hrow = row;
                 sp = 1;
@@ -269,7 +284,7 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
                     kd = hk - 1u;
                     hpend = false;
                 } else {
-                    if (hk >= kGKMax) { withdraw = true; phase = G_DONE; break; }   // top holds hk
+                    if (hk >= L::kmax) { withdraw = true; phase = G_DONE; break; }   // top holds hk
                     kd = hk;
                     ++hk;
                     ++y1;
@@ -296,7 +311,7 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
                 bool claimed = false;
                 if (ew == 0xFFFFFFFFu) {
                     old = ld_word(st + w);
-                    if (w_free(old)) {
+                    if (w_free<W>(old)) {
                         ew = old;
                         old = cas_word(st + w, ew, ew | mine);
                         claimed = old == ew;
@@ -305,7 +320,7 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
                     old = cas_word(st + w, ew, ew | mine);
                     claimed = old == ew;
                 }
-                for (int t = 0; t < 8 && !claimed && w_free(old); ++t) {
+                for (int t = 0; t < 8 && !claimed && w_free<W>(old); ++t) {
                     ew = old;
                     old = cas_word(st + w, ew, ew | mine);
                     claimed = old == ew;
@@ -316,7 +331,7 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
                     stk[sp - 1] = top;
                     ++sp;
                     h = w;
-                    hk = old & kGK;
+                    hk = old & L::k;
                     hpend = (old & kGPend) != 0u;
                     hrow = row;
                     top = (uint32_t)w | (hk << kNodeBits);
@@ -339,7 +354,7 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
                     phase = G_SCAN;
                     continue;
                 }
-                const uint32_t o = w_owner(old);
+                const uint32_t o = w_owner<W>(old);
                 if (o == j + 1u) {
                     // A cycle of stack tops closed at w: pop it; w draws again.
                     st_word(st + h, hk);
@@ -400,7 +415,7 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
         if (ld_u32(&ctl->status) & kWithdraw) {
             // Withdraw the sample: subtract the repeat visits counted so far.
             for (int32_t x = (int32_t)j; x < n; x += W) {
-                const uint32_t k = ld_word(st + x) & kGK;
+                const uint32_t k = ld_word(st + x) & L::k;
                 if (k >= 2u) atomicAdd(&p.rep1[x], (unsigned long long)(-(long long)(k - 1u)));
             }
             if (j == 0) {
@@ -457,6 +472,7 @@ cudaError_t lap_launch_sample_group(const LapSampleLaunch &p, int walkers, cudaS
     if (walkers == 2) lewalk_group_kernel<2><<<(unsigned)grid, block, 0, st>>>(p);
     else if (walkers == 4) lewalk_group_kernel<4><<<(unsigned)grid, block, 0, st>>>(p);
     else if (walkers == 8) lewalk_group_kernel<8><<<(unsigned)grid, block, 0, st>>>(p);
+    else if (walkers == 16) lewalk_group_kernel<16><<<(unsigned)grid, block, 0, st>>>(p);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

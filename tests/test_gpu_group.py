@@ -5,7 +5,8 @@ which the walkers find them).
 
 Integer outputs (visits per node, uniform-walk passes, sum Y1, sum Y2,
 per-sample Y1 and Y2) must be bit-exact with the sequential CPU oracle for
-every walker count, launch shape and graph, including samples the kernel
+every walker count (2, 4, 8, 16 and the automatic choice), launch shape and
+graph, including samples the kernel
 withdraws (a path longer than a walker's stack) and re-runs with the 8-byte
 kernel; FP64 estimates within 1e-12 of the oracle's finalize."""
 import numpy as np
@@ -22,7 +23,7 @@ from paper_2311_10290_gb300.lap import (LAP_OPT_KERNEL, LAP_OPT_PATH_START, LAP_
                                         LapGraph)
 
 
-def run3(g, seed, omega, walkers=8, root=-1, slots=None, stack=None, trace=False, start=None, ws=1 << 27,
+def run3(g, seed, omega, walkers=0, root=-1, slots=None, stack=None, trace=False, start=None, ws=1 << 27,
          splits=None):
     G = LapGraph(g.row_ptr, g.col, workspace_bytes=ws)
     try:
@@ -71,7 +72,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("walkers", [2, 4, 8])
+@pytest.mark.parametrize("walkers", [2, 4, 8, 16, 0])
 @pytest.mark.parametrize("name,maker,root,omega", CASES, ids=[c[0] for c in CASES])
 def test_group_kernel_counts_match_oracle(name, maker, root, omega, walkers):
     g = maker()
@@ -121,11 +122,12 @@ def test_group_kernel_fixed_start_rows():
     assert_counts(r, c, 800)
 
 
-def test_group_kernel_full_size_rmat22_small_omega():
+@pytest.mark.parametrize("walkers", [8, 16])
+def test_group_kernel_full_size_rmat22_small_omega(walkers):
     """The R-MAT scale-22 graph (2.4M nodes, a 162,713-degree hub as the
-    root): all counts bit-exact for 32 samples, 8 walkers each."""
+    root): all counts bit-exact for 32 samples, 8 or 16 walkers each."""
     g = I.rmat_22()
-    r = run3(g, 5, 32, walkers=8, ws=64 << 20 << 4)
+    r = run3(g, 5, 32, walkers=walkers, ws=64 << 20 << 4)
     c = oracle.sample_threads(g.row_ptr, g.col, r["v"], 5, 0, 32, 16)
     assert_counts(r, c, 32)
     assert r["fallbacks"] == 0
