@@ -958,9 +958,10 @@ def landmark_study(torch, g, args):
     batched launch sharing one copy of the CSR."""
     from paper_2311_10290_gb300.lap import LapBatch
     deg = np.diff(g.row_ptr.astype(np.int64))
-    top = [int(x) for x in np.argsort(-deg, kind="stable")[:8]]
+    n_rand = args.landmark_roots // 3
+    top = [int(x) for x in np.argsort(-deg, kind="stable")[:max(1, args.landmark_roots - n_rand)]]
     rng = np.random.Generator(np.random.PCG64(7))
-    rand = [int(x) for x in rng.choice(g.n, size=max(0, args.landmark_roots - len(top)), replace=False)]
+    rand = [int(x) for x in rng.choice(g.n, size=n_rand, replace=False)]
     roots = top + rand
     t0 = time.perf_counter()
     B = LapBatch([(g.row_ptr, g.col)] * len(roots), roots=roots)
