@@ -669,6 +669,72 @@ def cv_train(torch, LapGraph, count):
                     "loss_first_last_epoch": [round(hist[0], 5), round(hist[-1], 5)]}
 
 
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+# Useful (unpadded) products per row of the 8 -> 64 -> 64 -> 2 network:
+# forward 2 (8*64 + 64*64 + 64*2); the backward adds dY W3, dH2 W2 and the
+# three weight gradients.
+MLP_FLOP_FWD = 2 * (8 * 64 + 64 * 64 + 64 * 2)
+MLP_FLOP_TRAIN = MLP_FLOP_FWD + 2 * (2 * 64 + 64 * 64 + 64 * 64 + 64 * 8 + 2 * 64)
+
+
+def mlp_kernel_timing(torch, rows_list=(8192, 1 << 22), reps=20):
+    """CUDA-event time of the MLP kernels on random rows: the tcgen05 kernel
+    (TMEM accumulators) beside the mma.sync kernel, forward and loss+gradient,
+    with the useful tensor FLOP/s and the HBM bytes (X and Y or T) per second
+    against the measured peaks."""
+    from paper_2311_10290_gb300 import lap as L
+    hbm, hbm_kind = peaks()
+    tc, tc_kind = bf16_peak()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    P = torch.randn(L.LAP_MLP_PARAMS, device="cuda", generator=gen) * 0.1
+    st = torch.cuda.current_stream()
+    rows_out = []
+    try:
+        for rows in rows_list:
+            X = torch.randn(rows, 8, device="cuda", generator=gen)
+            T = torch.randn(rows, 2, device="cuda", generator=gen)
+            Y = torch.empty(rows, 2, device="cuda")
+            G = torch.zeros(L.LAP_MLP_PARAMS, device="cuda")
+            loss = torch.zeros(1, device="cuda")
+            for kname, k in (("tcgen05", L.LAP_MLP_TCGEN05), ("mma_sync", L.LAP_MLP_MMA_SYNC)):
+                L.lap_mlp_select(k)
+                calls = (("forward", MLP_FLOP_FWD, lambda: L.lap_mlp_forward(P, X, rows, Y, st.cuda_stream)),
+                         ("loss_grad", MLP_FLOP_TRAIN,
+                          lambda: L.lap_mlp_loss_grad(P, X, T, rows, 1.0, 1.0, G, loss, st.cuda_stream)))
+                for what, flop, fn in calls:
+                    for _ in range(3):
+                        fn()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    for _ in range(reps):
+                        fn()
+                    e1.record(st)
+                    e1.synchronize()
+                    ms = e0.elapsed_time(e1) / reps
+                    tflops = flop * rows / (ms * 1e-3) / 1e12
+                    gbs = 40.0 * rows / (ms * 1e-3) / 1e9
+                    rows_out.append({"kernel": kname, "call": what, "rows": rows, "ms": round(ms, 4),
+                                     "rows_per_s": rows / (ms * 1e-3), "tflops": round(tflops, 2),
+                                     "tensor_frac": round(tflops / tc, 4), "hbm_gbs": round(gbs, 1),
+                                     "hbm_frac": round(gbs / hbm, 4)})
+            del X, T, Y, G, loss
+    finally:
+        L.lap_mlp_select(L.LAP_MLP_TCGEN05)
+    return {"rows": rows_out, "flop_per_row": {"forward": MLP_FLOP_FWD, "loss_grad": MLP_FLOP_TRAIN},
+            "bytes_per_row": 40, "peaks": {"bf16_tflops": tc, "bf16_kind": tc_kind, "hbm_gbs": hbm,
+                                           "hbm_kind": hbm_kind},
+            "note": "each call is one launch; forward reads X (32 B) and writes Y (8 B) per row, loss+gradient "
+                    "reads X and T; 8192 rows is the training batch"}
+
+
 def cv_diagnostics(torch, LapGraph, params, graphs=None, omega=1 << 18, samples=8192):
     """What the trained network learned, on held-out graphs small enough for
     near-exact targets: R^2 of head 0 against the mean Wilson visits of
@@ -1350,6 +1416,8 @@ def run_ours(args, rank, world):
     if rank == 0 and args.cv_graphs > 0:
         note("control variate: training data and training")
         params, info = cv_train(torch, LapGraph, args.cv_graphs)
+        note("control variate: MLP kernels (tcgen05 and mma.sync)")
+        info["mlp_kernels"] = mlp_kernel_timing(torch)
         note("control variate: what the network learned (held-out graphs)")
         info["diagnostics"] = cv_diagnostics(torch, LapGraph, params)
         note("control variate: CV vs plain on %s" % g.name)

@@ -444,6 +444,18 @@ lap_status lap_cv_estimates(lap_graph *g, double beta1, double beta2, double *ld
 lap_status lap_sample_trace_cv(lap_graph *g, uint64_t n_samples, uint64_t seed, uint64_t *y1_dev, uint64_t *y2_dev,
                                double *m2_dev);
 
+/* MLP kernels.  LAP_MLP_TCGEN05 (the default): fifth-generation tensor-core
+ * products (tcgen05.mma, operands in shared memory, FP32 accumulators in
+ * tensor memory), 128 rows per tile; a product that does not complete within
+ * 1 s makes the call write NaN to its outputs (forward) or its loss
+ * (training).  LAP_MLP_MMA_SYNC: the warp-level mma.sync.m16n8k16 kernel,
+ * kept for comparison.  Both round at the same points (BF16 operands, FP32
+ * accumulation, FP32 bias gradients); they differ only in FP32 summation
+ * order.  lap_mlp_select sets the kernel for every later MLP call of the
+ * process (not per stream); LAP_ERR_INVALID_ARG for any other value. */
+enum lap_mlp_kernel { LAP_MLP_TCGEN05 = 0, LAP_MLP_MMA_SYNC = 1 };
+lap_status lap_mlp_select(int32_t kernel);
+
 /* MLP forward on rows x[rows][8] -> y[rows][2] (device float), BF16 tensor
  * cores with FP32 accumulation; params: LAP_MLP_PARAMS device floats. */
 lap_status lap_mlp_forward(const float *params_dev, const float *x_dev, int64_t rows, float *y_dev, void *cuda_stream);

@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/lap.h: argument checks, device
 // memory of a handle, stream handling, launch sizing and error reporting.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -278,6 +279,16 @@ lap_status poll_status(lap_graph *g)
         return fail(g, LAP_ERR_CUDA, buf);
     }
     return LAP_OK;
+}
+
+// Process-wide choice of the MLP kernel (lap_mlp_select).
+std::atomic<int32_t> g_mlp_kernel{LAP_MLP_TCGEN05};
+
+cudaError_t launch_mlp(const float *P, const float *X, const float *T, int64_t n, float wk0, float wk1, float *Y,
+                       float *G, float *loss, cudaStream_t st)
+{
+    return g_mlp_kernel.load() == LAP_MLP_MMA_SYNC ? lap_launch_mlp_mma_sync(P, X, T, n, wk0, wk1, Y, G, loss, st)
+                                                   : lap_launch_mlp_tc(P, X, T, n, wk0, wk1, Y, G, loss, st);
 }
 
 }  // namespace
@@ -1288,11 +1299,19 @@ lap_status lap_cv_estimates(lap_graph *g, double beta1, double beta2, double *ld
     return LAP_OK;
 }
 
+lap_status lap_mlp_select(int32_t kernel)
+{
+    if (kernel != LAP_MLP_TCGEN05 && kernel != LAP_MLP_MMA_SYNC)
+        return fail(nullptr, LAP_ERR_INVALID_ARG, "MLP kernel must be LAP_MLP_TCGEN05 or LAP_MLP_MMA_SYNC");
+    g_mlp_kernel.store(kernel);
+    return LAP_OK;
+}
+
 lap_status lap_mlp_forward(const float *params_dev, const float *x_dev, int64_t rows, float *y_dev, void *cuda_stream)
 {
     if (!params_dev || !x_dev || !y_dev || rows < 0) return fail(nullptr, LAP_ERR_INVALID_ARG, "bad MLP arguments");
-    cudaError_t e = lap_launch_mlp(params_dev, x_dev, nullptr, rows, 0.f, 0.f, y_dev, nullptr, nullptr,
-                                   reinterpret_cast<cudaStream_t>(cuda_stream));
+    cudaError_t e = launch_mlp(params_dev, x_dev, nullptr, rows, 0.f, 0.f, y_dev, nullptr, nullptr,
+                               reinterpret_cast<cudaStream_t>(cuda_stream));
     return e == cudaSuccess ? LAP_OK : cuda_fail(nullptr, e, "lap_mlp_forward");
 }
 
@@ -1304,7 +1323,7 @@ lap_status lap_mlp_loss_grad(const float *params_dev, const float *x_dev, const 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaMemsetAsync(grad_dev, 0, sizeof(float) * LAP_MLP_PARAMS, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(loss_dev, 0, sizeof(float), st);
-    if (e == cudaSuccess) e = lap_launch_mlp(params_dev, x_dev, t_dev, rows, w0, w1, nullptr, grad_dev, loss_dev, st);
+    if (e == cudaSuccess) e = launch_mlp(params_dev, x_dev, t_dev, rows, w0, w1, nullptr, grad_dev, loss_dev, st);
     return e == cudaSuccess ? LAP_OK : cuda_fail(nullptr, e, "lap_mlp_loss_grad");
 }
 

@@ -238,8 +238,12 @@ cudaError_t lap_launch_beta1_reduce(int32_t n, int32_t batches, const double *vb
                                     double *out, cudaStream_t st);
 cudaError_t lap_launch_beta2_reduce(const unsigned long long *y1, const unsigned long long *y2, const double *m2,
                                     int64_t count, double *red, double *out, cudaStream_t st);
-cudaError_t lap_launch_mlp(const float *P, const float *X, const float *T, int64_t n, float wk0, float wk1,
-                           float *Y, float *G, float *loss, cudaStream_t st);
+// MLP forward (T = nullptr) or loss and gradient: mlp_tc.cu (tcgen05, TMEM
+// accumulators) or mlp.cu (mma.sync), per lap_mlp_select.
+cudaError_t lap_launch_mlp_tc(const float *P, const float *X, const float *T, int64_t n, float wk0, float wk1,
+                              float *Y, float *G, float *loss, cudaStream_t st);
+cudaError_t lap_launch_mlp_mma_sync(const float *P, const float *X, const float *T, int64_t n, float wk0,
+                                    float wk1, float *Y, float *G, float *loss, cudaStream_t st);
 cudaError_t lap_launch_adamw(float *w, float *m, float *v, const float *g, int64_t count, int32_t step, float lr,
                              float b1, float b2, float eps, float wd, cudaStream_t st);
 

@@ -393,8 +393,8 @@ int current_sms()
 
 }  // namespace
 
-cudaError_t lap_launch_mlp(const float *P, const float *X, const float *T, int64_t n, float wk0, float wk1,
-                           float *Y, float *G, float *loss, cudaStream_t st)
+cudaError_t lap_launch_mlp_mma_sync(const float *P, const float *X, const float *T, int64_t n, float wk0,
+                                     float wk1, float *Y, float *G, float *loss, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const size_t smem = sizeof(Smem);

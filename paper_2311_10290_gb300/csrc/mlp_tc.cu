@@ -1,0 +1,522 @@
+// MLP of the learned control variate on the fifth-generation tensor cores:
+// tcgen05.mma with BF16 operands in shared memory and FP32 accumulators in
+// tensor memory (TMEM).  Same network, parameter packing and rounding points
+// as the mma.sync kernel of mlp.cu: 8 features -> 64 -> 64 -> 2 (ReLU),
+// inputs, weights, hidden activations and back-propagated errors rounded to
+// BF16 where they enter a product, biases, accumulators, bias gradients and
+// the loss in FP32.
+//
+// One CTA of 128 threads works on tiles of 128 rows: row r of a tile is TMEM
+// lane r and thread r (warp w reads lanes 32w..32w+31).  Per tile, one thread
+// issues each layer's products (M = 128, N = 16..64, K in steps of 16) and
+// commits them to an mbarrier; all threads wait on it, read their row's
+// accumulators with tcgen05.ld, apply bias and ReLU, and write the next
+// operand to shared memory.  Training adds the backward pass:
+//   dY  = 2 w (Y - T) / N                      (FP32, per thread)
+//   dH2 = (dY W3) * relu'(Z2)                  MMA, M 128, N 64, K 16
+//   dH1 = (dH2 W2) * relu'(Z1)                 MMA, M 128, N 64, K 64
+//   [dH2^T; dH1^T] H1    -> rows 0..63: dW2    MMA, M 128, N 64, K 128 (rows)
+//   [dH1^T; H2^T] [X | dY] -> dW1 and dW3^T    MMA, M 128, N 32, K 128
+// The two weight-gradient products accumulate in TMEM across all tiles of the
+// CTA (the other halves of their outputs are not used) and are added to the
+// global gradient once.  Bias gradients sum the unrounded FP32 errors through
+// a shared-memory transpose.
+//
+// Operands use the canonical no-swizzle K-major layout: 8x8 core matrices of
+// 128 contiguous bytes (8 rows of 16 bytes), core matrices adjacent along K
+// 128 bytes apart (leading byte offset), groups of 8 rows (K/8)*128 bytes
+// apart (stride byte offset).
+//
+// Every wait on the mbarrier is bounded (1 s of %globaltimer); a wait that
+// runs out stops the CTA, waits once more (bounded) for its products in
+// flight, frees its TMEM and writes NaN to its outputs (forward) or to the
+// loss (training).
+#include <cuda_bf16.h>
+
+#include "lap_internal.h"
+
+namespace {
+
+constexpr int kIn = 8, kHid = 64, kOut = 2;
+constexpr int oW1 = 0, ob1 = oW1 + kHid * kIn, oW2 = ob1 + kHid, ob2 = oW2 + kHid * kHid, oW3 = ob2 + kHid,
+              ob3 = oW3 + kOut * kHid, kParams = ob3 + kOut;
+static_assert(kParams == LAP_MLP_PARAMS, "packed parameter layout");
+
+constexpr int kTile = 128;       // rows per tile = TMEM lanes = threads
+constexpr int kThreads = 128;
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+// Byte offset of element (r, k) of a K-major operand with K columns.
+__host__ __device__ constexpr uint32_t cm_off(int r, int k, int K)
+{
+    return (uint32_t)((((r >> 3) * (K >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+// Shared-memory layout (bytes).  Forward operands first; training adds the
+// backward operands and the FP32 transpose buffer.
+constexpr uint32_t oX = 0;                              // A  [128 x 16]  X (features 0..7)
+constexpr uint32_t oSW1 = oX + kTile * 16 * 2;          // B  [64 x 16]   W1
+constexpr uint32_t oH1 = oSW1 + 64 * 16 * 2;            // A  [128 x 64]  H1
+constexpr uint32_t oSW2 = oH1 + kTile * 64 * 2;         // B  [64 x 64]   W2
+constexpr uint32_t oH2 = oSW2 + 64 * 64 * 2;            // A  [128 x 64]  H2
+constexpr uint32_t oSW3 = oH2 + kTile * 64 * 2;         // B  [16 x 64]   W3 (rows 0..1)
+constexpr uint32_t kFwdOps = oSW3 + 16 * 64 * 2;
+constexpr uint32_t oDY = kFwdOps;                       // A  [128 x 16]  dY (columns 0..1)
+constexpr uint32_t oSW3T = oDY + kTile * 16 * 2;        // B  [64 x 16]   W3^T (columns 0..1)
+constexpr uint32_t oDH2 = oSW3T + 64 * 16 * 2;          // A  [128 x 64]  dH2
+constexpr uint32_t oSW2T = oDH2 + kTile * 64 * 2;       // B  [64 x 64]   W2^T
+constexpr uint32_t oT = oSW2T + 64 * 64 * 2;            // A  [192 x 128] dH2^T | dH1^T | H2^T
+constexpr uint32_t oB1 = oT + 192 * kTile * 2;          // B  [64 x 128]  H1^T
+constexpr uint32_t oB2 = oB1 + 64 * kTile * 2;          // B  [32 x 128]  X^T (0..7) | dY^T (16..17)
+constexpr uint32_t kTrainOps = oB2 + 32 * kTile * 2;
+constexpr int kFLd = 65;                                // FP32 transpose buffer row length
+constexpr uint32_t oF = kTrainOps;
+constexpr uint32_t kTrainF = oF + kTile * kFLd * 4;
+
+struct Small {
+    unsigned long long bar;
+    uint32_t tmem;
+    uint32_t pad;
+    float b1[kHid], b2[kHid], b3[kOut];
+    float gb1[kHid], gb2[kHid], gb3[kOut];
+    float loss;
+};
+
+constexpr uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+constexpr uint32_t kFwdBytes = align_up(kFwdOps, 16) + (uint32_t)sizeof(Small);
+constexpr uint32_t kTrainBytes = align_up(kTrainF, 16) + (uint32_t)sizeof(Small);
+
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor, no swizzle: start >> 4 (bits 0-13), leading
+// byte offset >> 4 (16-29), stride byte offset >> 4 (32-45), version 1 (46).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+// D (+)= A B^T over `steps` K-steps of 16; A and B K-major with K columns.
+__device__ __forceinline__ void gemm(uint32_t d, uint32_t sa, uint32_t sb, int K, int steps, uint32_t id, bool acc)
+{
+    const uint32_t sbo = (uint32_t)(K >> 3) << 7;
+    for (int ks = 0; ks < steps; ++ks)
+        mma_bf16(d, sdesc(sa + 256u * ks, 128u, sbo), sdesc(sb + 256u * ks, 128u, sbo), id, (acc || ks) ? 1u : 0u);
+}
+
+__device__ __forceinline__ void commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the mbarrier phase with the given parity.
+__device__ bool wait_phase(uint32_t bar, uint32_t parity)
+{
+    const uint64_t t0 = now_ns();
+    for (uint32_t it = 1;; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+        if ((it & 63u) == 0 && now_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+// 16 consecutive FP32 columns of this thread's lane, waited for in the same
+// statement so that no use of the registers is scheduled before the wait.
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tm_ld64(uint32_t taddr, float *v)
+{
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tm_ld16(taddr + 16u * c, v + 16 * c);
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void st_bf16(unsigned char *sm, uint32_t off, float x)
+{
+    *reinterpret_cast<__nv_bfloat16 *>(sm + off) = __float2bfloat16_rn(x);
+}
+
+// Row r (64 values) of a K-major [128 x 64] operand: eight 16-byte stores.
+__device__ __forceinline__ void st_row64(unsigned char *sm, uint32_t base, int r, const float *h)
+{
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        const uint4 q = make_uint4(pack2(h[8 * g], h[8 * g + 1]), pack2(h[8 * g + 2], h[8 * g + 3]),
+                                   pack2(h[8 * g + 4], h[8 * g + 5]), pack2(h[8 * g + 6], h[8 * g + 7]));
+        *reinterpret_cast<uint4 *>(sm + base + cm_off(r, 8 * g, 64)) = q;
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+template <bool TRAIN>
+__global__ void __launch_bounds__(kThreads, TRAIN ? 1 : 4) mlp_tc_kernel(const float *__restrict__ P, const float *__restrict__ X,
+                                                            const float *__restrict__ T, int64_t n, float wk0,
+                                                            float wk1, float inv_n, float *__restrict__ Y,
+                                                            float *__restrict__ G, float *__restrict__ loss)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    constexpr uint32_t kOps = TRAIN ? align_up(kTrainF, 16) : align_up(kFwdOps, 16);
+    constexpr uint32_t kCols = TRAIN ? 256u : 128u;
+    Small &s = *reinterpret_cast<Small *>(sm + kOps);
+    float *sF = reinterpret_cast<float *>(sm + oF);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t s0 = smem_u32(sm), bar = smem_u32(&s.bar);
+
+    for (uint32_t i = tid; i < kOps / 16; i += kThreads) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    for (int i = tid; i < kHid * kIn; i += kThreads) st_bf16(sm, oSW1 + cm_off(i / kIn, i % kIn, 16), P[oW1 + i]);
+    for (int i = tid; i < kHid * kHid; i += kThreads) {
+        const int u = i / kHid, j = i % kHid;
+        st_bf16(sm, oSW2 + cm_off(u, j, 64), P[oW2 + i]);
+        if (TRAIN) st_bf16(sm, oSW2T + cm_off(j, u, 64), P[oW2 + i]);
+    }
+    for (int i = tid; i < kOut * kHid; i += kThreads) {
+        const int o = i / kHid, j = i % kHid;
+        st_bf16(sm, oSW3 + cm_off(o, j, 64), P[oW3 + i]);
+        if (TRAIN) st_bf16(sm, oSW3T + cm_off(j, o, 16), P[oW3 + i]);
+    }
+    if (tid < kHid) {
+        s.b1[tid] = P[ob1 + tid];
+        s.b2[tid] = P[ob2 + tid];
+        s.gb1[tid] = 0.f;
+        s.gb2[tid] = 0.f;
+    }
+    if (tid < kOut) {
+        s.b3[tid] = P[ob3 + tid];
+        s.gb3[tid] = 0.f;
+    }
+    if (tid == 0) {
+        s.loss = 0.f;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&s.tmem)),
+                     "r"(kCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_proxy();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tm = s.tmem;
+    const uint32_t lane_tm = tm + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes
+
+    uint32_t parity = 0;
+    bool ok = true, any = false;
+    for (int64_t tile = blockIdx.x; tile * kTile < n; tile += gridDim.x) {
+        const int64_t row = tile * kTile + tid;
+        const bool valid = row < n;
+
+        // ---- X (BF16) as layer 1's A operand and (training) X^T
+        float x[kIn];
+        {
+            const float4 a = valid ? *reinterpret_cast<const float4 *>(X + row * kIn) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 b = valid ? *reinterpret_cast<const float4 *>(X + row * kIn + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+            *reinterpret_cast<uint4 *>(sm + oX + cm_off(tid, 0, 16)) =
+                make_uint4(pack2(x[0], x[1]), pack2(x[2], x[3]), pack2(x[4], x[5]), pack2(x[6], x[7]));
+            if (TRAIN) {
+#pragma unroll
+                for (int f = 0; f < kIn; ++f) st_bf16(sm, oB2 + cm_off(f, tid, 128), x[f]);
+            }
+        }
+        fence_proxy();
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            gemm(tm + 0, s0 + oX, s0 + oSW1, 16, 1, idesc(128, 64), false);
+            commit(bar);
+        }
+        ok = __syncthreads_and(wait_phase(bar, parity));
+        parity ^= 1u;
+        if (!ok) break;
+        fence_after();
+
+        // ---- layer 1 epilogue: H1 = relu(Z1 + b1)
+        float h[kHid];
+        uint64_t m1 = 0, m2 = 0;
+        tm_ld64(lane_tm + 0, h);
+#pragma unroll
+        for (int j = 0; j < kHid; ++j) {
+            const float z = h[j] + s.b1[j];
+            if (z > 0.f) m1 |= 1ull << j;
+            h[j] = fmaxf(z, 0.f);
+        }
+        st_row64(sm, oH1, tid, h);
+        if (TRAIN) {
+#pragma unroll
+            for (int j = 0; j < kHid; ++j) st_bf16(sm, oB1 + cm_off(j, tid, 128), h[j]);
+        }
+        fence_proxy();
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            gemm(tm + 64, s0 + oH1, s0 + oSW2, 64, 4, idesc(128, 64), false);
+            commit(bar);
+        }
+        ok = __syncthreads_and(wait_phase(bar, parity));
+        parity ^= 1u;
+        if (!ok) break;
+        fence_after();
+
+        // ---- layer 2 epilogue: H2 = relu(Z2 + b2)
+        tm_ld64(lane_tm + 64, h);
+#pragma unroll
+        for (int j = 0; j < kHid; ++j) {
+            const float z = h[j] + s.b2[j];
+            if (z > 0.f) m2 |= 1ull << j;
+            h[j] = fmaxf(z, 0.f);
+        }
+        st_row64(sm, oH2, tid, h);
+        if (TRAIN) {
+#pragma unroll
+            for (int j = 0; j < kHid; ++j) st_bf16(sm, oT + cm_off(128 + j, tid, 128), h[j]);
+        }
+        fence_proxy();
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            gemm(tm + 0, s0 + oH2, s0 + oSW3, 64, 4, idesc(128, 16), false);
+            commit(bar);
+        }
+        ok = __syncthreads_and(wait_phase(bar, parity));
+        parity ^= 1u;
+        if (!ok) break;
+        fence_after();
+
+        // ---- layer 3 epilogue: Y = Z3 + b3
+        float y[16];
+        tm_ld16(lane_tm + 0, y);
+        y[0] += s.b3[0];
+        y[1] += s.b3[1];
+        if (!TRAIN) {
+            if (valid) *reinterpret_cast<float2 *>(Y + row * kOut) = make_float2(y[0], y[1]);
+            fence_before();    // this tile's TMEM reads precede the next tile's products
+            continue;
+        }
+
+        // ---- loss and dY = 2 w_k (y - t) / N (rows beyond n contribute nothing)
+        float dy0 = 0.f, dy1 = 0.f, l = 0.f;
+        if (valid) {
+            const float2 t = *reinterpret_cast<const float2 *>(T + row * kOut);
+            const float e0 = y[0] - t.x, e1 = y[1] - t.y;
+            dy0 = 2.f * wk0 * e0 * inv_n;
+            dy1 = 2.f * wk1 * e1 * inv_n;
+            l = (wk0 * e0 * e0 + wk1 * e1 * e1) * inv_n;
+        }
+        {
+            const float l_w = warp_sum(l), g0 = warp_sum(dy0), g1 = warp_sum(dy1);
+            if ((tid & 31) == 0) {
+                atomicAdd(&s.loss, l_w);
+                atomicAdd(&s.gb3[0], g0);
+                atomicAdd(&s.gb3[1], g1);
+            }
+        }
+        *reinterpret_cast<uint4 *>(sm + oDY + cm_off(tid, 0, 16)) = make_uint4(pack2(dy0, dy1), 0u, 0u, 0u);
+        st_bf16(sm, oB2 + cm_off(16, tid, 128), dy0);
+        st_bf16(sm, oB2 + cm_off(17, tid, 128), dy1);
+        fence_proxy();
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            gemm(tm + 64, s0 + oDY, s0 + oSW3T, 16, 1, idesc(128, 64), false);
+            commit(bar);
+        }
+        ok = __syncthreads_and(wait_phase(bar, parity));
+        parity ^= 1u;
+        if (!ok) break;
+        fence_after();
+
+        // ---- dH2 = (dY W3) * relu'(Z2)
+        tm_ld64(lane_tm + 64, h);
+#pragma unroll
+        for (int j = 0; j < kHid; ++j) {
+            h[j] = (m2 >> j) & 1ull ? h[j] : 0.f;
+            sF[tid * kFLd + j] = h[j];
+        }
+        st_row64(sm, oDH2, tid, h);
+#pragma unroll
+        for (int j = 0; j < kHid; ++j) st_bf16(sm, oT + cm_off(j, tid, 128), h[j]);
+        fence_proxy();
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            gemm(tm + 0, s0 + oDH2, s0 + oSW2T, 64, 4, idesc(128, 64), false);
+            commit(bar);
+        }
+        {   // bias gradient b2: column sums of the unrounded dH2 (two halves of the rows)
+            const int u = tid & 63, r0 = (tid >> 6) * 64;
+            float a = 0.f;
+            for (int r = r0; r < r0 + 64; ++r) a += sF[r * kFLd + u];
+            atomicAdd(&s.gb2[u], a);
+        }
+        __syncthreads();
+        ok = __syncthreads_and(wait_phase(bar, parity));
+        parity ^= 1u;
+        if (!ok) break;
+        fence_after();
+
+        // ---- dH1 = (dH2 W2) * relu'(Z1)
+        tm_ld64(lane_tm + 0, h);
+#pragma unroll
+        for (int j = 0; j < kHid; ++j) {
+            h[j] = (m1 >> j) & 1ull ? h[j] : 0.f;
+            sF[tid * kFLd + j] = h[j];
+            st_bf16(sm, oT + cm_off(64 + j, tid, 128), h[j]);
+        }
+        fence_proxy();
+        fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+            // rows 0..63 of [dH2^T; dH1^T] H1 are dW2; rows 0..63 of
+            // [dH1^T; H2^T] [X | dY] columns 0..7 are dW1, rows 64..127
+            // columns 16..17 are dW3^T.
+            gemm(tm + 128, s0 + oT, s0 + oB1, 128, 8, idesc(128, 64), any);
+            gemm(tm + 192, s0 + oT + cm_off(64, 0, 128), s0 + oB2, 128, 8, idesc(128, 32), any);
+            commit(bar);
+        }
+        any = true;
+        {
+            const int u = tid & 63, r0 = (tid >> 6) * 64;
+            float a = 0.f;
+            for (int r = r0; r < r0 + 64; ++r) a += sF[r * kFLd + u];
+            atomicAdd(&s.gb1[u], a);
+        }
+        // The gradient products read T, B1 and B2: wait before the next tile writes them.
+        ok = __syncthreads_and(wait_phase(bar, parity));
+        parity ^= 1u;
+        if (!ok) break;
+        fence_after();
+    }
+
+    if (!ok) {
+        // A product did not complete in time: wait once more (bounded) for the
+        // phase in flight, then report through the outputs.
+        wait_phase(bar, parity ^ 1u);
+        if (TRAIN) {
+            if (tid == 0) atomicAdd(loss, __int_as_float(0x7fc00000));
+        } else {
+            for (int64_t tile = blockIdx.x; tile * kTile < n; tile += gridDim.x) {
+                const int64_t row = tile * kTile + tid;
+                if (row < n) *reinterpret_cast<float2 *>(Y + row * kOut) = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+            }
+        }
+    } else if (TRAIN && any) {
+        const int m = warp * 32 + (tid & 31);     // TMEM lane = row of the gradient products
+        float v[kHid];
+        if (warp < 2) {
+            tm_ld64(lane_tm + 128, v);
+#pragma unroll
+            for (int j = 0; j < kHid; ++j) atomicAdd(&G[oW2 + m * kHid + j], v[j]);
+            tm_ld16(lane_tm + 192, v);
+#pragma unroll
+            for (int f = 0; f < kIn; ++f) atomicAdd(&G[oW1 + m * kIn + f], v[f]);
+        } else {
+            tm_ld16(lane_tm + 192 + 16, v);
+            atomicAdd(&G[oW3 + 0 * kHid + (m - 64)], v[0]);
+            atomicAdd(&G[oW3 + 1 * kHid + (m - 64)], v[1]);
+        }
+        __syncthreads();
+        if (tid < kHid) {
+            atomicAdd(&G[ob1 + tid], s.gb1[tid]);
+            atomicAdd(&G[ob2 + tid], s.gb2[tid]);
+        }
+        if (tid < kOut) atomicAdd(&G[ob3 + tid], s.gb3[tid]);
+        if (tid == 0) atomicAdd(loss, s.loss);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tm), "r"(kCols) : "memory");
+    }
+}
+
+}  // namespace
+
+cudaError_t lap_launch_mlp_tc(const float *P, const float *X, const float *T, int64_t n, float wk0, float wk1,
+                              float *Y, float *G, float *loss, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles = (n + kTile - 1) / kTile;
+    if (T) {
+        // One CTA per SM (shared memory), 256 TMEM columns each.
+        const int grid = (int)(tiles < sms ? tiles : sms);
+        cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kTrainBytes);
+        if (e != cudaSuccess) return e;
+        mlp_tc_kernel<true><<<grid, kThreads, kTrainBytes, st>>>(P, X, T, n, wk0, wk1, 1.f / (float)n, Y, G, loss);
+    } else {
+        // Up to four CTAs per SM: 4 x 128 TMEM columns fill the SM's 512.
+        const int64_t cap = (int64_t)sms * 4;
+        const int grid = (int)(tiles < cap ? tiles : cap);
+        cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kFwdBytes);
+        if (e != cudaSuccess) return e;
+        mlp_tc_kernel<false><<<grid, kThreads, kFwdBytes, st>>>(P, X, nullptr, n, 0.f, 0.f, 0.f, Y, nullptr, nullptr);
+    }
+    return cudaGetLastError();
+}

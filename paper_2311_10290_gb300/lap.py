@@ -31,6 +31,7 @@ LAP_OPT_PATH_START = 8
 LAP_OPT_WALKERS = 9
 LAP_STAT_SLOTS, LAP_STAT_KERNEL, LAP_STAT_FALLBACKS, LAP_STAT_LAST_KERNEL = 1, 2, 3, 4
 LAP_MLP_PARAMS = 4866
+LAP_MLP_TCGEN05, LAP_MLP_MMA_SYNC = 0, 1
 LAP_BOPT_LANES, LAP_BOPT_CLAIM, LAP_BOPT_ORDER, LAP_BOPT_BLOCK, LAP_BOPT_STACK, LAP_BOPT_PATHS = 1, 2, 3, 4, 5, 6
 LAP_BSTAT_LANES, LAP_BSTAT_CLAIM, LAP_BSTAT_UNITS, LAP_BSTAT_RERUNS, LAP_BSTAT_GRAPH_CAPTURES = 1, 2, 3, 4, 5
 
@@ -99,6 +100,7 @@ def library():
         "lap_cv_set_sums": (i32, [vp, vp, vp, vp, ctypes.c_int]),
         "lap_cv_estimates": (i32, [vp, ctypes.c_double, ctypes.c_double, vp, vp, ctypes.c_int, vp, vp]),
         "lap_sample_trace_cv": (i32, [vp, u64, u64, vp, vp, vp]),
+        "lap_mlp_select": (i32, [i32]),
         "lap_mlp_forward": (i32, [vp, vp, i64, vp, vp]),
         "lap_mlp_loss_grad": (i32, [vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp, vp, vp]),
         "lap_adamw": (i32, [vp, vp, vp, vp, i64, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -421,6 +423,10 @@ def lap_cv_estimates(h, n, beta1, beta2, ecc_out=None):
 
 def lap_sample_trace_cv(h, n_samples, seed, y1_dev, y2_dev, m2_dev):
     _check(library().lap_sample_trace_cv(h, int(n_samples), int(seed), _dp(y1_dev), _dp(y2_dev), _dp(m2_dev)), h)
+
+
+def lap_mlp_select(kernel):
+    _check(library().lap_mlp_select(int(kernel)))
 
 
 def lap_mlp_forward(params_dev, x_dev, rows, y_dev, stream=0):
