@@ -88,9 +88,10 @@ typedef enum {
                                   3 = several walkers per sample (LAP_OPT_WALKERS lanes share one
                                   Wilson run; 2 bytes of state per node): more independent memory
                                   chains when a call has few samples, and each sample finishes
-                                  sooner.  Kernel 3 needs n < 2^22 and covers the plain estimators
-                                  only (LAP_OPT_PATHS = 0, no control variate; otherwise kernel 2
-                                  runs).  Its samples that do not fit (a node drawn 1023 times, a
+                                  sooner.  Kernel 3 needs n < 2^22 and covers the estimators with
+                                  their own absorbed walks, with or without the control variate
+                                  (with LAP_OPT_PATHS = 1 kernel 2 runs instead).  Its samples
+                                  that do not fit (a node drawn 1023 times, a
                                   path longer than a walker's stack, a walker without progress for
                                   4 s) are withdrawn and re-run with kernel 1.
                                   Counts are identical with every kernel. */

@@ -109,11 +109,12 @@ uint64_t slot_bytes_of(const lap_graph *g, int kernel)
             255ull) & ~255ull;
 }
 
-// Kernel 3 covers the plain estimators (own draws, no control variate) on
-// graphs with n < 2^22 (its stack entries hold 22-bit node ids).
+// Kernel 3 covers the estimators with independent absorbed walks (no
+// loop-included paths), with or without the control variate, on graphs with
+// n < 2^22 (its stack entries hold 22-bit node ids).
 bool group_ok(const lap_graph *g)
 {
-    return g->n < (1 << 22) && !g->paths_opt && !g->cv1 && !g->cv2 && !g->compact_disabled &&
+    return g->n < (1 << 22) && !g->paths_opt && !g->compact_disabled &&
            (!g->ws || g->ws_bytes >= slot_bytes_of(g, LAP_KERNEL_GROUP));
 }
 

@@ -34,7 +34,13 @@
 // A sample that does not fit (a node drawn 1023 (511) times, a path longer than the
 // walker's stack, or a walker without progress for kStallNs) is withdrawn
 // exactly as in the 1-byte kernel: the group subtracts k - 1 for every node
-// and lists the id for a re-run with the 8-byte kernel.
+// (and, with the control variate, the potentials of all k draws) and lists
+// the id for a re-run with the 8-byte kernel.
+//
+// Control variate (CV): each Wilson draw of u with target w adds h1[w] to
+// A1[u] (once per draw: a pending arrow taken again adds nothing), and the
+// pi-start walk adds h2[w] to A2[u], 1 to P2[u] and (d_u h2[w] - S2[u]) / d_u
+// to the sample's M2, as in the other samplers.
 #include "lap_internal.h"
 #include "philox.cuh"
 
@@ -148,6 +154,12 @@ __device__ __forceinline__ int32_t ld_col(const int32_t *a, uint64_t pol)
     asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
     return v;
 }
+__device__ __forceinline__ long long ld_pot(const long long *a)
+{
+    long long v;
+    asm volatile("ld.global.nc.s64 %0, [%1];" : "=l"(v) : "l"(a));
+    return v;
+}
 // Target of draw k at node u (row record r of u), sample i.
 __device__ __forceinline__ int32_t arrow_of(const int32_t *col, uint64_t r, uint32_t u, uint32_t k, uint32_t i,
                                             uint32_t key0, uint32_t key1, uint64_t pol)
@@ -158,7 +170,7 @@ __device__ __forceinline__ int32_t arrow_of(const int32_t *col, uint64_t r, uint
 
 enum : uint32_t { G_SCAN = 0, G_STEP, G_MOVE, G_DONE };
 
-template <int W>
+template <int W, bool CV>
 __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
 {
     static_assert(W == 2 || W == 4 || W == 8 || W == 16, "walkers per sample");
@@ -225,6 +237,7 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
         uint64_t y1 = 0;
         uint32_t committed = 0;              // nodes this walker added to the tree, not yet in ctl->tree
         uint32_t iter = 0;
+        bool cvp = false;                    // CV: the head's new draw still owes h1[w] to A1[h]
         unsigned long long tprog = 0;        // last progress (set when a wait or an idle sweep begins)
         bool waiting = false;
         bool withdraw = false;
@@ -278,6 +291,9 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
                 continue;
             }
             if (phase == G_STEP) {
+                // Checked before a draw, so that every counted draw reaches G_MOVE
+                // (where its control-variate term is added).
+                if (((++iter) & 255u) == 0u && ld_u32(&ctl->status)) { phase = G_DONE; break; }
                 // Take the head's arrow: its pending one, or its next stack entry.
                 uint32_t kd;
                 if (hpend) {
@@ -294,12 +310,12 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
                     // reads its draw count, from the path entry.
                     top = (uint32_t)h | (hk << kNodeBits);
                     if (y1 > limit) { bad |= LAP_DEV_STEP_LIMIT; withdraw = true; phase = G_DONE; break; }
+                    cvp = CV && p.cv_h1;
                 }
                 top = (uint32_t)h | (hk << kNodeBits);
                 w = arrow_of(col, hrow, (uint32_t)h, kd, i, key0, key1, keep);
                 ew = 0xFFFFFFFFu;
                 phase = G_MOVE;
-                if (((++iter) & 255u) == 0u && ld_u32(&ctl->status)) { phase = G_DONE; break; }
                 // fall through to the claim in the same iteration
             }
             if (phase == G_MOVE) {
@@ -307,10 +323,16 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
                 // that claims it (InTree is final, so a plain read of it is
                 // conclusive; most steps end in the tree).
                 const uint64_t row = ld_row(rowinfo, w, keep);
+                long long hv = 0;
+                if (CV && cvp) hv = ld_pot(p.cv_h1 + w);     // issued with the row and word reads
                 uint32_t old;
                 bool claimed = false;
                 if (ew == 0xFFFFFFFFu) {
                     old = ld_word(st + w);
+                    if (CV && cvp) {
+                        atomicAdd(&p.cv_a1[h], (unsigned long long)hv);
+                        cvp = false;
+                    }
                     if (w_free<W>(old)) {
                         ew = old;
                         old = cas_word(st + w, ew, ew | mine);
@@ -417,6 +439,13 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
             for (int32_t x = (int32_t)j; x < n; x += W) {
                 const uint32_t k = ld_word(st + x) & L::k;
                 if (k >= 2u) atomicAdd(&p.rep1[x], (unsigned long long)(-(long long)(k - 1u)));
+                if (CV && p.cv_h1 && k) {
+                    // The potentials of all k draws, added to A1[x] one per draw.
+                    const uint64_t r = ld_row(rowinfo, x, keep);
+                    long long sub = 0;
+                    for (uint32_t d = 0; d < k; ++d) sub += ld_pot(p.cv_h1 + arrow_of(col, r, (uint32_t)x, d, i, key0, key1, keep));
+                    atomicAdd(&p.cv_a1[x], (unsigned long long)(-sub));
+                }
             }
             if (j == 0) {
                 const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
@@ -443,15 +472,24 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
             if (j == 1u) {
                 // Alg. 4: the v-absorbed walk from s ~ pi (the head of a uniform arc); Y2 = its length.
                 uint64_t y2 = 0;
+                double m2 = 0.0;
                 int32_t u = ld_col(col + (int64_t)lap::below(lap::philox_r64(0u, 0u, i, 2u, key0, key1), (uint64_t)p.g.arcs), keep);
                 while (u != v) {
                     if (++y2 > limit) { bad |= LAP_DEV_STEP_LIMIT; break; }
                     const uint64_t r = ld_row(rowinfo, u, keep);
-                    u = ld_col(col + (int64_t)(int32_t)(uint32_t)r +
-                               (int64_t)lap::below(lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1), (uint32_t)(r >> 32)), keep);
+                    const int32_t x = ld_col(col + (int64_t)(int32_t)(uint32_t)r +
+                                             (int64_t)lap::below(lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1), (uint32_t)(r >> 32)), keep);
+                    if (CV && p.cv_h2) {
+                        const long long d = (long long)(r >> 32), hx = ld_pot(p.cv_h2 + x), s2 = ld_pot(p.cv_S2 + u);
+                        atomicAdd(&p.cv_a2[u], (unsigned long long)hx);
+                        atomicAdd(&p.cv_p2[u], 1ull);
+                        m2 = __dadd_rn(m2, __ddiv_rn((double)(d * hx - s2), (double)d));
+                    }
+                    u = x;
                 }
                 acc2 += y2;
                 if (p.y2_out) p.y2_out[i - p.first] = y2;
+                if (CV && p.m2_out) p.m2_out[i - p.first] = m2;
             }
         }
         __syncwarp(gmask);
@@ -459,6 +497,13 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
     if (acc1) atomicAdd(&p.acc->sum_y1, acc1);
     if (acc2) atomicAdd(&p.acc->sum_y2, acc2);
     if (bad) atomicOr(&p.acc->status, bad);
+}
+
+template <int W>
+void launch_group(const LapSampleLaunch &p, bool cv, uint64_t grid, int block, cudaStream_t st)
+{
+    if (cv) lewalk_group_kernel<W, true><<<(unsigned)grid, block, 0, st>>>(p);
+    else lewalk_group_kernel<W, false><<<(unsigned)grid, block, 0, st>>>(p);
 }
 
 }  // namespace
@@ -469,10 +514,11 @@ cudaError_t lap_launch_sample_group(const LapSampleLaunch &p, int walkers, cudaS
     const uint64_t lanes = p.slots * (uint64_t)walkers;
     const int block = 256;
     const uint64_t grid = (lanes + block - 1) / block;
-    if (walkers == 2) lewalk_group_kernel<2><<<(unsigned)grid, block, 0, st>>>(p);
-    else if (walkers == 4) lewalk_group_kernel<4><<<(unsigned)grid, block, 0, st>>>(p);
-    else if (walkers == 8) lewalk_group_kernel<8><<<(unsigned)grid, block, 0, st>>>(p);
-    else if (walkers == 16) lewalk_group_kernel<16><<<(unsigned)grid, block, 0, st>>>(p);
+    const bool cv = p.cv_h1 || p.cv_h2;
+    if (walkers == 2) launch_group<2>(p, cv, grid, block, st);
+    else if (walkers == 4) launch_group<4>(p, cv, grid, block, st);
+    else if (walkers == 8) launch_group<8>(p, cv, grid, block, st);
+    else if (walkers == 16) launch_group<16>(p, cv, grid, block, st);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

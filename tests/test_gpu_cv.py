@@ -20,8 +20,9 @@ torch = pytest.importorskip("torch")
 
 from paper_2311_10290_gb300 import cv as CVG  # noqa: E402
 from paper_2311_10290_gb300.lap import (LAP_MLP_MMA_SYNC, LAP_MLP_PARAMS, LAP_MLP_TCGEN05, LAP_OPT_KERNEL,  # noqa: E402
-                                        LAP_OPT_PATHS, LapGraph, lap_adamw, lap_mlp_forward, lap_mlp_loss_grad,
-                                        lap_mlp_select)
+                                        LAP_OPT_PATHS, LAP_OPT_STACK, LAP_OPT_WALKERS, LAP_STAT_FALLBACKS,
+                                        LAP_STAT_LAST_KERNEL, LapGraph, lap_adamw, lap_mlp_forward,
+                                        lap_mlp_loss_grad, lap_mlp_select)
 
 
 def packed(p):
@@ -63,13 +64,17 @@ def test_hitting_walks_bit_exact():
     assert np.array_equal(s, oracle.hitting_walks(g.row_ptr, g.col, v, 99, 7))
 
 
-def _cv_run(g, root, seed, omega, phi1, phi2, kernel=None, splits=None, paths=False):
+def _cv_run(g, root, seed, omega, phi1, phi2, kernel=None, splits=None, paths=False, walkers=0, stack=0):
     G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 28)
     try:
         if kernel:
             G.set_option(LAP_OPT_KERNEL, kernel)
         if paths:
             G.set_option(LAP_OPT_PATHS, 1)
+        if walkers:
+            G.set_option(LAP_OPT_WALKERS, walkers)
+        if stack:
+            G.set_option(LAP_OPT_STACK, stack)
         v = G.set_root(root)
         G.cv_set_potentials(None if phi1 is None else torch.from_numpy(phi1).cuda(),
                             None if phi2 is None else torch.from_numpy(phi2).cuda())
@@ -78,47 +83,84 @@ def _cv_run(g, root, seed, omega, phi1, phi2, kernel=None, splits=None, paths=Fa
         c1, c2, s = G.counts()
         a1, a2, p2 = G.cv_sums()
         ld, ec, kc, m2 = G.cv_estimates(0.9, 1.1)
-        return dict(v=v, c1=c1, c2=c2, s=s, a1=a1, a2=a2, p2=p2, ld=ld, ec=ec, kc=kc, m2=m2)
+        return dict(v=v, c1=c1, c2=c2, s=s, a1=a1, a2=a2, p2=p2, ld=ld, ec=ec, kc=kc, m2=m2,
+                    kernel=G.stat(LAP_STAT_LAST_KERNEL), fallbacks=G.stat(LAP_STAT_FALLBACKS))
     finally:
         G.close()
 
 
 @pytest.mark.parametrize("paths", [False, True], ids=["own_draws", "stack_paths"])
-@pytest.mark.parametrize("kernel", [1, 2], ids=["wide", "compact"])
+@pytest.mark.parametrize("kernel", [1, 2, 3], ids=["wide", "compact", "group"])
 @pytest.mark.parametrize("name,maker,root", [("ba", lambda: I.ba(3000, 3, seed=5), -1),
                                              ("rmat", lambda: I.rmat(9, 8, seed=6), -1),
                                              ("path_counts_table", lambda: I.path(50), 0),
                                              ("path_table_heavy", lambda: I.path(256), 255)],
                          ids=["ba", "rmat", "path_counts_table", "path_table_heavy"])
 def test_cv_sums_and_estimates_match_oracle(name, maker, root, kernel, paths):
+    if kernel == 3 and paths:
+        pytest.skip("kernel 3 has no loop-included-path mode")
     g = maker()
     rng = np.random.default_rng(3)
     phi1 = rng.uniform(0.0, 3.0, g.n)
     phi2 = rng.uniform(0.0, 50.0, g.n)
     r = _cv_run(g, root, 17, 300, phi1, phi2, kernel=kernel, splits=[100, 200], paths=paths)
+    assert r["kernel"] == kernel
+    _check_cv(g, r, phi1, phi2, 17, 300, paths)
+
+
+@pytest.mark.parametrize("walkers", [2, 4, 8, 16])
+def test_cv_group_kernel_withdrawn_samples_are_rerun_exactly(walkers):
+    """Kernel 3 with a 16-entry stack per walker on a path graph rooted at
+    one end: samples are withdrawn (their repeat visits and the potentials of
+    all their Wilson draws subtracted) and re-run with kernel 1; every CV sum
+    stays bit-exact."""
+    g = I.path(200)
+    rng = np.random.default_rng(8)
+    phi1 = rng.uniform(0.0, 3.0, g.n)
+    phi2 = rng.uniform(0.0, 50.0, g.n)
+    r = _cv_run(g, 0, 23, 64, phi1, phi2, kernel=3, walkers=walkers, stack=16)
+    assert r["fallbacks"] > 0
+    _check_cv(g, r, phi1, phi2, 23, 64, False)
+
+
+@pytest.mark.parametrize("walkers", [8, 16])
+def test_cv_group_kernel_rmat(walkers):
+    g = I.rmat(12, 8, seed=3)
+    rng = np.random.default_rng(9)
+    phi1 = rng.uniform(0.0, 3.0, g.n)
+    phi2 = rng.uniform(0.0, 50.0, g.n)
+    r = _cv_run(g, -1, 31, 500, phi1, phi2, kernel=3, walkers=walkers, splits=[123, 377])
+    assert r["kernel"] == 3
+    _check_cv(g, r, phi1, phi2, 31, 500, False)
+
+
+def _check_cv(g, r, phi1, phi2, seed, omega, paths):
     v = r["v"]
     h1, h2 = CV.quantize_potential(phi1), CV.quantize_potential(phi2)
-    cnt, a1, a2, p2, m2 = oracle.sample_cv(g.row_ptr, g.col, v, 17, 0, 300, h1=h1, h2=h2, paths=paths)
+    cnt, a1, a2, p2, m2 = oracle.sample_cv(g.row_ptr, g.col, v, seed, 0, omega, h1=h1, h2=h2, paths=paths)
     assert np.array_equal(r["c1"], cnt.cnt1) and np.array_equal(r["c2"], cnt.cnt2)
     assert np.array_equal(r["a1"], a1) and np.array_equal(r["a2"], a2) and np.array_equal(r["p2"], p2)
     z1 = CV.martingale_z1(g.row_ptr, g.col, h1, cnt.cnt1, a1)
     m2t = CV.martingale_m2(g.row_ptr, g.col, h2, a2, p2)
     assert r["m2"] == pytest.approx(m2t, rel=1e-12, abs=1e-6)
-    ld, ec, kc = CV.finalize_cv(g.row_ptr, v, 300, cnt.cnt1, cnt.cnt2, cnt.sum_y1, cnt.sum_y2, z1, m2t, 0.9, 1.1)
+    ld, ec, kc = CV.finalize_cv(g.row_ptr, v, omega, cnt.cnt1, cnt.cnt2, cnt.sum_y1, cnt.sum_y2, z1, m2t, 0.9, 1.1)
     np.testing.assert_allclose(r["ld"], ld, rtol=1e-12)
     np.testing.assert_allclose(r["ec"], ec, rtol=1e-12)
     assert r["kc"] == pytest.approx(kc, rel=1e-12)
 
 
-def test_per_sample_m2_trace_bit_exact():
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_per_sample_m2_trace_bit_exact(kernel):
     g = I.ba(4000, 4, seed=8)
     phi2 = np.random.default_rng(5).uniform(0.0, 30.0, g.n)
     G = LapGraph(g.row_ptr, g.col, workspace_bytes=1 << 27)
     try:
+        G.set_option(LAP_OPT_KERNEL, kernel)
         v = G.set_root()
         G.cv_set_potentials(None, torch.from_numpy(phi2).cuda())
         y1, y2, m2 = G.sample_trace_cv(64, 3)
         torch.cuda.synchronize()
+        assert G.stat(LAP_STAT_LAST_KERNEL) == kernel
     finally:
         G.close()
     cnt, a1, a2, p2, m2o = oracle.sample_cv(g.row_ptr, g.col, v, 3, 0, 64, h2=CV.quantize_potential(phi2))
