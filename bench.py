@@ -95,10 +95,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ws-frac", type=float, default=0.6, help="fraction of free HBM lent as Wilson state")
     ap.add_argument("--ws-gb", type=float, default=0.0, help="cap on the Wilson-state workspace in GB (profiler runs)")
-    ap.add_argument("--tta-large", default="ba_1m:16384:plain+paths+cv,rmat_22:65536:plain",
+    ap.add_argument("--tta-large", default="ba_1m:16384:plain+paths+cv+cvpaths,rmat_22:65536:plain+cv",
                     help="time to accuracy on large graphs: workload:largest omega of the grid[:forms joined by +], "
                          "comma separated (forms default to --tta-forms)")
-    ap.add_argument("--tta-forms", default="plain,paths,cv", help="estimator forms of the large-graph runs")
+    ap.add_argument("--tta-forms", default="plain,paths,cv",
+                    help="estimator forms of the large-graph runs (plain, paths, cv, cvpaths: the control variate "
+                         "with the loop-included paths)")
     ap.add_argument("--tta-seeds", type=int, default=10, help="seeds (disjoint id ranges) per form")
     ap.add_argument("--kernel", type=int, default=0, help="LAP_OPT_KERNEL for the timed steps (0: the library's choice)")
     ap.add_argument("--walkers", type=int, default=8, help="LAP_OPT_WALKERS (kernel 3)")
@@ -406,11 +408,12 @@ class CheckpointBlocks:
         from paper_2311_10290_gb300.lap import LAP_OPT_SLOTS, LAP_OPT_WALKERS
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         lanes = sms * 1024
-        walkers = 8 if form == "plain" else 1          # kernel 3 counts groups of 8 lanes as one slot
+        paths = form in ("paths", "cvpaths")
+        walkers = 1 if paths else 8                    # kernel 3 counts groups of 8 lanes as one slot
         for k, sz in enumerate(sizes):
             ws = max(8 * g.n * 4, int(ws_total * sz / grid[-1]))
             H = LapGraph(g.row_ptr, g.col, workspace_bytes=ws, stream=self.streams[k])
-            H.set_option(LAP_OPT_PATHS, 1 if form == "paths" else 0)
+            H.set_option(LAP_OPT_PATHS, 1 if paths else 0)
             H.set_option(LAP_OPT_WALKERS, 8)
             H.set_option(LAP_OPT_SLOTS, max(1, int(lanes / walkers * sz / grid[-1])))
             self.handles.append(H)
@@ -501,7 +504,7 @@ def timed_run(torch, LapGraph, g, v, omega, first, seed, form, phi=None, betas=N
     from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, LAP_OPT_PATHS, LAP_STAT_LAST_KERNEL
     H = LapGraph(g.row_ptr, g.col, workspace_bytes=int(torch.cuda.mem_get_info()[0] * 0.5))
     try:
-        H.set_option(LAP_OPT_PATHS, 1 if form == "paths" else 0)
+        H.set_option(LAP_OPT_PATHS, 1 if form in ("paths", "cvpaths") else 0)
         H.set_root(v)
         H.set_option(LAP_OPT_CURSOR, first)
         if phi is not None:
@@ -548,17 +551,20 @@ def time_to_accuracy_large(torch, LapGraph, g, v, exact, omega_max, forms=("plai
     grid = omega_grid(omega_max)
     ws_total = int(torch.cuda.mem_get_info()[0] * ws_frac)
     stored, finals = [], []
-    base = {"plain": 0, "paths": 1 << 30, "cv": (1 << 30) + (1 << 29)}
+    base = {"plain": 0, "paths": 1 << 30, "cv": (1 << 30) + (1 << 29), "cvpaths": 1 << 31}
     for form in forms:
-        if form == "cv" and params is None:
+        if form in ("cv", "cvpaths") and params is None:
             continue
         t0 = time.perf_counter()
         phi = betas = None
         prep = 0.0
-        if form == "cv":
+        if form in ("cv", "cvpaths"):
+            from paper_2311_10290_gb300.lap import LAP_OPT_PATHS
             from paper_2311_10290_gb300.lap import LapGraph as LG
             P = LG(g.row_ptr, g.col, workspace_bytes=int(torch.cuda.mem_get_info()[0] * 0.3))
             try:
+                # The coefficients are fitted on pilot samples of the same form.
+                P.set_option(LAP_OPT_PATHS, 1 if form == "cvpaths" else 0)
                 P.set_root(v)
                 torch.cuda.synchronize()
                 tp = time.perf_counter()
@@ -599,7 +605,7 @@ def time_to_accuracy_large(torch, LapGraph, g, v, exact, omega_max, forms=("plai
         r = {"curve": [{"omega": w, "ecc_max_rel": round(float(mean[j, 0]), 5), "kc_rel": round(float(mean[j, 1]), 7)}
                        for j, w in enumerate(grid)],
              "truth_samples": (seeds - 1 if form == "plain" else seeds) * omega_max, "wall_seconds": round(wall, 1)}
-        if form == "cv":
+        if form in ("cv", "cvpaths"):
             r["betas"] = list(betas)
             r["prepare_seconds"] = round(prep, 2)
         if found is None:
@@ -822,12 +828,10 @@ def cv_measurement(torch, LapGraph, g, v, params, samples_per_batch, batches):
     estimator between `batches` independent batches.  The coefficients come
     from separate pilot samples, so both estimators stay unbiased."""
     from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, lap_counts
-    from paper_2311_10290_gb300.lap import LAP_OPT_KERNEL
     free, _ = torch.cuda.mem_get_info()
     G = LapGraph(g.row_ptr, g.col, workspace_bytes=int(free * 0.5))
     try:
-        G.set_option(LAP_OPT_KERNEL, 2)           # plain and CV timed on the same kernel
-        G.set_root(v)
+        G.set_root(v)                             # plain and CV: the library's kernel choice for the same calls
         t0 = time.perf_counter()
         phi1, phi2, beta1, beta2 = cv_prepare(G, params, 4242, pilot=2 * samples_per_batch, batches=4)
         t_prep = time.perf_counter() - t0
