@@ -88,12 +88,13 @@ typedef enum {
                                   3 = several walkers per sample (LAP_OPT_WALKERS lanes share one
                                   Wilson run; 2 bytes of state per node): more independent memory
                                   chains when a call has few samples, and each sample finishes
-                                  sooner.  Kernel 3 needs n < 2^22 and covers the estimators with
-                                  their own absorbed walks, with or without the control variate
-                                  (with LAP_OPT_PATHS = 1 kernel 2 runs instead).  Its samples
-                                  that do not fit (a node drawn 1023 times, a
-                                  path longer than a walker's stack, a walker without progress for
-                                  4 s) are withdrawn and re-run with kernel 1.
+                                  sooner.  Kernel 3 needs n < 2^22 and covers every estimator
+                                  form (LAP_OPT_PATHS 0 or 1, with or without the control
+                                  variate; 2 more bytes per node with LAP_OPT_PATHS = 1).  Its
+                                  samples that do not fit (a node drawn 1023 times, a path longer
+                                  than a walker's stack, a walker without progress for 4 s, a node
+                                  left 255 times by one loop-included path) are withdrawn and
+                                  re-run with kernel 1.
                                   Counts are identical with every kernel. */
     LAP_OPT_STACK = 6,         /* loop-erased path capacity per sample (kernel 2) or walker (kernel 3); 0 = default
                                   (16 sqrt(n) rounded up to a power of two, at least 1024) */

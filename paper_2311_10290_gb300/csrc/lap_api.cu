@@ -101,20 +101,21 @@ uint64_t slot_bytes_of(const lap_graph *g, int kernel)
 {
     if (kernel == LAP_KERNEL_WIDE) return 8ull * (uint64_t)g->n;
     if (kernel == LAP_KERNEL_GROUP)
-        // Control block, 16-bit words, path stacks: 8 stacks' worth of entries
-        // shared out among the sample's walkers.
-        return (64ull + 2ull * n_pad_of(g) + 4ull * stack_cap_of(g) * 8ull + 255ull) & ~255ull;
+        // Control block, 16-bit words, departure bytes of the two loop-included
+        // paths (2 per node, LAP_OPT_PATHS only), path stacks: 8 stacks' worth
+        // of entries shared out among the sample's walkers.
+        return (64ull + (g->paths_opt ? 4ull : 2ull) * n_pad_of(g) + 4ull * stack_cap_of(g) * 8ull + 255ull) & ~255ull;
     // State bytes, path-count bytes (loop-included paths only), stack, count table.
     return ((g->paths_opt ? 2ull : 1ull) * n_pad_of(g) + 4ull * stack_cap_of(g) + (8ull << lap_table_log2(g->n)) +
             255ull) & ~255ull;
 }
 
-// Kernel 3 covers the estimators with independent absorbed walks (no
-// loop-included paths), with or without the control variate, on graphs with
-// n < 2^22 (its stack entries hold 22-bit node ids).
+// Kernel 3 covers every estimator form (own absorbed walks or loop-included
+// paths, with or without the control variate) on graphs with n < 2^22 (its
+// stack entries hold 22-bit node ids).
 bool group_ok(const lap_graph *g)
 {
-    return g->n < (1 << 22) && !g->paths_opt && !g->compact_disabled &&
+    return g->n < (1 << 22) && !g->compact_disabled &&
            (!g->ws || g->ws_bytes >= slot_bytes_of(g, LAP_KERNEL_GROUP));
 }
 
@@ -213,7 +214,8 @@ lap_status launch(lap_graph *g, LapSampleLaunch &p, int kernel)
     p.stack_cap = kernel == LAP_KERNEL_COMPACT
                       ? (uint32_t)((p.slot_bytes - (p.paths ? 2ull : 1ull) * p.n_pad - (8ull << p.tbl_log2)) / 4ull)
                   : kernel == LAP_KERNEL_GROUP
-                      ? (uint32_t)(((p.slot_bytes - 64ull - 2ull * p.n_pad) / 4ull / (uint64_t)walkers_for(g, p.count)) & ~3ull)
+                      ? (uint32_t)(((p.slot_bytes - 64ull - (p.paths ? 4ull : 2ull) * p.n_pad) / 4ull /
+                                    (uint64_t)walkers_for(g, p.count)) & ~3ull)
                       : 0u;
     LAP_CUDA(g, cudaMemsetAsync(&g->d_acc->claim, 0, sizeof(unsigned int), g->stream));
     const cudaError_t e = kernel == LAP_KERNEL_WIDE    ? lap_launch_sample(p, g->stream)

@@ -41,6 +41,13 @@
 // A1[u] (once per draw: a pending arrow taken again adds nothing), and the
 // pi-start walk adds h2[w] to A2[u], 1 to P2[u] and (d_u h2[w] - S2[u]) / d_u
 // to the sample's M2, as in the other samplers.
+//
+// Loop-included paths (PATHS): the two absorbed walks take the sample's own
+// stacks (departure j from u follows u's stack entry j, the Philox draw
+// (u, j, i, 0)), counting departures per node in one byte per walk (a region
+// of 2 bytes per node after the state words).  A node left 255 times by one
+// walk withdraws the sample; the group then also subtracts the walks'
+// departures (cnt2, and with the CV the pi walk's A2 and P2 terms).
 #include "lap_internal.h"
 #include "philox.cuh"
 
@@ -170,7 +177,7 @@ __device__ __forceinline__ int32_t arrow_of(const int32_t *col, uint64_t r, uint
 
 enum : uint32_t { G_SCAN = 0, G_STEP, G_MOVE, G_DONE };
 
-template <int W, bool CV>
+template <int W, bool CV, bool PATHS>
 __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
 {
     static_assert(W == 2 || W == 4 || W == 8 || W == 16, "walkers per sample");
@@ -189,8 +196,9 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
     uint8_t *base = reinterpret_cast<uint8_t *>(p.ws) + slot * p.slot_bytes;
     GroupCtl *ctl = reinterpret_cast<GroupCtl *>(base);
     uint16_t *st = reinterpret_cast<uint16_t *>(base + 64);
+    uint8_t *pc = base + 64 + 2ull * p.n_pad;           // PATHS: departures, 2 bytes per node
     const uint32_t cap = p.stack_cap;                   // entries per walker, a multiple of 4
-    uint32_t *stk = reinterpret_cast<uint32_t *>(base + 64 + 2ull * p.n_pad) + (uint64_t)j * cap;
+    uint32_t *stk = reinterpret_cast<uint32_t *>(base + 64 + (PATHS ? 4ull : 2ull) * p.n_pad) + (uint64_t)j * cap;
     const uint32_t nchunks = (uint32_t)((n + (int32_t)kChunk - 1) / (int32_t)kChunk);   // chunks holding nodes
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
     const uint64_t limit = p.step_limit;
@@ -208,7 +216,7 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
         // Clear the slot's state and control block; the root starts in the tree.
         {
             uint4 *s4 = reinterpret_cast<uint4 *>(st);
-            const uint64_t n4 = 2ull * p.n_pad / 16u;
+            const uint64_t n4 = (PATHS ? 4ull : 2ull) * p.n_pad / 16u;    // state words and departure bytes
             for (uint64_t x = j; x < n4; x += W) s4[x] = make_uint4(0u, 0u, 0u, 0u);
             if (j == 0) {
                 uint4 *c4 = reinterpret_cast<uint4 *>(ctl);
@@ -434,8 +442,74 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
         atomicAdd(&ctl->y1, (unsigned long long)y1);
         __threadfence();
         __syncwarp(gmask);
-        if (ld_u32(&ctl->status) & kWithdraw) {
-            // Withdraw the sample: subtract the repeat visits counted so far.
+        bool wdrawn = (ld_u32(&ctl->status) & kWithdraw) != 0u;
+        uint64_t y2 = 0;
+        double m2 = 0.0;
+        if (!wdrawn) {
+            if (j == 0) {
+                // Alg. 2: the v-absorbed walk from a uniform start (or the fixed
+                // start of a single-source row), counting passes; with PATHS,
+                // the loop-included path on the sample's stacks.
+                uint64_t t = 0;
+                int32_t u = p.ustart ? (int32_t)(p.ustart - 1u)
+                                     : (int32_t)lap::below(lap::philox_r64(0u, 0u, i, 1u, key0, key1), (uint64_t)n);
+                if (!PATHS) {
+                    while (u != v) {
+                        atomicAdd(&p.cnt2[u], 1ull);
+                        if (++t > limit) { bad |= LAP_DEV_STEP_LIMIT; break; }
+                        const uint64_t r = ld_row(rowinfo, u, keep);
+                        u = ld_col(col + (int64_t)(int32_t)(uint32_t)r +
+                                   (int64_t)lap::below(lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1), (uint32_t)(r >> 32)), keep);
+                    }
+                } else {
+                    while (u != v) {
+                        if (++t > limit) { bad |= LAP_DEV_STEP_LIMIT; break; }
+                        const uint32_t jd = pc[2 * (int64_t)u];
+                        if (jd == 255u) { atomicOr(&ctl->status, kWithdraw); break; }
+                        const uint64_t r = ld_row(rowinfo, u, keep);
+                        const int32_t x = arrow_of(col, r, (uint32_t)u, jd, i, key0, key1, keep);
+                        pc[2 * (int64_t)u] = (uint8_t)(jd + 1u);
+                        atomicAdd(&p.cnt2[u], 1ull);
+                        u = x;
+                    }
+                }
+            }
+            if (j == 1u) {
+                // Alg. 4: the v-absorbed walk from s ~ pi (the head of a uniform
+                // arc); Y2 = its length.  With PATHS, the loop-included path.
+                int32_t u = ld_col(col + (int64_t)lap::below(lap::philox_r64(0u, 0u, i, 2u, key0, key1), (uint64_t)p.g.arcs), keep);
+                while (u != v) {
+                    if (++y2 > limit) { bad |= LAP_DEV_STEP_LIMIT; break; }
+                    const uint64_t r = ld_row(rowinfo, u, keep);
+                    int32_t x;
+                    if (PATHS) {
+                        const uint32_t jd = pc[2 * (int64_t)u + 1];
+                        if (jd == 255u) { atomicOr(&ctl->status, kWithdraw); break; }
+                        x = arrow_of(col, r, (uint32_t)u, jd, i, key0, key1, keep);
+                        pc[2 * (int64_t)u + 1] = (uint8_t)(jd + 1u);
+                    } else {
+                        x = ld_col(col + (int64_t)(int32_t)(uint32_t)r +
+                                   (int64_t)lap::below(lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1), (uint32_t)(r >> 32)), keep);
+                    }
+                    if (CV && p.cv_h2) {
+                        const long long d = (long long)(r >> 32), hx = ld_pot(p.cv_h2 + x), s2 = ld_pot(p.cv_S2 + u);
+                        atomicAdd(&p.cv_a2[u], (unsigned long long)hx);
+                        atomicAdd(&p.cv_p2[u], 1ull);
+                        m2 = __dadd_rn(m2, __ddiv_rn((double)(d * hx - s2), (double)d));
+                    }
+                    u = x;
+                }
+            }
+            if (PATHS) {
+                // A walk that met a node's 255th departure withdraws the sample.
+                __threadfence();
+                __syncwarp(gmask);
+                wdrawn = (ld_u32(&ctl->status) & kWithdraw) != 0u;
+            }
+        }
+        if (wdrawn) {
+            // Withdraw the sample: subtract the repeat visits counted so far
+            // (and the control-variate and path terms added so far).
             for (int32_t x = (int32_t)j; x < n; x += W) {
                 const uint32_t k = ld_word(st + x) & L::k;
                 if (k >= 2u) atomicAdd(&p.rep1[x], (unsigned long long)(-(long long)(k - 1u)));
@@ -446,6 +520,17 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
                     for (uint32_t d = 0; d < k; ++d) sub += ld_pot(p.cv_h1 + arrow_of(col, r, (uint32_t)x, d, i, key0, key1, keep));
                     atomicAdd(&p.cv_a1[x], (unsigned long long)(-sub));
                 }
+                if (PATHS) {
+                    const uint32_t cu = pc[2 * (int64_t)x], cp = pc[2 * (int64_t)x + 1];
+                    if (cu) atomicAdd(&p.cnt2[x], (unsigned long long)(-(long long)cu));
+                    if (CV && p.cv_h2 && cp) {
+                        const uint64_t r = ld_row(rowinfo, x, keep);
+                        long long sub = 0;
+                        for (uint32_t d = 0; d < cp; ++d) sub += ld_pot(p.cv_h2 + arrow_of(col, r, (uint32_t)x, d, i, key0, key1, keep));
+                        atomicAdd(&p.cv_a2[x], (unsigned long long)(-sub));
+                        atomicAdd(&p.cv_p2[x], (unsigned long long)(-(long long)cp));
+                    }
+                }
             }
             if (j == 0) {
                 const unsigned int ix = atomicAdd(&p.acc->ovf_count, 1u);
@@ -453,40 +538,11 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
             }
         } else {
             if (j == 0) {
-                // Alg. 2: the v-absorbed walk from a uniform start (or the fixed
-                // start of a single-source row), counting passes.
-                uint64_t t = 0;
-                int32_t u = p.ustart ? (int32_t)(p.ustart - 1u)
-                                     : (int32_t)lap::below(lap::philox_r64(0u, 0u, i, 1u, key0, key1), (uint64_t)n);
-                while (u != v) {
-                    atomicAdd(&p.cnt2[u], 1ull);
-                    if (++t > limit) { bad |= LAP_DEV_STEP_LIMIT; break; }
-                    const uint64_t r = ld_row(rowinfo, u, keep);
-                    u = ld_col(col + (int64_t)(int32_t)(uint32_t)r +
-                               (int64_t)lap::below(lap::philox_r64((uint32_t)t, 0u, i, 1u, key0, key1), (uint32_t)(r >> 32)), keep);
-                }
                 const unsigned long long sy1 = ld_u64(&ctl->y1);
                 acc1 += sy1;
                 if (p.y1_out) p.y1_out[i - p.first] = sy1;
             }
             if (j == 1u) {
-                // Alg. 4: the v-absorbed walk from s ~ pi (the head of a uniform arc); Y2 = its length.
-                uint64_t y2 = 0;
-                double m2 = 0.0;
-                int32_t u = ld_col(col + (int64_t)lap::below(lap::philox_r64(0u, 0u, i, 2u, key0, key1), (uint64_t)p.g.arcs), keep);
-                while (u != v) {
-                    if (++y2 > limit) { bad |= LAP_DEV_STEP_LIMIT; break; }
-                    const uint64_t r = ld_row(rowinfo, u, keep);
-                    const int32_t x = ld_col(col + (int64_t)(int32_t)(uint32_t)r +
-                                             (int64_t)lap::below(lap::philox_r64((uint32_t)y2, 0u, i, 2u, key0, key1), (uint32_t)(r >> 32)), keep);
-                    if (CV && p.cv_h2) {
-                        const long long d = (long long)(r >> 32), hx = ld_pot(p.cv_h2 + x), s2 = ld_pot(p.cv_S2 + u);
-                        atomicAdd(&p.cv_a2[u], (unsigned long long)hx);
-                        atomicAdd(&p.cv_p2[u], 1ull);
-                        m2 = __dadd_rn(m2, __ddiv_rn((double)(d * hx - s2), (double)d));
-                    }
-                    u = x;
-                }
                 acc2 += y2;
                 if (p.y2_out) p.y2_out[i - p.first] = y2;
                 if (CV && p.m2_out) p.m2_out[i - p.first] = m2;
@@ -502,8 +558,13 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
 template <int W>
 void launch_group(const LapSampleLaunch &p, bool cv, uint64_t grid, int block, cudaStream_t st)
 {
-    if (cv) lewalk_group_kernel<W, true><<<(unsigned)grid, block, 0, st>>>(p);
-    else lewalk_group_kernel<W, false><<<(unsigned)grid, block, 0, st>>>(p);
+    if (p.paths) {
+        if (cv) lewalk_group_kernel<W, true, true><<<(unsigned)grid, block, 0, st>>>(p);
+        else lewalk_group_kernel<W, false, true><<<(unsigned)grid, block, 0, st>>>(p);
+    } else {
+        if (cv) lewalk_group_kernel<W, true, false><<<(unsigned)grid, block, 0, st>>>(p);
+        else lewalk_group_kernel<W, false, false><<<(unsigned)grid, block, 0, st>>>(p);
+    }
 }
 
 }  // namespace

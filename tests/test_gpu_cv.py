@@ -97,8 +97,6 @@ def _cv_run(g, root, seed, omega, phi1, phi2, kernel=None, splits=None, paths=Fa
                                              ("path_table_heavy", lambda: I.path(256), 255)],
                          ids=["ba", "rmat", "path_counts_table", "path_table_heavy"])
 def test_cv_sums_and_estimates_match_oracle(name, maker, root, kernel, paths):
-    if kernel == 3 and paths:
-        pytest.skip("kernel 3 has no loop-included-path mode")
     g = maker()
     rng = np.random.default_rng(3)
     phi1 = rng.uniform(0.0, 3.0, g.n)
@@ -108,19 +106,21 @@ def test_cv_sums_and_estimates_match_oracle(name, maker, root, kernel, paths):
     _check_cv(g, r, phi1, phi2, 17, 300, paths)
 
 
+@pytest.mark.parametrize("paths", [False, True], ids=["own_draws", "stack_paths"])
 @pytest.mark.parametrize("walkers", [2, 4, 8, 16])
-def test_cv_group_kernel_withdrawn_samples_are_rerun_exactly(walkers):
+def test_cv_group_kernel_withdrawn_samples_are_rerun_exactly(walkers, paths):
     """Kernel 3 with a 16-entry stack per walker on a path graph rooted at
     one end: samples are withdrawn (their repeat visits and the potentials of
-    all their Wilson draws subtracted) and re-run with kernel 1; every CV sum
+    all their Wilson draws subtracted, and with loop-included paths their
+    departures and pi-path terms) and re-run with kernel 1; every CV sum
     stays bit-exact."""
     g = I.path(200)
     rng = np.random.default_rng(8)
     phi1 = rng.uniform(0.0, 3.0, g.n)
     phi2 = rng.uniform(0.0, 50.0, g.n)
-    r = _cv_run(g, 0, 23, 64, phi1, phi2, kernel=3, walkers=walkers, stack=16)
+    r = _cv_run(g, 0, 23, 64, phi1, phi2, kernel=3, walkers=walkers, stack=16, paths=paths)
     assert r["fallbacks"] > 0
-    _check_cv(g, r, phi1, phi2, 23, 64, False)
+    _check_cv(g, r, phi1, phi2, 23, 64, paths)
 
 
 @pytest.mark.parametrize("walkers", [8, 16])

@@ -18,17 +18,19 @@ from paper_2311_10290_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-from paper_2311_10290_gb300.lap import (LAP_OPT_KERNEL, LAP_OPT_PATH_START, LAP_OPT_SLOTS,  # noqa: E402
-                                        LAP_OPT_STACK, LAP_OPT_WALKERS, LAP_STAT_FALLBACKS, LAP_STAT_KERNEL,
-                                        LapGraph)
+from paper_2311_10290_gb300.lap import (LAP_OPT_KERNEL, LAP_OPT_PATH_START, LAP_OPT_PATHS,  # noqa: E402
+                                        LAP_OPT_SLOTS, LAP_OPT_STACK, LAP_OPT_WALKERS, LAP_STAT_FALLBACKS,
+                                        LAP_STAT_KERNEL, LAP_STAT_LAST_KERNEL, LapGraph)
 
 
 def run3(g, seed, omega, walkers=0, root=-1, slots=None, stack=None, trace=False, start=None, ws=1 << 27,
-         splits=None):
+         splits=None, paths=False):
     G = LapGraph(g.row_ptr, g.col, workspace_bytes=ws)
     try:
         G.set_option(LAP_OPT_KERNEL, 3)
         G.set_option(LAP_OPT_WALKERS, walkers)
+        if paths:
+            G.set_option(LAP_OPT_PATHS, 1)
         if slots:
             G.set_option(LAP_OPT_SLOTS, slots)
         if stack:
@@ -44,7 +46,8 @@ def run3(g, seed, omega, walkers=0, root=-1, slots=None, stack=None, trace=False
             for part in (splits or [omega]):
                 G.sample(part, seed)
         c1, c2, s = G.counts()
-        out = dict(v=v, cnt1=c1, cnt2=c2, sums=s, fallbacks=G.stat(LAP_STAT_FALLBACKS))
+        out = dict(v=v, cnt1=c1, cnt2=c2, sums=s, fallbacks=G.stat(LAP_STAT_FALLBACKS),
+                   kernel=G.stat(LAP_STAT_LAST_KERNEL))
         if start is None:
             out.update(ld=G.ldiag(), ecc=G.ecc(), kc=G.kemeny())
         if y is not None:
@@ -131,3 +134,33 @@ def test_group_kernel_full_size_rmat22_small_omega(walkers):
     c = oracle.sample_threads(g.row_ptr, g.col, r["v"], 5, 0, 32, 16)
     assert_counts(r, c, 32)
     assert r["fallbacks"] == 0
+
+
+@pytest.mark.parametrize("walkers", [2, 4, 8, 16])
+@pytest.mark.parametrize("name,maker,root,omega", [c for c in CASES if c[0] in ("k4e_v0", "cycle101", "ba3000",
+                                                                                  "rmat12", "er300_sparse")],
+                         ids=["k4e_v0", "cycle101", "ba3000", "rmat12", "er300_sparse"])
+def test_group_kernel_loop_included_paths_match_oracle(name, maker, root, omega, walkers):
+    """LAP_OPT_PATHS = 1 on kernel 3: the two absorbed walks take the
+    sample's own stacks; counts bit-exact with the oracle's paths mode."""
+    g = maker()
+    r = run3(g, 4711, omega, walkers=walkers, root=root, paths=True, splits=[omega // 3, omega - omega // 3])
+    assert r["kernel"] == 3
+    c = oracle.sample(g.row_ptr, g.col, r["v"], 4711, 0, omega, keep_per_sample=False, paths=True)
+    assert_counts(r, c, omega)
+    ld, ec, kc = oracle.finalize(g.row_ptr, r["v"], omega, c.cnt1, c.cnt2, c.sum_y1, c.sum_y2)
+    np.testing.assert_allclose(r["ecc"], ec, rtol=1e-12, atol=0)
+    assert r["kc"] == pytest.approx(kc, rel=1e-12)
+
+
+@pytest.mark.parametrize("walkers", [4, 16])
+def test_group_kernel_paths_departure_cap_withdraws_exactly(walkers):
+    """On a path graph rooted at one end, loop-included paths leave some nodes
+    255 or more times in one sample: those samples are withdrawn (their
+    Wilson and path departures subtracted) and re-run with kernel 1."""
+    g = I.path(200)
+    r = run3(g, 19, 48, walkers=walkers, root=0, paths=True, trace=True)
+    assert r["fallbacks"] > 0
+    c = oracle.sample(g.row_ptr, g.col, 0, 19, 0, 48, paths=True)
+    assert_counts(r, c, 48)
+    assert np.array_equal(r["y1"], c.y1) and np.array_equal(r["y2"], c.y2)
