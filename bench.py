@@ -95,7 +95,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ws-frac", type=float, default=0.6, help="fraction of free HBM lent as Wilson state")
     ap.add_argument("--ws-gb", type=float, default=0.0, help="cap on the Wilson-state workspace in GB (profiler runs)")
-    ap.add_argument("--tta-large", default="ba_1m:16384:plain+paths+cv+cvpaths,rmat_22:65536:plain+cv",
+    ap.add_argument("--tta-large", default="ba_1m:16384:plain+paths+cv+cvpaths,rmat_22:65536:plain+cvpaths",
                     help="time to accuracy on large graphs: workload:largest omega of the grid[:forms joined by +], "
                          "comma separated (forms default to --tta-forms)")
     ap.add_argument("--tta-forms", default="plain,paths,cv",
@@ -409,7 +409,7 @@ class CheckpointBlocks:
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         lanes = sms * 1024
         paths = form in ("paths", "cvpaths")
-        walkers = 1 if paths else 8                    # kernel 3 counts groups of 8 lanes as one slot
+        walkers = 8                                    # kernel 3 counts groups of 8 lanes as one slot
         for k, sz in enumerate(sizes):
             ws = max(8 * g.n * 4, int(ws_total * sz / grid[-1]))
             H = LapGraph(g.row_ptr, g.col, workspace_bytes=ws, stream=self.streams[k])
@@ -896,10 +896,9 @@ def paths_measurement(torch, LapGraph, g, v, args, samples=8192, batches=4):
     """LAP_OPT_PATHS = 1 against own draws on one graph: per-sample variance
     of Y1 - Y2 (Kemeny), per-node variance of the L^+_uu numerator
     (cnt1 - 2 cnt2) / d between batches (ECC), and sampler time."""
-    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, LAP_OPT_KERNEL, LAP_OPT_PATHS, lap_counts
+    from paper_2311_10290_gb300.lap import LAP_OPT_CURSOR, LAP_OPT_PATHS, LAP_STAT_LAST_KERNEL, lap_counts
     free, _ = torch.cuda.mem_get_info()
-    out = {"workload": g.name, "samples": samples, "batches": batches,
-           "kernel": "the 1-byte kernel in both modes (the several-walkers kernel has no path mode)"}
+    out = {"workload": g.name, "samples": samples, "batches": batches}
     d = np.diff(g.row_ptr.astype(np.int64)).astype(np.float64)
     keep = np.ones(g.n, bool)
     keep[v] = False
@@ -907,8 +906,7 @@ def paths_measurement(torch, LapGraph, g, v, args, samples=8192, batches=4):
     for mode in (0, 1):
         G = LapGraph(g.row_ptr, g.col, workspace_bytes=int(free * 0.5))
         try:
-            G.set_option(LAP_OPT_KERNEL, 2)
-            G.set_option(LAP_OPT_PATHS, mode)
+            G.set_option(LAP_OPT_PATHS, mode)             # the library's kernel choice in both modes
             G.set_root(v)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -917,6 +915,7 @@ def paths_measurement(torch, LapGraph, g, v, args, samples=8192, batches=4):
             b.record()
             torch.cuda.synchronize()
             t = a.elapsed_time(b) / 1e3
+            out["kernel_paths%d" % mode] = G.stat(LAP_STAT_LAST_KERNEL)
             kvar = float(np.var((y1 - y2).double().cpu().numpy()))
             G.set_root(v)
             G.set_option(LAP_OPT_CURSOR, samples)
