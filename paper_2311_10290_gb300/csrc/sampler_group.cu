@@ -442,7 +442,11 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
         atomicAdd(&ctl->y1, (unsigned long long)y1);
         __threadfence();
         __syncwarp(gmask);
-        bool wdrawn = (ld_u32(&ctl->status) & kWithdraw) != 0u;
+        // One lane reads the status and the group takes its value: with PATHS a
+        // walk below may set kWithdraw while a slower walker of the group has
+        // not read it yet, and every walker must take the same branch (they
+        // meet at warp barriers).
+        bool wdrawn = __shfl_sync(gmask, (int)(j == 0 && (ld_u32(&ctl->status) & kWithdraw) != 0u), (int)gbase) != 0;
         uint64_t y2 = 0;
         double m2 = 0.0;
         if (!wdrawn) {
@@ -504,7 +508,7 @@ __global__ void __launch_bounds__(256, 5) lewalk_group_kernel(LapSampleLaunch p)
                 // A walk that met a node's 255th departure withdraws the sample.
                 __threadfence();
                 __syncwarp(gmask);
-                wdrawn = (ld_u32(&ctl->status) & kWithdraw) != 0u;
+                wdrawn = __shfl_sync(gmask, (int)(j == 0 && (ld_u32(&ctl->status) & kWithdraw) != 0u), (int)gbase) != 0;
             }
         }
         if (wdrawn) {

@@ -118,10 +118,11 @@ def test_group_kernel_withdrawn_samples_are_rerun_exactly():
     assert_counts(r, c, 64)
 
 
-def test_group_kernel_fixed_start_rows():
+@pytest.mark.parametrize("paths", [False, True], ids=["own_draws", "stack_paths"])
+def test_group_kernel_fixed_start_rows(paths):
     g = I.er(300, 0.02, seed=2)
-    r = run3(g, 4242, 800, walkers=8, start=17)
-    c = oracle.sample(g.row_ptr, g.col, r["v"], 4242, 0, 800, keep_per_sample=False, path_start=17)
+    r = run3(g, 4242, 800, walkers=8, start=17, paths=paths)
+    c = oracle.sample(g.row_ptr, g.col, r["v"], 4242, 0, 800, keep_per_sample=False, path_start=17, paths=paths)
     assert_counts(r, c, 800)
 
 
