@@ -113,7 +113,10 @@ def parse():
     ap.add_argument("--batched-orders", default="0",
                     help="unit orders to time on the uneven batch: 0 largest first, 1 smallest first")
     ap.add_argument("--landmark-roots", type=int, default=6,
-                    help="roots of the landmark study on the BA 1e6 graph (0: skip)")
+                    help="highest-degree roots of the landmark study on the BA 1e6 graph (0: skip)")
+    ap.add_argument("--landmark-random", type=int, default=0,
+                    help="random roots added to the landmark study (their absorbed walks to low-degree roots "
+                         "run ~1e7 steps one after another: about 80 s for 256 samples)")
     ap.add_argument("--kemeny-sweep", type=int, default=1, help="kappa/n of 1e6-node BA and ER graphs (0: skip)")
     ap.add_argument("--study-samples", type=int, default=256, help="samples per root / graph of the two studies")
     ap.add_argument("--paths", type=int, default=1,
@@ -1027,8 +1030,8 @@ def landmark_study(torch, g, args):
     batched launch sharing one copy of the CSR."""
     from paper_2311_10290_gb300.lap import LapBatch
     deg = np.diff(g.row_ptr.astype(np.int64))
-    n_rand = args.landmark_roots // 3
-    top = [int(x) for x in np.argsort(-deg, kind="stable")[:max(1, args.landmark_roots - n_rand)]]
+    n_rand = args.landmark_random
+    top = [int(x) for x in np.argsort(-deg, kind="stable")[:max(1, args.landmark_roots)]]
     rng = np.random.Generator(np.random.PCG64(7))
     rand = [int(x) for x in rng.choice(g.n, size=n_rand, replace=False)]
     roots = top + rand
