@@ -76,8 +76,9 @@ typedef enum {
                                   first sample after lap_set_root.  Lets several processes or GPUs
                                   draw disjoint sample-id ranges whose counts add up exactly. */
     LAP_OPT_KERNEL = 5,        /* 0 = automatic: kernel 3 for calls of at most 320 samples per SM
-                                  (1024 when the graph's arrays exceed 96 MB) when it applies,
-                                  else kernel 2 when n < 2^27, else kernel 1.
+                                  (1024 when the graph's arrays exceed 96 MB) on graphs of at
+                                  least 2^14 nodes when it applies, else kernel 2 when n < 2^27,
+                                  else kernel 1.
                                   1 = 8-byte state per node.
                                   2 = 1-byte state per node.  Kernel 2 keeps draw counts above 30
                                   (and, with LAP_OPT_PATHS = 1, path departure counts above 14) in

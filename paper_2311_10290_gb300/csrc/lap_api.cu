@@ -127,6 +127,13 @@ bool group_ok(const lap_graph *g)
 constexpr uint64_t kGroupAutoPerSm = 320;
 constexpr uint64_t kGroupAutoPerSmLarge = 1024;     // graphs whose arrays exceed kL2Graph
 constexpr uint64_t kL2Graph = 96ull << 20;
+// Smaller graphs keep kernel 2: on a 1000-node graph a Wilson run is ~1,600
+// steps and a group's per-sample costs (slot clearing, chunk scans, walkers
+// meeting on few nodes) outweigh the shorter runs (92,682 samples: 15.7 ms
+// with kernel 2, 44 ms with 8 walkers; 23,170 samples with loop-included
+// paths: 16 ms and 27 ms), while from 10^5 nodes up kernel 3 wins for small
+// calls.  The threshold lies between the measured sizes.
+constexpr int32_t kGroupAutoMinNodes = 1 << 14;
 
 // Walkers per sample of kernel 3 for a call of n_samples: the option, or
 // 16 when the call's 16 lanes per sample fit on the GPU at once (1280 lanes
@@ -144,7 +151,8 @@ int choose_kernel(const lap_graph *g, uint64_t n_samples = 0)
     if (g->kernel_opt == LAP_KERNEL_GROUP && group_ok(g)) return LAP_KERNEL_GROUP;
     const bool large_graph = 4ull * (uint64_t)g->arcs + 8ull * (uint64_t)g->n > kL2Graph;
     const uint64_t per_sm = large_graph ? kGroupAutoPerSmLarge : kGroupAutoPerSm;
-    if (g->kernel_opt == 0 && n_samples > 0 && n_samples <= per_sm * (uint64_t)g->num_sms && group_ok(g))
+    if (g->kernel_opt == 0 && n_samples > 0 && n_samples <= per_sm * (uint64_t)g->num_sms &&
+        g->n >= kGroupAutoMinNodes && group_ok(g))
         return LAP_KERNEL_GROUP;
     if (g->n >= (1 << 27) || g->compact_disabled) return LAP_KERNEL_WIDE;
     if (g->ws && g->ws_bytes < slot_bytes_of(g, LAP_KERNEL_COMPACT)) return LAP_KERNEL_WIDE;
