@@ -201,11 +201,13 @@ __device__ __forceinline__ float warp_sum(float x)
     return x;
 }
 
+// Forward (TRAIN = false: Y = MLP(X)) or loss and gradient (TRAIN = true:
+// G and loss accumulate the batch's MSE gradient and loss).
 template <bool TRAIN>
-__global__ void __launch_bounds__(kThreads, TRAIN ? 1 : 4) mlp_tc_kernel(const float *__restrict__ P, const float *__restrict__ X,
-                                                            const float *__restrict__ T, int64_t n, float wk0,
-                                                            float wk1, float inv_n, float *__restrict__ Y,
-                                                            float *__restrict__ G, float *__restrict__ loss)
+__global__ void __launch_bounds__(kThreads, TRAIN ? 1 : 4)
+    mlp_tc_kernel(const float *__restrict__ P, const float *__restrict__ X, const float *__restrict__ T, int64_t n,
+                  float wk0, float wk1, float inv_n, float *__restrict__ Y, float *__restrict__ G,
+                  float *__restrict__ loss)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     constexpr uint32_t kOps = TRAIN ? align_up(kTrainF, 16) : align_up(kFwdOps, 16);
@@ -458,7 +460,10 @@ __global__ void __launch_bounds__(kThreads, TRAIN ? 1 : 4) mlp_tc_kernel(const f
         } else {
             for (int64_t tile = blockIdx.x; tile * kTile < n; tile += gridDim.x) {
                 const int64_t row = tile * kTile + tid;
-                if (row < n) *reinterpret_cast<float2 *>(Y + row * kOut) = make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+                if (row < n) {
+                    const float nan = __int_as_float(0x7fc00000);
+                    *reinterpret_cast<float2 *>(Y + row * kOut) = make_float2(nan, nan);
+                }
             }
         }
     } else if (TRAIN && any) {
