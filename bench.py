@@ -380,6 +380,13 @@ def time_to_accuracy(torch, LapGraph, seeds=10, target=1e-2, params=None, paths=
     return res
 
 
+# First sample id of each estimator form in the large-graph time-to-accuracy
+# runs: seed s of a form takes [base + s * omega_max, base + (s + 1) * omega_max),
+# its timed call [base + TTA_TIMED_OFFSET, ... + omega); all disjoint below 2^32.
+TTA_ID_BASE = {"plain": 0, "paths": 1 << 30, "cv": (1 << 30) + (1 << 29), "cvpaths": 1 << 31}
+TTA_TIMED_OFFSET = 1 << 28
+
+
 def omega_grid(omega_max, lo=256):
     """round(lo * 2^(k/2)) up to omega_max (the last point is omega_max)."""
     out, k = [], 0
@@ -554,7 +561,7 @@ def time_to_accuracy_large(torch, LapGraph, g, v, exact, omega_max, forms=("plai
     grid = omega_grid(omega_max)
     ws_total = int(torch.cuda.mem_get_info()[0] * ws_frac)
     stored, finals = [], []
-    base = {"plain": 0, "paths": 1 << 30, "cv": (1 << 30) + (1 << 29), "cvpaths": 1 << 31}
+    base = TTA_ID_BASE
     for form in forms:
         if form in ("cv", "cvpaths") and params is None:
             continue
@@ -624,7 +631,8 @@ def time_to_accuracy_large(torch, LapGraph, g, v, exact, omega_max, forms=("plai
             j = grid.index(found)
             r.update({"reached": True, "omega": found, "ecc_max_rel_err_mean": float(mean[j, 0]),
                       "kc_rel_err_mean": float(mean[j, 1])})
-            r.update(timed_run(torch, LapGraph, g, v, found, base[form] + (1 << 28), 1, form, phi=phi, betas=betas))
+            r.update(timed_run(torch, LapGraph, g, v, found, base[form] + TTA_TIMED_OFFSET, 1, form, phi=phi,
+                               betas=betas))
         res[form] = r
     return res
 
