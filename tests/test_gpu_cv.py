@@ -123,6 +123,21 @@ def test_cv_group_kernel_withdrawn_samples_are_rerun_exactly(walkers, paths):
     _check_cv(g, r, phi1, phi2, 23, 64, paths)
 
 
+@pytest.mark.parametrize("walkers", [4, 16])
+def test_cv_group_kernel_paths_departure_cap(walkers):
+    """Kernel 3, loop-included paths and the control variate on a path graph
+    rooted at one end (the samples of test_group_kernel_paths_departure_cap_*:
+    some paths leave a node 255 times): withdrawn samples give back their
+    path departures and the pi path's A2 and P2 terms; every sum bit-exact."""
+    g = I.path(200)
+    rng = np.random.default_rng(10)
+    phi1 = rng.uniform(0.0, 3.0, g.n)
+    phi2 = rng.uniform(0.0, 50.0, g.n)
+    r = _cv_run(g, 0, 19, 48, phi1, phi2, kernel=3, walkers=walkers, paths=True)
+    assert r["kernel"] == 3 and r["fallbacks"] > 0
+    _check_cv(g, r, phi1, phi2, 19, 48, True)
+
+
 @pytest.mark.parametrize("walkers", [8, 16])
 def test_cv_group_kernel_rmat(walkers):
     g = I.rmat(12, 8, seed=3)
